@@ -1,0 +1,388 @@
+#!/usr/bin/env python
+"""Benchmark of the hot path: one complex-Langevin step followed by gauge-
+cooling sweeps on a 32^4 lattice (SU(3) Wilson + clover theta-term,
+beta = 6.2, theta = 1.0, Haar-random SU(3) start), measured in
+site-updates/s (one site through one CL step and all of that step's cooling
+sweeps).
+
+Prints ONE JSON line (rank 0).  The headline `value` is the FP64 form; the
+FP32-storage form (FP32 links, FP64 exponentials / re-projection /
+reductions) runs on the same seeded noise and is reported under
+"forms".  Per-kernel durations come from CUDA events recorded by the library
+around each launch on the lattice's stream; `roofline` is for the kernel
+that dominates the step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+N > 1 (torchrun): every rank advances its own lattice (independent chains,
+no data-path collective); value = all ranks' site-updates / max rank time.
+--impl reference times the FP64 CPU oracle (the reference implementation of
+this method) on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOAD = dict(L=(32, 32, 32, 32), beta=6.2, theta=1.0, seed=1, eps=0.005, sweeps=10, alpha=1.0)
+WORKLOAD_NAME = ("32^4 SU(3) Wilson + clover theta, beta 6.2, theta 1.0, Haar hot start; "
+                 "1 CL step (eps 0.005) + 10 adaptive gauge-cooling sweeps (D2 = <|f|>, alpha 1)")
+METRIC = "CL+cooling site-updates/s"
+UNIT = "site-updates/s"
+# Bytes that must move per site-update (links read + written once per CL step
+# and once per fused cooling sweep, plus f): FP64 13,952 B, FP32 links 7,616 B.
+ALG_BYTES = {"fp64": 1152 + 10 * 1280, "fp32": 576 + 10 * 704}
+CPU_SAMPLE_L = (8, 8, 8, 8)
+
+
+# FP64 flops per launch unit of each kernel, counted from the kernel source
+# (FMA = 2 flops, transcendental library calls not counted): see flop_model().
+def flop_model(prec, theta_on=True):
+    mul, mul_acc, adj, axpy, cmul, cfma = 198, 216, 126, 36, 6, 8
+    # one plaquette of the drift: theta on -> 6 mul, 8 mul_acc, 5 adj, 2 axpy
+    plaq = (6 * mul + 8 * mul_acc + 5 * adj + 2 * axpy) if theta_on else (2 * mul + 3 * adj + 2 * axpy)
+    drift = 6 * plaq + mul + mul_acc + adj
+    n_taylor = 15
+    expm = mul + 6 + 72 + 36 + 7 + 2 * cfma * n_taylor + 9 * (cmul + cfma) + 6
+    upd_fp64 = 12 + 19 + 38 + 48 + expm + 64 + 36  # exponent, noise, exp, det, cube root
+    if prec == "fp64":
+        per_link = drift + upd_fp64 + mul + 9 * cmul
+    else:
+        per_link = upd_fp64  # the drift, E*U and the rescaling run in FP32
+    # cooling Omega (per site): H^2 ~33, det ~16, 2 Horner series, 2 assemblies
+    omega = 8 + 33 + 2 + 16 + 2 * 2 * 2 * 8 + 2 * 18 * 2
+    return {"update_per_link": per_link, "omega_per_site": omega}
+
+
+def fp64_peak_tflops(sm_max_mhz):
+    # 152 SMs x 2 FP64 FMA per SM per clock (4 flops) x clock: 1.259 TFLOP/s at 2070 MHz.
+    return 152 * 4 * sm_max_mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            return json.load(fh)
+    except Exception:
+        return {}
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    cs = os.path.join(ROOT, "paper_1311_1056_gb300", "csrc")
+    for f in sorted(os.listdir(cs)):
+        with open(os.path.join(cs, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def dram_traffic(kernel, prec):
+    """Per-launch DRAM bytes from a committed ncu summary, if taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        e = d[prec][kernel]
+        if e.get("source_hash") != kernel_source_hash():
+            return None
+        return e["bytes_per_launch"]
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def cpu_baseline(seconds=10.0, L=CPU_SAMPLE_L):
+    """The FP64 oracle on a bounded sample of the workload: an 8^4 lattice with
+    the same parameters, one site-update (CL step + 10 sweeps) per repetition."""
+    import oracle as O
+    w = WORKLOAD
+    U = O.hot_start(L, w["seed"])
+    cp = O.cool_params(w["eps"], w["alpha"], O.D2_MEANABS, forced_sweeps=w["sweeps"])
+    V = 1
+    for v in L:
+        V *= v
+    reps, t0, step = 0, time.perf_counter(), 0
+    while True:
+        U = O.cl_step(L, U, w["beta"], w["theta"], w["eps"], w["seed"], step)
+        U, _ = O.cool(L, U, cp)
+        reps += 1
+        step += 1
+        el = time.perf_counter() - t0
+        if el >= seconds:
+            break
+    return {"value": V * reps / el, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+            "sample": "%d^4 lattice (%d sites), %d site-update(s) of the same workload "
+                      "(1 CL step + %d sweeps), %.1f s" % (L[0], V, reps, w["sweeps"], el)}
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def run_form(cl, torch, prec_name, args, rank, stream):
+    w = WORKLOAD
+    prec = cl.CL_FP64 if prec_name == "fp64" else cl.CL_FP32_STORAGE
+    L = tuple(args.L) if args.L else w["L"]
+    V = L[0] * L[1] * L[2] * L[3]
+    lat = cl.Lattice(L, beta=w["beta"], theta=w["theta"], prec=prec, seed=w["seed"] + rank,
+                     start=cl.CL_START_HOT, stream=stream.cuda_stream)
+    cp = cl.make_cool(w["eps"], w["alpha"], cl.CL_D2_MEANABS, forced_sweeps=w["sweeps"])
+
+    def one_step():
+        cl.cl_step(lat.h, w["eps"], 1)
+        cl.cl_cool(lat.h, cp, want_report=False)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    cl.cl_set_timing(lat.h, 1)
+    n0 = lat.launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    if args.world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        one_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if args.world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1) / args.steps
+    launches = lat.launches() - n0
+    phases = cl.cl_get_timing(lat.h)
+    cl.cl_set_timing(lat.h, 0)
+    obs = lat.observables()
+    return lat, V, ms, launches, phases, obs, one_step
+
+
+def e2e_measure(cl, torch, lat, V, one_step, steps):
+    """Through the public API with host buffers: each step copies the links in
+    from pinned host memory, runs the step and reads the links back."""
+    import numpy as np
+    n = V * 4 * 18
+    hin = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    hout = torch.empty(n, dtype=torch.float64, pin_memory=True)
+    a_in = hin.numpy().view(np.complex128).reshape(V, 4, 3, 3)
+    a_out = hout.numpy().view(np.complex128).reshape(V, 4, 3, 3)
+    cl.cl_get_links(lat.h, V, a_in)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        cl.cl_set_links(lat.h, a_in)
+        one_step()
+        cl.cl_get_links(lat.h, V, a_out)
+    el = (time.perf_counter() - t0) / steps
+    return {"value": V / el, "unit": UNIT, "h2d_bytes_per_step": n * 8, "d2h_bytes_per_step": n * 8,
+            "ms_per_step": el * 1e3}
+
+
+def roofline_of(prec_name, V, phases, sm_max_mhz, theta_on=True):
+    fm = flop_model(prec_name, theta_on)
+    dom = max(phases, key=lambda k: phases[k][0])
+    ms_tot, n = phases[dom]
+    per = ms_tot / max(n, 1)
+    peak = fp64_peak_tflops(sm_max_mhz)
+    if dom == "update":
+        flops = fm["update_per_link"] * 4 * V
+    elif dom == "cool_omega":
+        flops = fm["omega_per_site"] * V
+    else:
+        flops = None
+    out = {"kernel": dom, "bound": "alu", "pipe": "fp64", "unit": "TFLOP/s", "peak": round(peak, 4),
+           "peak_source": "152 SMs x 2 FP64 FMA/clk x %d MHz (FP64 not in MEASURED_PEAKS.json)" % sm_max_mhz,
+           "avg_launch_ms": round(per, 4), "launches": n,
+           "traffic": dram_traffic(dom, prec_name)}
+    if flops is not None:
+        ach = flops / (per * 1e-3) / 1e12
+        out.update({"achieved": round(ach, 4), "frac": round(ach / peak, 4), "flops_per_launch": flops})
+    else:
+        out.update({"achieved": None, "frac": None})
+    return out
+
+
+def native(args):
+    import torch
+    from paper_1311_1056_gb300 import build, cl
+
+    ws, rank, local = dist_setup()
+    args.world = ws
+    if ws > 1:
+        torch.distributed.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    if rank == 0 or ws == 1:
+        build.build()
+    if ws > 1:
+        torch.distributed.barrier()
+    cl.load()
+    stream = torch.cuda.Stream()
+    peaks = measured_peaks()
+    sampler = ClockSampler(local)
+    sampler.start()
+    lat, V, ms, launches, phases, obs, one_step = run_form(cl, torch, "fp64", args, rank, stream)
+    clocks = sampler.stop()
+    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if ws > 1:
+        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    value = ws * V / (ms_max * 1e-3)
+    sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "lattice": list(args.L or WORKLOAD["L"]),
+                   "beta": WORKLOAD["beta"], "theta": WORKLOAD["theta"], "eps": WORKLOAD["eps"],
+                   "cooling": "D2 mean |f|, alpha 1, 10 sweeps per step (forced count)",
+                   "precision": "fp64 links and arithmetic",
+                   "l2": "no flush: the link fields (604 MB fp64 / 302 MB fp32) exceed the 129 MB L2",
+                   "parallelism": "replicas x%d (independent chains)" % ws},
+        "gpu_launches": launches,
+        "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phases.items()},
+        "roofline": roofline_of("fp64", V, phases, sm_max),
+        "hbm": {"alg_bytes_per_site_update": ALG_BYTES["fp64"],
+                "achieved_gbs": round(ALG_BYTES["fp64"] * value / ws / 1e9, 2),
+                "peak_gbs": peaks.get("hbm_gbs"),
+                "frac": round(ALG_BYTES["fp64"] * value / ws / 1e9 / peaks["hbm_gbs"], 5)
+                if peaks.get("hbm_gbs") else None},
+        "observables_after": {k: obs[k] for k in ("plaq_re", "un", "q_re", "q_im")},
+        "clocks": clocks,
+    }
+    result["e2e"] = e2e_measure(cl, torch, lat, V, one_step, max(2, min(args.steps, 5)))
+    if ws > 1:
+        t = torch.tensor([result["e2e"]["ms_per_step"]], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        result["e2e"]["value"] = ws * V / (float(t.item()) * 1e-3)
+    lat.close()
+    if not args.no_fp32:
+        lat32, V32, ms32, l32, ph32, obs32, _ = run_form(cl, torch, "fp32", args, rank, stream)
+        lat32.close()
+        result["forms"] = {"fp32_storage": {
+            "value": ws * V32 / (ms32 * 1e-3), "ms_per_step": ms32, "gpu_launches": l32,
+            "dtype": "f32 links + f64 exp/reprojection/reductions",
+            "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in ph32.items()},
+            "roofline": roofline_of("fp32", V32, ph32, sm_max),
+            "hbm_frac": round(ALG_BYTES["fp32"] * V32 / (ms32 * 1e-3) / 1e9 / peaks["hbm_gbs"], 5)
+            if peaks.get("hbm_gbs") else None,
+            "observables_after": {k: obs32[k] for k in ("plaq_re", "un", "q_re", "q_im")}}}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(result))
+
+
+def reference(args):
+    ws, rank, _ = dist_setup()
+    if rank != 0:
+        return
+    import oracle as O
+    w = WORKLOAD
+    L = CPU_SAMPLE_L
+    V = L[0] * L[1] * L[2] * L[3]
+    U = O.hot_start(L, w["seed"])
+    cp = O.cool_params(w["eps"], w["alpha"], O.D2_MEANABS, forced_sweeps=w["sweeps"])
+    times = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        U = O.cl_step(L, U, w["beta"], w["theta"], w["eps"], w["seed"], i)
+        U, _ = O.cool(L, U, cp)
+        if i >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = V / (ms * 1e-3)
+    sample = "%d^4 lattice (%d sites) per step, same parameters as the workload" % (L[0], V)
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "lattice": list(WORKLOAD["L"]), "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": O.num_threads(), "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["native", "reference"], default="native")
+    ap.add_argument("--L", type=int, nargs=4, default=None, help="override the lattice (testing)")
+    ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "native":
+        args.warmup = 3
+    if args.impl == "reference":
+        reference(args)
+    else:
+        native(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,200 @@
+/*
+ * cl.h -- C-ABI of the GB300 complex-Langevin + adaptive gauge-cooling library
+ * (libcl.so), following Bongiovanni, Aarts, Seiler, Sexty, Stamatescu,
+ * "Adaptive gauge cooling for complex Langevin dynamics", LATTICE 2013
+ * (arXiv:1311.1056).
+ *
+ * The method: SU(3) Yang-Mills with a theta-term, S = S_W - i theta sum_x q_L(x)
+ * (Sec. 5, eq. "eq:st"), evolved by complex Langevin on SL(3,C) links
+ * (Sec. 2), each step followed by gauge-cooling sweeps
+ * Omega_x = exp(-eps alpha f_ax lambda_a) that lower the unitarity norm
+ * (Sec. 2, eq. "eq:24"), with the adaptive strength alpha_ad = alpha / D
+ * (Sec. 4).
+ *
+ * Conventions shared by every call:
+ *  - Lattice: periodic, extents L[0..3] >= 1, V = L0 L1 L2 L3 sites,
+ *    site s = x0 + L0 (x1 + L1 (x2 + L2 x3)), direction mu = 0..3 along x_mu.
+ *  - Host link arrays ("AoS"): V*4*9 complex numbers as 2*V*4*9 doubles,
+ *    index ((s*4 + mu)*9 + 3*row + col)*2 + {0: re, 1: im}.
+ *  - Ownership: the library owns every device buffer it allocates; the
+ *    caller owns every host buffer and every device pointer it passes in.
+ *    Device pointers passed in must stay valid until the call's work on the
+ *    lattice's stream has completed.
+ *  - Streams: all device work of a lattice is enqueued on the CUDA stream
+ *    given to cl_init_lattice (NULL = legacy default stream).  Calls that
+ *    return host results (cl_observables, cl_get_*, cl_cool with a report,
+ *    cl_trajectory, cl_drift, cl_cool_gradient, cl_qdensity) synchronise
+ *    that stream; the others only enqueue.
+ *  - Errors: every call returns a cl_status and never aborts.  A CUDA error
+ *    gives CL_ERR_CUDA; its text is kept (per thread) for cl_last_error().
+ *    A lattice is not thread-safe: one host thread per lattice at a time.
+ *  - Precision (cl_precision): CL_FP64 keeps links and all arithmetic in
+ *    FP64.  CL_FP32_STORAGE stores and multiplies links in FP32 and keeps in
+ *    FP64 the matrix exponentials of the Langevin and cooling updates, the
+ *    det U = 1 re-projection and every global reduction.
+ *  - Noise: Philox4x32-10 keyed by (seed, step, site, mu), so results do not
+ *    depend on launch shape, and a run resumed from cl_get_links /
+ *    cl_get_step reproduces the uninterrupted one.
+ */
+#ifndef CL_GAUGECOOL_H
+#define CL_GAUGECOOL_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cl_lattice cl_lattice; /* opaque; owns its device memory */
+
+typedef enum {
+  CL_OK = 0,
+  CL_ERR_INVALID = 1,   /* bad argument (NULL pointer, size, mode) */
+  CL_ERR_OOM = 2,       /* device allocation failed */
+  CL_ERR_CUDA = 3,      /* a CUDA runtime error; see cl_last_error() */
+  CL_ERR_NONFINITE = 4, /* a NaN/Inf appeared in the links (CL runaway) */
+  CL_ERR_RUNAWAY = 5,   /* unitarity norm above the caller's bound */
+  CL_ERR_TIMEOUT = 6    /* a bounded device wait gave up */
+} cl_status;
+
+typedef enum { CL_FP64 = 0, CL_FP32_STORAGE = 1 } cl_precision;
+typedef enum { CL_START_COLD = 0, CL_START_HOT = 1 } cl_start;
+
+/* Choice of D in alpha_ad = alpha / D (Sec. 4): D_0 = 1; D_1 = (1/3)<Tr U U^+>
+ * (the normalised unitarity norm, >= 1); D_2 = <|f_ax|>_{a,x}; D_2 RMS =
+ * sqrt(<f_ax^2>_{a,x}). */
+typedef enum { CL_D0 = 0, CL_D1 = 1, CL_D2_MEANABS = 2, CL_D2_RMS = 3 } cl_adapt;
+
+typedef struct {
+  int L[4];             /* lattice extents, each >= 1 */
+  double beta;          /* Wilson coupling beta = 6/g^2 */
+  double theta_re;      /* theta_L, complex (real theta: complex action; */
+  double theta_im;      /*   imaginary theta: real action, Sec. 5) */
+  cl_precision prec;
+  uint64_t seed;        /* Philox key of every random number of this lattice */
+  cl_start start;       /* cold (U = 1) or Haar-random SU(3) (Philox stream 2) */
+  double gauge_sigma;   /* > 0: then U_{x,mu} <- Om_x U Om_{x+mu}^{-1} with
+                           Om_x = exp(i w_a lambda_a), w_a = i N(0, gauge_sigma^2)
+                           (Philox stream 1); 0: no transformation */
+} cl_params;
+
+typedef struct {
+  double eps;        /* epsilon in Omega_x = exp(-eps alpha_ad f_ax lambda_a) */
+  double alpha;      /* alpha_gf (alpha of alpha_ad = alpha / D) */
+  cl_adapt mode;     /* choice of D */
+  int n_min, n_max;  /* sweep-count bounds of the adaptive stop rule */
+  double tol_rel;    /* stop when UN_prev - UN < tol_rel (UN_prev - 1) */
+  double d_floor;    /* stop when UN - 1 < d_floor */
+  double d_guard;    /* no sweep when D < d_guard (gradient at rounding level) */
+  int forced_sweeps; /* >= 0: exactly this many sweeps (reproducible counts) */
+} cl_cool_params;
+
+/* Observables: plaquette (1/3)<Tr U_P> (complex), unitarity norm
+ * (1/3)<Tr U U^+> over links (Sec. 2; distance d = un - 1, Sec. 3),
+ * topological charge Q_L = sum_x q_L(x) (complex, Sec. 5), Wilson action
+ * S_W, full action S = S_W - i theta Q_L, and max |det U - 1|. */
+typedef struct {
+  double plaq_re, plaq_im, un, q_re, q_im, sw_re, sw_im, s_re, s_im, max_det_dev;
+} cl_obs;
+
+typedef struct {
+  int sweeps;             /* cooling sweeps applied */
+  double alpha_ad_last;   /* alpha_ad of the last applied sweep (0 if none) */
+  double un_before;       /* unitarity norm before the first sweep */
+  double un_after;        /* after the last sweep */
+} cl_cool_report;
+
+/* Create a lattice on the current CUDA device and initialise its links
+ * (start, then the optional random gauge transformation).  cuda_stream is a
+ * cudaStream_t (may be NULL).  On success *out owns the device memory
+ * (about V * (2 link fields + clover field + cooling scratch) bytes).
+ * Errors: CL_ERR_INVALID (NULL, extents < 1, V*6*9 beyond int range),
+ * CL_ERR_OOM, CL_ERR_CUDA. */
+cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice** out);
+
+/* n_steps complex Langevin steps, no cooling (Sec. 2; the update
+ * U' = exp(i lambda_a (eps K_a + sqrt(eps) eta_a)) U, K_a = -D_a S,
+ * <eta_a eta_b> = 2 delta_ab, all links at once, then U' <- U' det(U')^{-1/3}).
+ * The drift contains the Wilson staples and the clover theta-term (Sec. 5).
+ * Enqueue only.  Errors: CL_ERR_INVALID (eps < 0, n_steps < 0), CL_ERR_CUDA. */
+cl_status cl_step(cl_lattice* lat, double eps, int n_steps);
+
+/* Gauge cooling with the adaptive rule (Sec. 2 eq. "eq:24", Sec. 4).  The
+ * rule runs on the device; report may be NULL (then nothing is
+ * synchronised).  With a report: CL_ERR_NONFINITE if the links hold a
+ * NaN/Inf.  Errors: CL_ERR_INVALID (bad mode/bounds), CL_ERR_CUDA. */
+cl_status cl_cool(cl_lattice* lat, const cl_cool_params* cp, cl_cool_report* report);
+
+/* Observables of the current links (synchronises).  CL_ERR_NONFINITE when a
+ * link holds a NaN/Inf (*out is still written). */
+cl_status cl_observables(cl_lattice* lat, cl_obs* out);
+
+/* The fused hot path: n_steps times [one CL step, cooling with cp (may be
+ * NULL: no cooling)]; after every obs_every-th step (obs_every > 0) the
+ * observables go to obs_out[k] and the cooling report to rep_out[k] (either
+ * may be NULL), k = 0 .. n_steps/obs_every - 1.  Records are kept on the
+ * device and copied once at the end (synchronises when obs_every > 0).
+ * runaway_un > 0: CL_ERR_RUNAWAY if a recorded unitarity norm exceeds it. */
+cl_status cl_trajectory(cl_lattice* lat, double eps, int n_steps, const cl_cool_params* cp,
+                        int obs_every, cl_obs* obs_out, cl_cool_report* rep_out,
+                        double runaway_un);
+
+/* Links as host AoS doubles (layout above), any precision (FP32 links are
+ * widened).  host_aos holds V*4*18 doubles; pinned memory copies fastest.
+ * Synchronises.  Errors: CL_ERR_INVALID (NULL), CL_ERR_OOM (staging), CL_ERR_CUDA. */
+cl_status cl_get_links(cl_lattice* lat, double* host_aos);
+/* Replace the links from host AoS doubles (FP32 storage rounds them).
+ * Enqueue only, but host_aos may be reused on return (the copy completes first). */
+cl_status cl_set_links(cl_lattice* lat, const double* host_aos);
+/* The same with a caller-owned device AoS buffer (e.g. a torch tensor). */
+cl_status cl_get_links_device(cl_lattice* lat, double* dev_aos);
+cl_status cl_set_links_device(cl_lattice* lat, const double* dev_aos);
+
+/* Philox step counter (number of CL steps taken; keys the noise). */
+cl_status cl_get_step(const cl_lattice* lat, uint64_t* step);
+cl_status cl_set_step(cl_lattice* lat, uint64_t step);
+
+/* Drift matrix X_S of every link, D_a S = i Tr(lambda_a X_S) (Sec. 5 action),
+ * as host AoS doubles (V*4*18).  Synchronises. */
+cl_status cl_drift(cl_lattice* lat, double* host_aos);
+/* Cooling gradient f_ax = 2 Tr[lambda_a sum_mu (U U^+ - U^+_{x-mu} U_{x-mu})]
+ * (Sec. 2, eq. "eq:24"), host doubles, layout [a][site] (8*V).  Synchronises. */
+cl_status cl_cool_gradient(cl_lattice* lat, double* host_f);
+/* Topological charge density q_L(x) (Sec. 5), host doubles [site]{re,im} (2*V). */
+cl_status cl_qdensity(cl_lattice* lat, double* host_q);
+
+/* Optional per-phase timing: with timing on, every kernel launch of the
+ * lattice is bracketed by two CUDA events on the lattice's stream and its
+ * duration is added to its phase.  cl_set_timing clears the totals (and
+ * waits for pending events); cl_get_timing synchronises the stream and
+ * returns, per phase, the summed milliseconds and the number of launches
+ * (arrays of CL_NPHASE entries, either may be NULL).  Timing adds two event
+ * records per launch and is off by default. */
+enum {
+  CL_PHASE_CLOVER = 0,     /* clover field of the theta drift */
+  CL_PHASE_UPDATE = 1,     /* drift + noise + exponential update */
+  CL_PHASE_COOL_GRAD = 2,  /* cooling gradient f_ax + partial sums */
+  CL_PHASE_COOL_RULE = 3,  /* adaptive rule (one block) */
+  CL_PHASE_COOL_OMEGA = 4, /* Omega_x, Omega_x^{-1} */
+  CL_PHASE_COOL_APPLY = 5, /* U <- Omega U Omega^{-1} */
+  CL_PHASE_OBS = 6,        /* observables */
+  CL_NPHASE = 7
+};
+cl_status cl_set_timing(cl_lattice* lat, int on);
+cl_status cl_get_timing(cl_lattice* lat, double* ms, int64_t* launches);
+
+/* Number of kernels this lattice has launched so far. */
+cl_status cl_launch_count(const cl_lattice* lat, int64_t* count);
+/* Wait for the lattice's stream. */
+cl_status cl_synchronize(cl_lattice* lat);
+/* Release every device buffer of the lattice (NULL is ignored). */
+void cl_free(cl_lattice* lat);
+
+const char* cl_status_str(cl_status s);
+/* Text of the last error on this host thread ("" if none). */
+const char* cl_last_error(void);
+int cl_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,330 @@
+"""ctypes binding of libcl.so (include/cl.h), same names as the C functions.
+
+Argument marshalling only: every step of the computation runs in the CUDA
+kernels of the library.  Importing works without a GPU; calling into the
+library needs libcl.so (built by paper_1311_1056_gb300/build.py) and raises
+if it is missing -- there is no CPU fallback.
+
+Host link arrays are numpy complex128 of shape (V, 4, 3, 3) (the AoS layout
+of cl.h); `cl_get_links_device` / `cl_set_links_device` take device pointers
+(e.g. torch.Tensor.data_ptr() of a float64 CUDA tensor of 2*V*4*9 elements).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libcl.so")
+
+CL_OK, CL_ERR_INVALID, CL_ERR_OOM, CL_ERR_CUDA, CL_ERR_NONFINITE, CL_ERR_RUNAWAY, CL_ERR_TIMEOUT = range(7)
+CL_FP64, CL_FP32_STORAGE = 0, 1
+CL_START_COLD, CL_START_HOT = 0, 1
+CL_D0, CL_D1, CL_D2_MEANABS, CL_D2_RMS = 0, 1, 2, 3
+
+
+class cl_params(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("beta", ctypes.c_double),
+                ("theta_re", ctypes.c_double), ("theta_im", ctypes.c_double),
+                ("prec", ctypes.c_int), ("seed", ctypes.c_uint64), ("start", ctypes.c_int),
+                ("gauge_sigma", ctypes.c_double)]
+
+
+class cl_cool_params(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("alpha", ctypes.c_double), ("mode", ctypes.c_int),
+                ("n_min", ctypes.c_int), ("n_max", ctypes.c_int), ("tol_rel", ctypes.c_double),
+                ("d_floor", ctypes.c_double), ("d_guard", ctypes.c_double),
+                ("forced_sweeps", ctypes.c_int)]
+
+
+class cl_obs(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_double) for n in ("plaq_re", "plaq_im", "un", "q_re", "q_im", "sw_re",
+                                               "sw_im", "s_re", "s_im", "max_det_dev")]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class cl_cool_report(ctypes.Structure):
+    _fields_ = [("sweeps", ctypes.c_int), ("alpha_ad_last", ctypes.c_double),
+                ("un_before", ctypes.c_double), ("un_after", ctypes.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class CLError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__("%s: %s (%s)" % (where, _status_str(status), _last_error()))
+
+
+_lib = None
+_P = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+
+SIGNATURES = {
+    "cl_init_lattice": (ctypes.c_int, [ctypes.POINTER(cl_params), _P, ctypes.POINTER(_P)]),
+    "cl_step": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int]),
+    "cl_cool": (ctypes.c_int, [_P, ctypes.POINTER(cl_cool_params), ctypes.POINTER(cl_cool_report)]),
+    "cl_observables": (ctypes.c_int, [_P, ctypes.POINTER(cl_obs)]),
+    "cl_trajectory": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_int,
+                                     ctypes.POINTER(cl_cool_params), ctypes.c_int,
+                                     ctypes.POINTER(cl_obs), ctypes.POINTER(cl_cool_report),
+                                     ctypes.c_double]),
+    "cl_get_links": (ctypes.c_int, [_P, _dp]),
+    "cl_set_links": (ctypes.c_int, [_P, _dp]),
+    "cl_get_links_device": (ctypes.c_int, [_P, _P]),
+    "cl_set_links_device": (ctypes.c_int, [_P, _P]),
+    "cl_get_step": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "cl_set_step": (ctypes.c_int, [_P, ctypes.c_uint64]),
+    "cl_drift": (ctypes.c_int, [_P, _dp]),
+    "cl_cool_gradient": (ctypes.c_int, [_P, _dp]),
+    "cl_qdensity": (ctypes.c_int, [_P, _dp]),
+    "cl_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
+    "cl_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cl_get_timing": (ctypes.c_int, [_P, _dp, ctypes.POINTER(ctypes.c_int64)]),
+    "cl_synchronize": (ctypes.c_int, [_P]),
+    "cl_free": (None, [_P]),
+    "cl_status_str": (ctypes.c_char_p, [ctypes.c_int]),
+    "cl_last_error": (ctypes.c_char_p, []),
+    "cl_version": (ctypes.c_int, []),
+}
+
+
+def load(path=LIB_PATH):
+    """Load libcl.so; raises if it has not been built (no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError("libcl.so not found at %s: run paper_1311_1056_gb300/build.py "
+                               "(or __graft_entry__.build()) first" % path)
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _status_str(s):
+    return load().cl_status_str(s).decode()
+
+
+def _last_error():
+    return load().cl_last_error().decode()
+
+
+def _check(s, where):
+    if s != CL_OK:
+        raise CLError(s, where)
+
+
+def _f64(a, n):
+    a = np.ascontiguousarray(a, dtype=np.complex128)
+    assert a.size * 2 == n, (a.shape, n)
+    return a
+
+
+# ----------------------------------------------------------------- C names
+def cl_init_lattice(params, stream=0):
+    h = _P()
+    _check(load().cl_init_lattice(ctypes.byref(params), _P(stream or None), ctypes.byref(h)),
+           "cl_init_lattice")
+    return h
+
+
+def cl_step(lat, eps, n_steps):
+    _check(load().cl_step(lat, eps, n_steps), "cl_step")
+
+
+def cl_cool(lat, cp, want_report=True):
+    rep = cl_cool_report()
+    _check(load().cl_cool(lat, ctypes.byref(cp), ctypes.byref(rep) if want_report else None), "cl_cool")
+    return rep.as_dict() if want_report else None
+
+
+def cl_observables(lat, check=True):
+    o = cl_obs()
+    s = load().cl_observables(lat, ctypes.byref(o))
+    if check:
+        _check(s, "cl_observables")
+    return o.as_dict()
+
+
+def cl_trajectory(lat, eps, n_steps, cp=None, obs_every=0, runaway_un=0.0):
+    nrec = n_steps // obs_every if obs_every > 0 else 0
+    obs = (cl_obs * max(nrec, 1))()
+    rep = (cl_cool_report * max(nrec, 1))()
+    _check(load().cl_trajectory(lat, eps, n_steps, ctypes.byref(cp) if cp is not None else None,
+                                obs_every, obs, rep, runaway_un), "cl_trajectory")
+    return [obs[k].as_dict() for k in range(nrec)], [rep[k].as_dict() for k in range(nrec)]
+
+
+def cl_get_links(lat, V, out=None):
+    if out is None:
+        out = np.empty((V, 4, 3, 3), np.complex128)
+    _check(load().cl_get_links(lat, out.ctypes.data_as(_dp)), "cl_get_links")
+    return out
+
+
+def cl_set_links(lat, U):
+    U = _f64(U, 2 * U.size)
+    _check(load().cl_set_links(lat, U.ctypes.data_as(_dp)), "cl_set_links")
+
+
+def cl_get_links_device(lat, dev_ptr):
+    _check(load().cl_get_links_device(lat, _P(dev_ptr)), "cl_get_links_device")
+
+
+def cl_set_links_device(lat, dev_ptr):
+    _check(load().cl_set_links_device(lat, _P(dev_ptr)), "cl_set_links_device")
+
+
+def cl_get_step(lat):
+    v = ctypes.c_uint64()
+    _check(load().cl_get_step(lat, ctypes.byref(v)), "cl_get_step")
+    return v.value
+
+
+def cl_set_step(lat, step):
+    _check(load().cl_set_step(lat, step), "cl_set_step")
+
+
+def cl_drift(lat, V):
+    out = np.empty((V, 4, 3, 3), np.complex128)
+    _check(load().cl_drift(lat, out.ctypes.data_as(_dp)), "cl_drift")
+    return out
+
+
+def cl_cool_gradient(lat, V):
+    out = np.empty((8, V))
+    _check(load().cl_cool_gradient(lat, out.ctypes.data_as(_dp)), "cl_cool_gradient")
+    return out.T.copy()  # (V, 8), like the oracle
+
+
+def cl_qdensity(lat, V):
+    out = np.empty(2 * V)
+    _check(load().cl_qdensity(lat, out.ctypes.data_as(_dp)), "cl_qdensity")
+    return out[0::2] + 1j * out[1::2]
+
+
+def cl_launch_count(lat):
+    v = ctypes.c_int64()
+    _check(load().cl_launch_count(lat, ctypes.byref(v)), "cl_launch_count")
+    return v.value
+
+
+PHASES = ("clover", "update", "cool_grad", "cool_rule", "cool_omega", "cool_apply", "obs")
+
+
+def cl_set_timing(lat, on):
+    _check(load().cl_set_timing(lat, 1 if on else 0), "cl_set_timing")
+
+
+def cl_get_timing(lat):
+    ms = (ctypes.c_double * len(PHASES))()
+    n = (ctypes.c_int64 * len(PHASES))()
+    _check(load().cl_get_timing(lat, ms, n), "cl_get_timing")
+    return {p: (ms[i], n[i]) for i, p in enumerate(PHASES)}
+
+
+def cl_synchronize(lat):
+    _check(load().cl_synchronize(lat), "cl_synchronize")
+
+
+def cl_free(lat):
+    if lat:
+        load().cl_free(lat)
+
+
+def cl_status_str(s):
+    return _status_str(s)
+
+
+def cl_last_error():
+    return _last_error()
+
+
+def cl_version():
+    return load().cl_version()
+
+
+# ----------------------------------------------------------- convenience
+def make_params(L, beta=6.0, theta=0.0, prec=CL_FP64, seed=1, start=CL_START_COLD, gauge_sigma=0.0):
+    theta = complex(theta)
+    p = cl_params()
+    for mu in range(4):
+        p.L[mu] = int(L[mu])
+    p.beta = beta
+    p.theta_re, p.theta_im = theta.real, theta.imag
+    p.prec, p.seed, p.start, p.gauge_sigma = prec, seed, start, gauge_sigma
+    return p
+
+
+def make_cool(eps, alpha=1.0, mode=CL_D0, n_min=0, n_max=0, tol_rel=1e-3, d_floor=0.0,
+              d_guard=1e-12, forced_sweeps=-1):
+    return cl_cool_params(eps, alpha, mode, n_min, n_max, tol_rel, d_floor, d_guard, forced_sweeps)
+
+
+class Lattice:
+    """Owning wrapper: frees the device lattice when closed or collected."""
+
+    def __init__(self, L, beta=6.0, theta=0.0, prec=CL_FP64, seed=1, start=CL_START_COLD,
+                 gauge_sigma=0.0, stream=0):
+        self.L = tuple(int(v) for v in L)
+        self.V = int(np.prod(self.L))
+        self.params = make_params(L, beta, theta, prec, seed, start, gauge_sigma)
+        self.h = cl_init_lattice(self.params, stream)
+
+    def step(self, eps, n=1):
+        cl_step(self.h, eps, n)
+
+    def cool(self, cp, want_report=True):
+        return cl_cool(self.h, cp, want_report)
+
+    def observables(self):
+        return cl_observables(self.h)
+
+    def trajectory(self, eps, n_steps, cp=None, obs_every=0, runaway_un=0.0):
+        return cl_trajectory(self.h, eps, n_steps, cp, obs_every, runaway_un)
+
+    def links(self):
+        return cl_get_links(self.h, self.V)
+
+    def set_links(self, U):
+        cl_set_links(self.h, U)
+
+    def drift(self):
+        return cl_drift(self.h, self.V)
+
+    def cool_gradient(self):
+        return cl_cool_gradient(self.h, self.V)
+
+    def qdensity(self):
+        return cl_qdensity(self.h, self.V)
+
+    @property
+    def step_count(self):
+        return cl_get_step(self.h)
+
+    def launches(self):
+        return cl_launch_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cl_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,537 @@
+// capi.cu -- the C-ABI runtime of libcl.so (include/cl.h): lattice state in
+// HBM, the CL step / cooling / observables orchestration and host <-> device
+// link exchange.  All arithmetic runs in the kernels (kernels.cu,
+// k_update_*.cu); this file only allocates, sequences launches and copies.
+#include <climits>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cl.h"
+#include "launch.h"
+
+using namespace clgc;
+
+namespace {
+
+thread_local std::string g_err;
+
+const double KAPPA_Q = -1.0 / (256.0 * 9.86960440108935861883);  // q_L = kappa [Tr F F ...]
+
+cl_status fail(cl_status s, const std::string& msg) {
+  g_err = msg;
+  return s;
+}
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(e_ == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA,      \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));             \
+  } while (0)
+
+}  // namespace
+
+struct cl_lattice {
+  cl_params p;
+  GeoH g;
+  int prec;
+  size_t esz;  // bytes of one complex element (16 or 8)
+  cudaStream_t st;
+  void* U;     // links, SoA [4][9][V]
+  void* Un;    // second link buffer (CL update target)
+  void* F;     // clover field, SoA [6][9][V]
+  void* f;     // cooling gradient [8][V] (real)
+  void* Om;    // packed Hermitian Omega [9][V]
+  void* Omi;   // and its inverse
+  double* partials;
+  CoolState* cs;
+  ObsOut* obs;
+  double* stage;  // AoS double staging, V*4*18 (allocated on first use)
+  double* qsite;  // per-site q_L (on first use)
+  uint64_t step;
+  int64_t launches;
+  // optional per-phase CUDA-event timing (cl_set_timing)
+  int timing;
+  std::vector<cudaEvent_t>* ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>* ev_pending;
+  double phase_ms[CL_NPHASE];
+  int64_t phase_n[CL_NPHASE];
+};
+
+namespace {
+
+size_t real_size(const cl_lattice* l) { return l->prec == 0 ? 8 : 4; }
+
+cudaEvent_t take_event(cl_lattice* l) {
+  if (!l->ev_pool->empty()) {
+    cudaEvent_t e = l->ev_pool->back();
+    l->ev_pool->pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Launch through f(); with timing on, bracket it by two events on the
+// lattice's stream and remember them under `phase`.
+template <typename Fn>
+cudaError_t timed(cl_lattice* l, int phase, Fn f) {
+  l->launches++;
+  if (!l->timing) return f();
+  cudaEvent_t a = take_event(l), b = take_event(l);
+  if (!a || !b) return cudaErrorMemoryAllocation;
+  cudaEventRecord(a, l->st);
+  cudaError_t e = f();
+  cudaEventRecord(b, l->st);
+  l->ev_pending->push_back({phase, {a, b}});
+  return e;
+}
+
+cudaError_t resolve_timing(cl_lattice* l) {
+  if (l->ev_pending->empty()) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(l->st);
+  if (e != cudaSuccess) return e;
+  for (auto& p : *l->ev_pending) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, p.second.first, p.second.second);
+    if (e != cudaSuccess) return e;
+    l->phase_ms[p.first] += ms;
+    l->phase_n[p.first] += 1;
+    l->ev_pool->push_back(p.second.first);
+    l->ev_pool->push_back(p.second.second);
+  }
+  l->ev_pending->clear();
+  return cudaSuccess;
+}
+
+cl_status ensure_stage(cl_lattice* l) {
+  if (l->stage) return CL_OK;
+  CK(cudaMalloc(&l->stage, sizeof(double) * 18 * 4 * (size_t)l->g.V));
+  return CL_OK;
+}
+
+bool theta_nonzero(const cl_lattice* l) { return l->p.theta_re != 0.0 || l->p.theta_im != 0.0; }
+
+cl_status do_steps(cl_lattice* l, double eps, int n) {
+  const bool th = theta_nonzero(l);
+  // F^ = -i theta kappa F: -i (a + ib) kappa = kappa b - i kappa a
+  const double sre = KAPPA_Q * l->p.theta_im, sim = -KAPPA_Q * l->p.theta_re;
+  for (int i = 0; i < n; ++i) {
+    if (th) CK(timed(l, CL_PHASE_CLOVER, [&] { return launch_clover(l->prec, l->g, l->U, l->F, sre, sim, l->st); }));
+    CK(timed(l, CL_PHASE_UPDATE, [&] {
+      return launch_cl_update(l->prec, th, 0, l->g, l->U, l->F, l->Un, l->p.beta, eps, l->p.seed,
+                              (uint32_t)l->step, l->st);
+    }));
+    std::swap(l->U, l->Un);
+    l->step++;
+  }
+  return CL_OK;
+}
+
+CoolArgs cool_args(const cl_cool_params* cp) {
+  CoolArgs a;
+  a.eps = cp->eps;
+  a.alpha = cp->alpha;
+  a.tol_rel = cp->tol_rel;
+  a.d_floor = cp->d_floor;
+  a.d_guard = cp->d_guard;
+  a.mode = (int)cp->mode;
+  a.n_min = cp->n_min;
+  a.n_max = cp->n_max;
+  a.forced_sweeps = cp->forced_sweeps;
+  return a;
+}
+
+cl_status check_cool(const cl_cool_params* cp) {
+  if (!cp) return fail(CL_ERR_INVALID, "NULL cooling parameters");
+  if ((int)cp->mode < 0 || (int)cp->mode > 3) return fail(CL_ERR_INVALID, "bad cooling mode");
+  if (cp->forced_sweeps < 0 && (cp->n_max < 0 || cp->n_min < 0 || cp->n_min > cp->n_max))
+    return fail(CL_ERR_INVALID, "bad sweep bounds");
+  if (!(cp->eps >= 0.0) || !(cp->alpha >= 0.0)) return fail(CL_ERR_INVALID, "bad eps/alpha");
+  return CL_OK;
+}
+
+// Enqueue the whole cooling loop; the device rule decides how many sweeps
+// actually run (later launches return at once once it says done).
+cl_status do_cool(cl_lattice* l, const cl_cool_params* cp) {
+  CoolArgs a = cool_args(cp);
+  const int n_iter = cp->forced_sweeps >= 0 ? cp->forced_sweeps : cp->n_max;
+  for (int k = 0; k <= n_iter; ++k) {
+    // the first gradient of a call always runs: the done flag still holds
+    // the previous call's decision until the rule resets it (first = 1)
+    CK(timed(l, CL_PHASE_COOL_GRAD, [&] {
+      return launch_cool_grad(l->prec, l->g, l->U, l->f, l->partials, k == 0 ? nullptr : l->cs, l->st);
+    }));
+    CK(timed(l, CL_PHASE_COOL_RULE, [&] { return launch_cool_adapt(l->g, l->partials, a, l->cs, k == 0, l->st); }));
+    if (k == n_iter) break;
+    CK(timed(l, CL_PHASE_COOL_OMEGA, [&] {
+      return launch_cool_omega(l->prec, l->g, l->f, l->Om, l->Omi, cp->eps, l->cs, l->st);
+    }));
+    CK(timed(l, CL_PHASE_COOL_APPLY, [&] { return launch_cool_apply(l->prec, l->g, l->U, l->Om, l->Omi, l->cs, l->st); }));
+  }
+  return CL_OK;
+}
+
+cl_status do_obs(cl_lattice* l, ObsOut* dst, double* q_site) {
+  CK(timed(l, CL_PHASE_OBS, [&] { return launch_clover(l->prec, l->g, l->U, l->F, 1.0, 0.0, l->st); }));
+  CK(timed(l, CL_PHASE_OBS, [&] { return launch_obs(l->prec, l->g, l->U, l->F, 1, l->partials, q_site, l->st); }));
+  CK(timed(l, CL_PHASE_OBS, [&] {
+    return launch_obs_final(l->g, l->partials, l->p.beta, l->p.theta_re, l->p.theta_im, dst, l->st);
+  }));
+  return CL_OK;
+}
+
+void to_cl_obs(const ObsOut& o, cl_obs* out) {
+  out->plaq_re = o.plaq_re;
+  out->plaq_im = o.plaq_im;
+  out->un = o.un;
+  out->q_re = o.q_re;
+  out->q_im = o.q_im;
+  out->sw_re = o.sw_re;
+  out->sw_im = o.sw_im;
+  out->s_re = o.s_re;
+  out->s_im = o.s_im;
+  out->max_det_dev = o.max_det_dev;
+}
+
+void to_report(const CoolState& c, cl_cool_report* r) {
+  r->sweeps = c.sweeps;
+  r->alpha_ad_last = c.alpha_ad_last;
+  r->un_before = c.un_before;
+  r->un_after = c.un_after;
+}
+
+}  // namespace
+
+extern "C" {
+
+cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice** out) {
+  if (!params || !out) return fail(CL_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  long long V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (params->L[mu] < 1) return fail(CL_ERR_INVALID, "lattice extent < 1");
+    V *= params->L[mu];
+    if (V * 6 * 9 > INT_MAX) return fail(CL_ERR_INVALID, "lattice too large");
+  }
+  if (params->prec != CL_FP64 && params->prec != CL_FP32_STORAGE)
+    return fail(CL_ERR_INVALID, "bad precision");
+  if (params->start != CL_START_COLD && params->start != CL_START_HOT)
+    return fail(CL_ERR_INVALID, "bad start");
+  cl_lattice* l = new cl_lattice();
+  std::memset(l, 0, sizeof(*l));
+  l->p = *params;
+  for (int mu = 0; mu < 4; ++mu) l->g.L[mu] = params->L[mu];
+  l->g.V = (int)V;
+  l->prec = params->prec == CL_FP64 ? 0 : 1;
+  l->esz = l->prec == 0 ? 16 : 8;
+  l->st = (cudaStream_t)cuda_stream;
+  l->ev_pool = new std::vector<cudaEvent_t>();
+  l->ev_pending = new std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>();
+  cl_status s = CL_OK;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (s != CL_OK) return;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess)
+      s = fail(e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA,
+               std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  };
+  const size_t Vs = (size_t)V;
+  alloc(&l->U, l->esz * 4 * 9 * Vs);
+  alloc(&l->Un, l->esz * 4 * 9 * Vs);
+  alloc(&l->F, l->esz * 6 * 9 * Vs);
+  alloc(&l->f, real_size(l) * 8 * Vs);
+  alloc(&l->Om, real_size(l) * 9 * Vs);
+  alloc(&l->Omi, real_size(l) * 9 * Vs);
+  alloc((void**)&l->partials, sizeof(double) * NQ_OBS * (size_t)reduce_blocks(l->g.V));
+  alloc((void**)&l->cs, sizeof(CoolState));
+  alloc((void**)&l->obs, sizeof(ObsOut));
+  if (s != CL_OK) {
+    cl_free(l);
+    return s;
+  }
+  cudaError_t e = cudaMemsetAsync(l->cs, 0, sizeof(CoolState), l->st);
+  if (e == cudaSuccess)
+    e = params->start == CL_START_HOT ? launch_hot(l->prec, l->g, l->U, params->seed, l->st)
+                                      : launch_cold(l->prec, l->g, l->U, l->st);
+  l->launches++;
+  if (e == cudaSuccess && params->gauge_sigma > 0.0) {
+    e = launch_gauge_omega(l->prec, l->g, l->Om, l->Omi, params->seed, params->gauge_sigma, l->st);
+    if (e == cudaSuccess) e = launch_cool_apply(l->prec, l->g, l->U, l->Om, l->Omi, nullptr, l->st);
+    l->launches += 2;
+  }
+  if (e != cudaSuccess) {
+    cl_free(l);
+    return fail(CL_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e));
+  }
+  *out = l;
+  return CL_OK;
+}
+
+cl_status cl_step(cl_lattice* l, double eps, int n_steps) {
+  if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  if (!(eps >= 0.0) || n_steps < 0) return fail(CL_ERR_INVALID, "bad eps or n_steps");
+  return do_steps(l, eps, n_steps);
+}
+
+cl_status cl_cool(cl_lattice* l, const cl_cool_params* cp, cl_cool_report* report) {
+  if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  cl_status s = check_cool(cp);
+  if (s != CL_OK) return s;
+  s = do_cool(l, cp);
+  if (s != CL_OK || !report) return s;
+  CoolState c;
+  CK(cudaMemcpyAsync(&c, l->cs, sizeof(c), cudaMemcpyDeviceToHost, l->st));
+  CK(cudaStreamSynchronize(l->st));
+  to_report(c, report);
+  if (c.nonfinite) return fail(CL_ERR_NONFINITE, "non-finite links during cooling");
+  return CL_OK;
+}
+
+cl_status cl_observables(cl_lattice* l, cl_obs* out) {
+  if (!l || !out) return fail(CL_ERR_INVALID, "NULL argument");
+  cl_status s = do_obs(l, l->obs, nullptr);
+  if (s != CL_OK) return s;
+  ObsOut o;
+  CK(cudaMemcpyAsync(&o, l->obs, sizeof(o), cudaMemcpyDeviceToHost, l->st));
+  CK(cudaStreamSynchronize(l->st));
+  to_cl_obs(o, out);
+  if (o.nonfinite != 0.0) return fail(CL_ERR_NONFINITE, "non-finite links");
+  return CL_OK;
+}
+
+cl_status cl_trajectory(cl_lattice* l, double eps, int n_steps, const cl_cool_params* cp,
+                        int obs_every, cl_obs* obs_out, cl_cool_report* rep_out,
+                        double runaway_un) {
+  if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  if (!(eps >= 0.0) || n_steps < 0) return fail(CL_ERR_INVALID, "bad eps or n_steps");
+  if (cp) {
+    cl_status s = check_cool(cp);
+    if (s != CL_OK) return s;
+  }
+  const int nrec = obs_every > 0 ? n_steps / obs_every : 0;
+  ObsOut* dobs = nullptr;
+  CoolState* dcs = nullptr;
+  if (nrec > 0) {
+    CK(cudaMalloc(&dobs, sizeof(ObsOut) * nrec));
+    cudaError_t e = cudaMalloc(&dcs, sizeof(CoolState) * nrec);
+    if (e != cudaSuccess) {
+      cudaFree(dobs);
+      return fail(CL_ERR_OOM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
+  cl_status s = CL_OK;
+  int rec = 0;
+  for (int i = 0; i < n_steps && s == CL_OK; ++i) {
+    s = do_steps(l, eps, 1);
+    if (s == CL_OK && cp) s = do_cool(l, cp);
+    if (s == CL_OK && nrec > 0 && (i + 1) % obs_every == 0) {
+      s = do_obs(l, dobs + rec, nullptr);
+      if (s == CL_OK && cp) {
+        cudaError_t e = cudaMemcpyAsync(dcs + rec, l->cs, sizeof(CoolState), cudaMemcpyDeviceToDevice, l->st);
+        if (e != cudaSuccess) s = fail(CL_ERR_CUDA, cudaGetErrorString(e));
+      }
+      ++rec;
+    }
+  }
+  if (s == CL_OK && nrec > 0) {
+    std::vector<ObsOut> ho(nrec);
+    std::vector<CoolState> hc(nrec);
+    cudaError_t e = cudaMemcpyAsync(ho.data(), dobs, sizeof(ObsOut) * nrec, cudaMemcpyDeviceToHost, l->st);
+    if (e == cudaSuccess && cp)
+      e = cudaMemcpyAsync(hc.data(), dcs, sizeof(CoolState) * nrec, cudaMemcpyDeviceToHost, l->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(l->st);
+    if (e != cudaSuccess) {
+      s = fail(CL_ERR_CUDA, cudaGetErrorString(e));
+    } else {
+      for (int k = 0; k < nrec; ++k) {
+        if (obs_out) to_cl_obs(ho[k], obs_out + k);
+        if (rep_out) {
+          if (cp) to_report(hc[k], rep_out + k);
+          else std::memset(rep_out + k, 0, sizeof(cl_cool_report));
+        }
+        if (ho[k].nonfinite != 0.0 && s == CL_OK) s = fail(CL_ERR_NONFINITE, "non-finite links");
+        if (runaway_un > 0.0 && ho[k].un > runaway_un && s == CL_OK)
+          s = fail(CL_ERR_RUNAWAY, "unitarity norm above the runaway bound");
+      }
+    }
+  }
+  if (dobs) cudaFree(dobs);
+  if (dcs) cudaFree(dcs);
+  return s;
+}
+
+cl_status cl_get_links_device(cl_lattice* l, double* dev_aos) {
+  if (!l || !dev_aos) return fail(CL_ERR_INVALID, "NULL argument");
+  CK(launch_soa_to_aos(l->prec, l->g, l->U, dev_aos, 4, l->st));
+  l->launches++;
+  return CL_OK;
+}
+
+cl_status cl_set_links_device(cl_lattice* l, const double* dev_aos) {
+  if (!l || !dev_aos) return fail(CL_ERR_INVALID, "NULL argument");
+  CK(launch_aos_to_soa(l->prec, l->g, dev_aos, l->U, 4, l->st));
+  l->launches++;
+  return CL_OK;
+}
+
+cl_status cl_get_links(cl_lattice* l, double* host_aos) {
+  if (!l || !host_aos) return fail(CL_ERR_INVALID, "NULL argument");
+  cl_status s = ensure_stage(l);
+  if (s != CL_OK) return s;
+  s = cl_get_links_device(l, l->stage);
+  if (s != CL_OK) return s;
+  CK(cudaMemcpyAsync(host_aos, l->stage, sizeof(double) * 18 * 4 * (size_t)l->g.V,
+                     cudaMemcpyDeviceToHost, l->st));
+  CK(cudaStreamSynchronize(l->st));
+  return CL_OK;
+}
+
+cl_status cl_set_links(cl_lattice* l, const double* host_aos) {
+  if (!l || !host_aos) return fail(CL_ERR_INVALID, "NULL argument");
+  cl_status s = ensure_stage(l);
+  if (s != CL_OK) return s;
+  CK(cudaMemcpyAsync(l->stage, host_aos, sizeof(double) * 18 * 4 * (size_t)l->g.V,
+                     cudaMemcpyHostToDevice, l->st));
+  s = cl_set_links_device(l, l->stage);
+  if (s != CL_OK) return s;
+  // the host buffer may be reused on return: wait for the copy only
+  CK(cudaStreamSynchronize(l->st));
+  return CL_OK;
+}
+
+cl_status cl_get_step(const cl_lattice* l, uint64_t* step) {
+  if (!l || !step) return fail(CL_ERR_INVALID, "NULL argument");
+  *step = l->step;
+  return CL_OK;
+}
+
+cl_status cl_set_step(cl_lattice* l, uint64_t step) {
+  if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  l->step = step;
+  return CL_OK;
+}
+
+cl_status cl_drift(cl_lattice* l, double* host_aos) {
+  if (!l || !host_aos) return fail(CL_ERR_INVALID, "NULL argument");
+  cl_status s = ensure_stage(l);
+  if (s != CL_OK) return s;
+  const bool th = theta_nonzero(l);
+  if (th) {
+    CK(launch_clover(l->prec, l->g, l->U, l->F, KAPPA_Q * l->p.theta_im, -KAPPA_Q * l->p.theta_re, l->st));
+    l->launches++;
+  }
+  CK(launch_cl_update(l->prec, th, 1, l->g, l->U, l->F, l->Un, l->p.beta, 0.0, l->p.seed,
+                      (uint32_t)l->step, l->st));
+  CK(launch_soa_to_aos(l->prec, l->g, l->Un, l->stage, 4, l->st));
+  l->launches += 2;
+  CK(cudaMemcpyAsync(host_aos, l->stage, sizeof(double) * 18 * 4 * (size_t)l->g.V,
+                     cudaMemcpyDeviceToHost, l->st));
+  CK(cudaStreamSynchronize(l->st));
+  return CL_OK;
+}
+
+cl_status cl_cool_gradient(cl_lattice* l, double* host_f) {
+  if (!l || !host_f) return fail(CL_ERR_INVALID, "NULL argument");
+  CK(launch_cool_grad(l->prec, l->g, l->U, l->f, l->partials, nullptr, l->st));
+  l->launches++;
+  const size_t n = 8 * (size_t)l->g.V;
+  if (l->prec == 0) {
+    CK(cudaMemcpyAsync(host_f, l->f, sizeof(double) * n, cudaMemcpyDeviceToHost, l->st));
+    CK(cudaStreamSynchronize(l->st));
+  } else {
+    std::vector<float> t(n);
+    CK(cudaMemcpyAsync(t.data(), l->f, sizeof(float) * n, cudaMemcpyDeviceToHost, l->st));
+    CK(cudaStreamSynchronize(l->st));
+    for (size_t i = 0; i < n; ++i) host_f[i] = t[i];
+  }
+  return CL_OK;
+}
+
+cl_status cl_qdensity(cl_lattice* l, double* host_q) {
+  if (!l || !host_q) return fail(CL_ERR_INVALID, "NULL argument");
+  if (!l->qsite) CK(cudaMalloc(&l->qsite, sizeof(double) * 2 * (size_t)l->g.V));
+  cl_status s = do_obs(l, l->obs, l->qsite);
+  if (s != CL_OK) return s;
+  CK(cudaMemcpyAsync(host_q, l->qsite, sizeof(double) * 2 * (size_t)l->g.V,
+                     cudaMemcpyDeviceToHost, l->st));
+  CK(cudaStreamSynchronize(l->st));
+  return CL_OK;
+}
+
+cl_status cl_launch_count(const cl_lattice* l, int64_t* count) {
+  if (!l || !count) return fail(CL_ERR_INVALID, "NULL argument");
+  *count = l->launches;
+  return CL_OK;
+}
+
+cl_status cl_set_timing(cl_lattice* l, int on) {
+  if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  CK(resolve_timing(l));
+  for (int i = 0; i < CL_NPHASE; ++i) {
+    l->phase_ms[i] = 0.0;
+    l->phase_n[i] = 0;
+  }
+  l->timing = on ? 1 : 0;
+  return CL_OK;
+}
+
+cl_status cl_get_timing(cl_lattice* l, double* ms, int64_t* launches) {
+  if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  CK(resolve_timing(l));
+  for (int i = 0; i < CL_NPHASE; ++i) {
+    if (ms) ms[i] = l->phase_ms[i];
+    if (launches) launches[i] = l->phase_n[i];
+  }
+  return CL_OK;
+}
+
+cl_status cl_synchronize(cl_lattice* l) {
+  if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  CK(cudaStreamSynchronize(l->st));
+  return CL_OK;
+}
+
+void cl_free(cl_lattice* l) {
+  if (!l) return;
+  void* bufs[] = {l->U, l->Un, l->F, l->f, l->Om, l->Omi, l->partials, l->cs, l->obs,
+                  l->stage, l->qsite};
+  if (l->st) cudaStreamSynchronize(l->st);
+  for (void* b : bufs)
+    if (b) cudaFree(b);
+  if (l->ev_pending) {
+    for (auto& p : *l->ev_pending) {
+      cudaEventDestroy(p.second.first);
+      cudaEventDestroy(p.second.second);
+    }
+    delete l->ev_pending;
+  }
+  if (l->ev_pool) {
+    for (cudaEvent_t e : *l->ev_pool) cudaEventDestroy(e);
+    delete l->ev_pool;
+  }
+  delete l;
+}
+
+const char* cl_status_str(cl_status s) {
+  switch (s) {
+    case CL_OK: return "ok";
+    case CL_ERR_INVALID: return "invalid argument";
+    case CL_ERR_OOM: return "out of device memory";
+    case CL_ERR_CUDA: return "CUDA error";
+    case CL_ERR_NONFINITE: return "non-finite links";
+    case CL_ERR_RUNAWAY: return "runaway (unitarity norm above bound)";
+    case CL_ERR_TIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+const char* cl_last_error(void) { return g_err.c_str(); }
+
+int cl_version(void) { return 1; }
+
+}  // extern "C"

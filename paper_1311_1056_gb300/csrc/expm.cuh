@@ -1,0 +1,220 @@
+// expm.cuh -- FP64 matrix exponentials of traceless 3x3 matrices and the
+// det = 1 re-projection.
+//
+// Method (Cayley-Hamilton reduction): a traceless 3x3 A satisfies
+//   A^3 = c1 A + c0 1,  c1 = Tr(A^2)/2,  c0 = det A = Tr(A^3)/3,
+// so every power series in A collapses to a 1 + b A + c A^2.  The truncated
+// Taylor series of exp is evaluated by Horner's rule directly on the three
+// coefficients: multiplying a 1 + b A + c A^2 by A gives
+//   (c c0) 1 + (a + c c1) A + b A^2,
+// i.e. 8 FP64 operations per term instead of a 3x3 product.  The number of
+// terms follows from the Frobenius norm r (remainder r^(N+1)/(N+1)! < 2^-54);
+// for r > 1 the argument is scaled by 2^-s and the coefficients are squared
+// s times in the same three-term representation.
+//
+// The Hermitian variant (cooling transformation Omega = exp(H), H = -eps
+// alpha f_a lambda_a, Sec. 2, eq. "eq:24") has real c0, c1 and real
+// coefficients, and produces exp(-H) = Omega^{-1} from the same H^2.
+#pragma once
+#include "su3.cuh"
+
+namespace clgc {
+
+__constant__ double c_invfact[28] = {
+    1.0, 1.0, 0.5, 1.0 / 6, 1.0 / 24, 1.0 / 120, 1.0 / 720, 1.0 / 5040, 1.0 / 40320,
+    1.0 / 362880, 1.0 / 3628800, 1.0 / 39916800, 1.0 / 479001600, 1.0 / 6227020800.0,
+    1.0 / 87178291200.0, 1.0 / 1307674368000.0, 1.0 / 20922789888000.0,
+    1.0 / 355687428096000.0, 1.0 / 6402373705728000.0, 1.0 / 121645100408832000.0,
+    1.0 / 2432902008176640000.0, 1.0 / 51090942171709440000.0,
+    1.0 / 1124000727777607680000.0, 1.0 / 25852016738884976640000.0,
+    1.0 / 620448401733239439360000.0, 1.0 / 15511210043330985984000000.0,
+    1.0 / 403291461126605635584000000.0, 1.0 / 10888869450418352160768000000.0};
+
+// Number of Taylor terms for ||B||_F <= r <= 1 (float arithmetic: an estimate
+// on the cheap pipe; the bound has a factor > 2 of slack at the cut).
+__device__ __forceinline__ int taylor_terms(float r) {
+  float t = 1.0f;
+  int n = 0;
+  do {
+    ++n;
+    t *= r / (float)n;
+  } while (t >= 1.4e-17f && n < 26);
+  return n;
+}
+
+// exp(A) for traceless complex A, FP64.
+__device__ __forceinline__ void expm_traceless(mat<double>& E, const mat<double>& A) {
+  mat<double> A2;
+  mul(A2, A, A);
+  cx<double> c1 = trace(A2);
+  c1.re *= 0.5;
+  c1.im *= 0.5;
+  cx<double> c0 = trace_mul(A2, A);
+  c0.re *= (1.0 / 3.0);
+  c0.im *= (1.0 / 3.0);
+  double r2 = norm2(A);
+  float r = sqrtf((float)r2);
+  int s = 0;
+  double sc = 1.0;  // scaling 2^-s
+  if (r > 1.0f) {
+    s = (int)ceilf(log2f(r));
+    sc = ldexp(1.0, -s);
+    r = (float)(r * sc);
+  }
+  double sc2 = sc * sc;
+  cx<double> b0 = {c0.re * sc2 * sc, c0.im * sc2 * sc};  // det(A 2^-s)
+  cx<double> b1 = {c1.re * sc2, c1.im * sc2};            // Tr((A 2^-s)^2)/2
+  int N = taylor_terms(r);
+  cx<double> a = {c_invfact[N], 0.0}, b = {0.0, 0.0}, c = {0.0, 0.0};
+  for (int k = N - 1; k >= 0; --k) {
+    cx<double> na = cfma(c, b0, cx<double>{c_invfact[k], 0.0});
+    cx<double> nb = cfma(c, b1, a);
+    c = b;
+    b = nb;
+    a = na;
+  }
+  for (int i = 0; i < s; ++i) {  // (a + bB + cB^2)^2 with B^3 = b1 B + b0
+    cx<double> bc = cmul(b, c);
+    cx<double> cc = cmul(c, c);
+    cx<double> na = cmul(a, a);
+    na = cfma(cx<double>{2.0 * bc.re, 2.0 * bc.im}, b0, na);
+    cx<double> nb = cmul(cx<double>{2.0 * a.re, 2.0 * a.im}, b);
+    nb = cfma(cx<double>{2.0 * bc.re, 2.0 * bc.im}, b1, nb);
+    nb = cfma(cc, b0, nb);
+    cx<double> nc = cmul(b, b);
+    nc = cfma(cx<double>{2.0 * a.re, 2.0 * a.im}, c, nc);
+    nc = cfma(cc, b1, nc);
+    a = na;
+    b = nb;
+    c = nc;
+  }
+  // back to powers of A: b B = (b sc) A, c B^2 = (c sc^2) A^2
+  b.re *= sc;
+  b.im *= sc;
+  c.re *= sc2;
+  c.im *= sc2;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    cx<double> v = cmul(b, A.e[k]);
+    v = cfma(c, A2.e[k], v);
+    if (k % 4 == 0) {
+      v.re += a.re;
+      v.im += a.im;
+    }
+    E.e[k] = v;
+  }
+}
+
+// Packed Hermitian 3x3: d0, d1, d2 real diagonal, o01, o02, o12 upper entries.
+struct herm {
+  double d0, d1, d2;
+  cx<double> o01, o02, o12;
+};
+
+__device__ __forceinline__ void herm_square(herm& q, const herm& h) {
+  double n01 = fma(h.o01.re, h.o01.re, h.o01.im * h.o01.im);
+  double n02 = fma(h.o02.re, h.o02.re, h.o02.im * h.o02.im);
+  double n12 = fma(h.o12.re, h.o12.re, h.o12.im * h.o12.im);
+  q.d0 = fma(h.d0, h.d0, n01 + n02);
+  q.d1 = fma(h.d1, h.d1, n01 + n12);
+  q.d2 = fma(h.d2, h.d2, n02 + n12);
+  // (H^2)_01 = (d0 + d1) o01 + o02 conj(o12)
+  double s01 = h.d0 + h.d1, s02 = h.d0 + h.d2, s12 = h.d1 + h.d2;
+  q.o01.re = fma(s01, h.o01.re, fma(h.o02.re, h.o12.re, h.o02.im * h.o12.im));
+  q.o01.im = fma(s01, h.o01.im, fma(h.o02.im, h.o12.re, -h.o02.re * h.o12.im));
+  // (H^2)_02 = (d0 + d2) o02 + o01 o12
+  q.o02.re = fma(s02, h.o02.re, fma(h.o01.re, h.o12.re, -h.o01.im * h.o12.im));
+  q.o02.im = fma(s02, h.o02.im, fma(h.o01.re, h.o12.im, h.o01.im * h.o12.re));
+  // (H^2)_12 = (d1 + d2) o12 + conj(o01) o02
+  q.o12.re = fma(s12, h.o12.re, fma(h.o01.re, h.o02.re, h.o01.im * h.o02.im));
+  q.o12.im = fma(s12, h.o12.im, fma(h.o01.re, h.o02.im, -h.o01.im * h.o02.re));
+}
+
+// Omega = exp(H) and Omega^{-1} = exp(-H) for traceless Hermitian H.
+__device__ __forceinline__ void expm_hermitian_pair(herm& om, herm& omi, const herm& h) {
+  herm h2;
+  herm_square(h2, h);
+  double c1 = 0.5 * (h2.d0 + h2.d1 + h2.d2);  // Tr H^2 / 2 = ||H||_F^2 / 2
+  // det H = d0 d1 d2 + 2 Re(o01 o12 conj(o02)) - d0|o12|^2 - d1|o02|^2 - d2|o01|^2
+  double t_re = fma(h.o01.re, h.o12.re, -h.o01.im * h.o12.im);
+  double t_im = fma(h.o01.re, h.o12.im, h.o01.im * h.o12.re);
+  double c0 = h.d0 * h.d1 * h.d2;
+  c0 = fma(2.0, fma(t_re, h.o02.re, t_im * h.o02.im), c0);
+  c0 = fma(-h.d0, fma(h.o12.re, h.o12.re, h.o12.im * h.o12.im), c0);
+  c0 = fma(-h.d1, fma(h.o02.re, h.o02.re, h.o02.im * h.o02.im), c0);
+  c0 = fma(-h.d2, fma(h.o01.re, h.o01.re, h.o01.im * h.o01.im), c0);
+  float r = sqrtf((float)(2.0 * c1));
+  int s = 0;
+  double sc = 1.0;
+  if (r > 1.0f) {
+    s = (int)ceilf(log2f(r));
+    sc = ldexp(1.0, -s);
+    r = (float)(r * sc);
+  }
+  double b1 = c1 * sc * sc, b0 = c0 * sc * sc * sc;
+  int N = taylor_terms(r);
+  // exp(B) = a + bB + cB^2 and exp(-B) = ap - bp B + cp B^2 (det(-B) = -det B)
+  double a = c_invfact[N], b = 0.0, c = 0.0;
+  double ap = a, bp = 0.0, cp = 0.0;
+  for (int k = N - 1; k >= 0; --k) {
+    double na = fma(c, b0, c_invfact[k]);
+    double nb = fma(c, b1, a);
+    c = b;
+    b = nb;
+    a = na;
+    double nap = fma(-cp, b0, c_invfact[k]);
+    double nbp = fma(cp, b1, ap);
+    cp = bp;
+    bp = nbp;
+    ap = nap;
+  }
+  for (int i = 0; i < s; ++i) {
+    double na = fma(2.0 * b * c, b0, a * a);
+    double nb = fma(c * c, b0, fma(2.0 * b * c, b1, 2.0 * a * b));
+    double nc = fma(c * c, b1, fma(2.0 * a, c, b * b));
+    a = na; b = nb; c = nc;
+    na = fma(-2.0 * bp * cp, b0, ap * ap);
+    nb = fma(-cp * cp, b0, fma(2.0 * bp * cp, b1, 2.0 * ap * bp));
+    nc = fma(cp * cp, b1, fma(2.0 * ap, cp, bp * bp));
+    ap = na; bp = nb; cp = nc;
+  }
+  b *= sc;
+  c *= sc * sc;
+  bp *= -sc;
+  cp *= sc * sc;
+  om.d0 = fma(c, h2.d0, fma(b, h.d0, a));
+  om.d1 = fma(c, h2.d1, fma(b, h.d1, a));
+  om.d2 = fma(c, h2.d2, fma(b, h.d2, a));
+  om.o01 = cx<double>{fma(c, h2.o01.re, b * h.o01.re), fma(c, h2.o01.im, b * h.o01.im)};
+  om.o02 = cx<double>{fma(c, h2.o02.re, b * h.o02.re), fma(c, h2.o02.im, b * h.o02.im)};
+  om.o12 = cx<double>{fma(c, h2.o12.re, b * h.o12.re), fma(c, h2.o12.im, b * h.o12.im)};
+  omi.d0 = fma(cp, h2.d0, fma(bp, h.d0, ap));
+  omi.d1 = fma(cp, h2.d1, fma(bp, h.d1, ap));
+  omi.d2 = fma(cp, h2.d2, fma(bp, h.d2, ap));
+  omi.o01 = cx<double>{fma(cp, h2.o01.re, bp * h.o01.re), fma(cp, h2.o01.im, bp * h.o01.im)};
+  omi.o02 = cx<double>{fma(cp, h2.o02.re, bp * h.o02.re), fma(cp, h2.o02.im, bp * h.o02.im)};
+  omi.o12 = cx<double>{fma(cp, h2.o12.re, bp * h.o12.re), fma(cp, h2.o12.im, bp * h.o12.im)};
+}
+
+// det(U)^(-1/3) on the principal branch.  Near det = 1 (|det - 1| < 1e-4, the
+// normal case after an update that preserves det up to rounding) the binomial
+// series (1 + d)^(-1/3) = 1 - d/3 + 2d^2/9 - 14d^3/81 + 35d^4/243 - ... is
+// exact to 1e-17; otherwise |det|^(-1/3) exp(-i arg(det)/3).
+__device__ __forceinline__ cx<double> det_inv_cuberoot(cx<double> d) {
+  cx<double> e = {d.re - 1.0, d.im};
+  if (fma(e.re, e.re, e.im * e.im) < 1e-8) {
+    cx<double> p = {35.0 / 243.0, 0.0};
+    p = cfma(p, e, cx<double>{-14.0 / 81.0, 0.0});
+    p = cfma(p, e, cx<double>{2.0 / 9.0, 0.0});
+    p = cfma(p, e, cx<double>{-1.0 / 3.0, 0.0});
+    p = cfma(p, e, cx<double>{1.0, 0.0});
+    return p;
+  }
+  double mag = exp(-log(hypot(d.re, d.im)) / 3.0);
+  double ang = -atan2(d.im, d.re) / 3.0;
+  double sn, cs;
+  sincos(ang, &sn, &cs);
+  return cx<double>{mag * cs, mag * sn};
+}
+
+}  // namespace clgc

@@ -1,0 +1,644 @@
+// kernels.cu -- starts, layout conversion, clover field, gauge cooling and
+// observables.  The CL update kernel itself is in k_update.cuh
+// (instantiated by k_update_f64.cu / k_update_f32.cu).
+#include "expm.cuh"
+#include "launch.h"
+#include "lattice.cuh"
+#include "philox.cuh"
+#include "su3.cuh"
+
+namespace clgc {
+
+namespace {
+
+const double KAPPA_Q = -1.0 / (256.0 * 9.86960440108935861883);  // -1/(256 pi^2)
+
+Geo to_geo(const GeoH& h) { return make_geo(h.L, h.V); }
+
+inline dim3 grid_sites(int V, int planes = 1) {
+  return dim3((unsigned)((V + RED_THREADS - 1) / RED_THREADS), (unsigned)planes);
+}
+
+// Fixed-order block reduction of NQ doubles (slot MAXSLOT takes the max);
+// one record per block into partials.
+template <int NQ, int MAXSLOT>
+__device__ __forceinline__ void block_reduce_store(double* v, double* partials) {
+  __shared__ double sm[RED_THREADS / 32][NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q)
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      double o = __shfl_down_sync(0xffffffffu, v[q], off);
+      v[q] = (q == MAXSLOT) ? fmax(v[q], o) : v[q] + o;
+    }
+  int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) sm[w][q] = v[q];
+  __syncthreads();
+  if (threadIdx.x < NQ) {
+    int q = threadIdx.x;
+    double s = sm[0][q];
+    for (int k = 1; k < RED_THREADS / 32; ++k) s = (q == MAXSLOT) ? fmax(s, sm[k][q]) : s + sm[k][q];
+    partials[(size_t)blockIdx.x * NQ + q] = s;
+  }
+}
+
+// Single-block fixed-order sum of nb records of NQ doubles.
+template <int NQ, int MAXSLOT>
+__device__ __forceinline__ void reduce_partials(const double* partials, int nb, double* out) {
+  __shared__ double sm[256][NQ];
+  double v[NQ];
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) v[q] = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+      double x = partials[(size_t)b * NQ + q];
+      v[q] = (q == MAXSLOT) ? fmax(v[q], x) : v[q] + x;
+    }
+#pragma unroll
+  for (int q = 0; q < NQ; ++q) sm[threadIdx.x][q] = v[q];
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if ((int)threadIdx.x < w)
+#pragma unroll
+      for (int q = 0; q < NQ; ++q)
+        sm[threadIdx.x][q] = (q == MAXSLOT) ? fmax(sm[threadIdx.x][q], sm[threadIdx.x + w][q])
+                                            : sm[threadIdx.x][q] + sm[threadIdx.x + w][q];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) out[q] = sm[0][q];
+}
+
+template <typename T>
+__device__ __forceinline__ bool finite_mat(const mat<T>& a) {
+  bool ok = true;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) ok = ok && isfinite(a.e[k].re) && isfinite(a.e[k].im);
+  return ok;
+}
+
+// --------------------------------------------------------------- starts
+template <typename T>
+__global__ void k_cold(Geo g, typename vec2_of<T>::type* U) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  mat<T> I;
+  set_ident(I);
+  store(U, blockIdx.y, s, g.V, I);
+}
+
+// Haar SU(3): Gram-Schmidt on the rows of a complex Gaussian matrix (Philox
+// stream 2) gives Haar U(3); the principal cube root of the determinant maps
+// it to SU(3).
+template <typename T>
+__global__ void k_hot(Geo g, typename vec2_of<T>::type* U, uint64_t seed) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int mu = blockIdx.y;
+  double z[18];
+  normals_f64<9>(z, seed, 0u, (uint32_t)s, (uint32_t)mu, STREAM_HOT);
+  mat<double> m;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m.e[k] = cx<double>{z[2 * k], z[2 * k + 1]};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+#pragma unroll
+    for (int k = 0; k < i; ++k) {
+      cx<double> ip = {0.0, 0.0};  // <row_k, row_i>
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        cx<double> ck = {m.e[3 * k + j].re, -m.e[3 * k + j].im};
+        ip = cfma(ck, m.e[3 * i + j], ip);
+      }
+#pragma unroll
+      for (int j = 0; j < 3; ++j) m.e[3 * i + j] = cfms(ip, m.e[3 * k + j], m.e[3 * i + j]);
+    }
+    double n = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) n = fma(m.e[3 * i + j].re, m.e[3 * i + j].re, fma(m.e[3 * i + j].im, m.e[3 * i + j].im, n));
+    double inv = 1.0 / sqrt(n);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) { m.e[3 * i + j].re *= inv; m.e[3 * i + j].im *= inv; }
+  }
+  cx<double> zf = det_inv_cuberoot(det(m));
+#pragma unroll
+  for (int k = 0; k < 9; ++k) m.e[k] = cmul(m.e[k], zf);
+  mat<T> t;
+  convert(t, m);
+  store(U, mu, s, g.V, t);
+}
+
+// Packed Hermitian field: planes d0, d1, d2, re01, im01, re02, im02, re12, im12.
+template <typename T>
+__device__ __forceinline__ void store_herm(T* P, int s, int V, const herm& h) {
+  P[0 * (size_t)V + s] = (T)h.d0;
+  P[1 * (size_t)V + s] = (T)h.d1;
+  P[2 * (size_t)V + s] = (T)h.d2;
+  P[3 * (size_t)V + s] = (T)h.o01.re;
+  P[4 * (size_t)V + s] = (T)h.o01.im;
+  P[5 * (size_t)V + s] = (T)h.o02.re;
+  P[6 * (size_t)V + s] = (T)h.o02.im;
+  P[7 * (size_t)V + s] = (T)h.o12.re;
+  P[8 * (size_t)V + s] = (T)h.o12.im;
+}
+template <typename T>
+__device__ __forceinline__ void load_herm_mat(mat<T>& m, const T* __restrict__ P, int s, int V) {
+  T d0 = __ldg(P + s), d1 = __ldg(P + (size_t)V + s), d2 = __ldg(P + 2 * (size_t)V + s);
+  T a = __ldg(P + 3 * (size_t)V + s), b = __ldg(P + 4 * (size_t)V + s);
+  T c = __ldg(P + 5 * (size_t)V + s), d = __ldg(P + 6 * (size_t)V + s);
+  T e = __ldg(P + 7 * (size_t)V + s), f = __ldg(P + 8 * (size_t)V + s);
+  m.e[0] = cx<T>{d0, T(0)};
+  m.e[4] = cx<T>{d1, T(0)};
+  m.e[8] = cx<T>{d2, T(0)};
+  m.e[1] = cx<T>{a, b};
+  m.e[3] = cx<T>{a, -b};
+  m.e[2] = cx<T>{c, d};
+  m.e[6] = cx<T>{c, -d};
+  m.e[5] = cx<T>{e, f};
+  m.e[7] = cx<T>{e, -f};
+}
+
+// H = c * sum_a g_a lambda_a (Hermitian, traceless), g real.
+__device__ __forceinline__ herm herm_from_algebra(const double* g, double c) {
+  const double r3 = 0.57735026918962576451;
+  herm h;
+  h.d0 = c * (g[2] + g[7] * r3);
+  h.d1 = c * (-g[2] + g[7] * r3);
+  h.d2 = c * (-2.0 * g[7] * r3);
+  h.o01 = cx<double>{c * g[0], -c * g[1]};
+  h.o02 = cx<double>{c * g[3], -c * g[4]};
+  h.o12 = cx<double>{c * g[5], -c * g[6]};
+  return h;
+}
+
+// Omega_x = exp(i w_a lambda_a) with w_a = i sigma g_a, i.e. exp(-sigma g_a lambda_a).
+template <typename T>
+__global__ void k_gauge_omega(Geo g, T* Om, T* Omi, uint64_t seed, double sigma) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  double r[8];
+  normals_f64<4>(r, seed, 0u, (uint32_t)s, 0u, STREAM_GAUGE);
+  herm h = herm_from_algebra(r, -sigma), om, omi;
+  expm_hermitian_pair(om, omi, h);
+  store_herm(Om, s, g.V, om);
+  store_herm(Omi, s, g.V, omi);
+}
+
+// ------------------------------------------------------------ conversion
+// AoS [site][plane][row][col]{re,im} doubles <-> SoA planes of T2.
+template <typename T>
+__global__ void k_aos_to_soa(Geo g, const double* __restrict__ aos, typename vec2_of<T>::type* U,
+                             int nplanes) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // complex element index
+  size_t n = (size_t)g.V * nplanes * 9;
+  if (idx >= n) return;
+  int s = (int)(idx / (9 * nplanes));
+  int r = (int)(idx - (size_t)s * 9 * nplanes);
+  int p = r / 9, k = r - 9 * p;
+  typename vec2_of<T>::type v;
+  v.x = (T)aos[2 * idx];
+  v.y = (T)aos[2 * idx + 1];
+  U[((size_t)p * 9 + k) * g.V + s] = v;
+}
+template <typename T>
+__global__ void k_soa_to_aos(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                             double* aos, int nplanes) {
+  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  size_t n = (size_t)g.V * nplanes * 9;
+  if (idx >= n) return;
+  int s = (int)(idx / (9 * nplanes));
+  int r = (int)(idx - (size_t)s * 9 * nplanes);
+  int p = r / 9, k = r - 9 * p;
+  typename vec2_of<T>::type v = U[((size_t)p * 9 + k) * g.V + s];
+  aos[2 * idx] = (double)v.x;
+  aos[2 * idx + 1] = (double)v.y;
+}
+
+// ------------------------------------------------------------ clover field
+// F_{mu nu}(x) = sum over the four leaves L at x, oriented mu -> nu, of (L - L^{-1}):
+//   L1 = U_mu(x) U_nu(x+mu) [U_nu(x) U_mu(x+nu)]^{-1}
+//   L2 = U_nu(x) [U_nu(x-mu) U_mu(x-mu+nu)]^{-1} U_mu(x-mu)
+//   L3 = [U_nu(x-mu-nu) U_mu(x-mu)]^{-1} U_mu(x-mu-nu) U_nu(x-nu)
+//   L4 = U_nu(x-nu)^{-1} U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^{-1}
+// Stored times a complex scale (-i theta kappa for the drift, 1 for q_L).
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_clover(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                       typename vec2_of<T>::type* __restrict__ F,
+                                                       double sre, double sim) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int p = blockIdx.y, mu = plane_mu(p), nu = plane_nu(p);
+  int x[4];
+  site_coords(g, s, x);
+  const int xpm = hop(g, s, x, mu, 1), xmm = hop(g, s, x, mu, -1);
+  const int xpn = hop(g, s, x, nu, 1), xmn = hop(g, s, x, nu, -1);
+  const int xmm_pn = hop2(g, s, x, mu, -1, nu, 1), xmm_mn = hop2(g, s, x, mu, -1, nu, -1);
+  const int xpm_mn = hop2(g, s, x, mu, 1, nu, -1);
+  mat<T> acc, a, b, A, B, L, Li;
+  set_zero(acc);
+  // L1
+  load(a, U, mu, s, g.V); load(b, U, nu, xpm, g.V); mul(A, a, b);
+  load(a, U, nu, s, g.V); load(b, U, mu, xpn, g.V); mul(B, a, b);
+  adj(a, B); mul(L, A, a); adj(Li, L);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc.e[k] = cadd(acc.e[k], csub(L.e[k], Li.e[k]));
+  // L2
+  load(a, U, nu, xmm, g.V); load(b, U, mu, xmm_pn, g.V); mul(B, a, b); adj(A, B);
+  load(a, U, nu, s, g.V); mul(B, a, A);
+  load(b, U, mu, xmm, g.V); mul(L, B, b); adj(Li, L);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc.e[k] = cadd(acc.e[k], csub(L.e[k], Li.e[k]));
+  // L3
+  load(a, U, nu, xmm_mn, g.V); load(b, U, mu, xmm, g.V); mul(B, a, b); adj(A, B);
+  load(a, U, mu, xmm_mn, g.V); load(b, U, nu, xmn, g.V); mul(B, a, b);
+  mul(L, A, B); adj(Li, L);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc.e[k] = cadd(acc.e[k], csub(L.e[k], Li.e[k]));
+  // L4
+  load(a, U, mu, xmn, g.V); load(b, U, nu, xpm_mn, g.V); mul(B, a, b);
+  load(a, U, nu, xmn, g.V); adj(A, a); mul(a, A, B);
+  load(b, U, mu, s, g.V); adj(A, b); mul(L, a, A); adj(Li, L);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc.e[k] = cadd(acc.e[k], csub(L.e[k], Li.e[k]));
+  cx<T> sc = {(T)sre, (T)sim};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc.e[k] = cmul(acc.e[k], sc);
+  store(F, p, s, g.V, acc);
+}
+
+// --------------------------------------------------------------- cooling
+// f_ax = 2 Tr[lambda_a G_x], G_x = sum_mu (U_{x,mu} U_{x,mu}^+ - U_{x-mu,mu}^+ U_{x-mu,mu})
+// (Sec. 2, eq. "eq:24"); per block: sum |f|, sum f^2, sum (1/3) Tr U U^+ of
+// the links at x, nonfinite count.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                          T* __restrict__ f, double* partials,
+                                                          const CoolState* cs) {
+  if (cs && cs->done) return;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[NQ_COOL] = {0.0, 0.0, 0.0, 0.0};
+  if (s < g.V) {
+    int x[4];
+    site_coords(g, s, x);
+    T g00 = 0, g11 = 0, g22 = 0;
+    cx<T> g01 = {0, 0}, g02 = {0, 0}, g12 = {0, 0};
+    T un = 0;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      mat<T> u;
+      load(u, U, mu, s, g.V);
+      un += norm2(u);
+      // + U U^+ : (i,j) = sum_k U_ik conj(U_jk)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        cx<T> r0 = u.e[k], r1 = u.e[3 + k], r2 = u.e[6 + k];
+        g00 = fma(r0.re, r0.re, fma(r0.im, r0.im, g00));
+        g11 = fma(r1.re, r1.re, fma(r1.im, r1.im, g11));
+        g22 = fma(r2.re, r2.re, fma(r2.im, r2.im, g22));
+        g01 = cfma(r0, cx<T>{r1.re, -r1.im}, g01);
+        g02 = cfma(r0, cx<T>{r2.re, -r2.im}, g02);
+        g12 = cfma(r1, cx<T>{r2.re, -r2.im}, g12);
+      }
+      load(u, U, mu, hop(g, s, x, mu, -1), g.V);
+      // - U^+ U : (i,j) = sum_k conj(U_ki) U_kj
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        cx<T> c0 = u.e[3 * k], c1 = u.e[3 * k + 1], c2 = u.e[3 * k + 2];
+        g00 = fma(-c0.re, c0.re, fma(-c0.im, c0.im, g00));
+        g11 = fma(-c1.re, c1.re, fma(-c1.im, c1.im, g11));
+        g22 = fma(-c2.re, c2.re, fma(-c2.im, c2.im, g22));
+        g01 = cfms(cx<T>{c0.re, -c0.im}, c1, g01);
+        g02 = cfms(cx<T>{c0.re, -c0.im}, c2, g02);
+        g12 = cfms(cx<T>{c1.re, -c1.im}, c2, g12);
+      }
+    }
+    const T r3 = (T)0.57735026918962576451;
+    T fa[8];
+    fa[0] = 4 * g01.re;
+    fa[1] = -4 * g01.im;
+    fa[2] = 2 * (g00 - g11);
+    fa[3] = 4 * g02.re;
+    fa[4] = -4 * g02.im;
+    fa[5] = 4 * g12.re;
+    fa[6] = -4 * g12.im;
+    fa[7] = 2 * r3 * (g00 + g11 - 2 * g22);
+    bool ok = true;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      f[(size_t)a * g.V + s] = fa[a];
+      double d = (double)fa[a];
+      v[0] += fabs(d);
+      v[1] = fma(d, d, v[1]);
+      ok = ok && isfinite(fa[a]);
+    }
+    v[2] = (double)un * (1.0 / 3.0);
+    v[3] = ok ? 0.0 : 1.0;
+  }
+  block_reduce_store<NQ_COOL, -1>(v, partials);
+}
+
+// The adaptive rule (Sec. 4): alpha_ad = alpha / D with D_0 = 1,
+// D_1 = (1/3)<Tr U U^+> (normalised unitarity norm), D_2 = <|f_ax|>_{a,x}
+// (or its RMS).  Sweep count: at least n_min, at most n_max; stop once the
+// norm decreases by less than tol_rel of its distance from 1 or that distance
+// is below d_floor; no sweep when D < d_guard; forced_sweeps >= 0 fixes the count.
+__global__ void k_cool_adapt(Geo g, const double* partials, int nb, CoolArgs a, CoolState* cs,
+                             int first) {
+  __shared__ double tot[NQ_COOL];
+  reduce_partials<NQ_COOL, -1>(partials, nb, tot);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  if (first) {
+    cs->alpha_ad = 0.0;
+    cs->alpha_ad_last = 0.0;
+    cs->un_prev = 0.0;
+    cs->sweeps = 0;
+    cs->done = 0;
+    cs->k = 0;
+    cs->nonfinite = 0;
+  }
+  if (cs->done) return;
+  const double V = (double)g.V;
+  double un = tot[2] / (4.0 * V);
+  double D = 1.0;
+  if (a.mode == 1) D = un;
+  if (a.mode == 2) D = tot[0] / (8.0 * V);
+  if (a.mode == 3) D = sqrt(tot[1] / (8.0 * V));
+  int k = cs->k;
+  if (k == 0) cs->un_before = un;
+  cs->un_after = un;
+  cs->D = D;
+  bool stop;
+  if (a.forced_sweeps >= 0) {
+    stop = k >= a.forced_sweeps;
+  } else {
+    stop = k >= a.n_max;
+    if (k >= a.n_min) {
+      if (un - 1.0 < a.d_floor) stop = true;
+      if (k >= 1 && (cs->un_prev - un) < a.tol_rel * (cs->un_prev - 1.0)) stop = true;
+    }
+  }
+  if (D < a.d_guard) stop = true;
+  if (tot[3] != 0.0 || !isfinite(un)) {
+    cs->nonfinite = 1;
+    stop = true;
+  }
+  cs->k = k + 1;
+  if (stop) {
+    cs->done = 1;
+    return;
+  }
+  cs->alpha_ad = a.alpha / D;
+  cs->alpha_ad_last = cs->alpha_ad;
+  cs->sweeps += 1;
+  cs->un_prev = un;
+}
+
+// Omega_x = exp(-eps alpha_ad f_ax lambda_a) and its inverse, FP64.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_cool_omega(Geo g, const T* __restrict__ f, T* Om, T* Omi,
+                                                           double eps, const CoolState* cs) {
+  if (cs->done) return;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  double fa[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) fa[a] = (double)__ldg(f + (size_t)a * g.V + s);
+  herm h = herm_from_algebra(fa, -eps * cs->alpha_ad), om, omi;
+  expm_hermitian_pair(om, omi, h);
+  store_herm(Om, s, g.V, om);
+  store_herm(Omi, s, g.V, omi);
+}
+
+// U_{x,mu} <- Omega_x U_{x,mu} Omega_{x+mu}^{-1}, all links at once (in place:
+// every link is read and written by the same thread).
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_cool_apply(Geo g, typename vec2_of<T>::type* U, const T* __restrict__ Om,
+                                                           const T* __restrict__ Omi,
+                                                           const CoolState* cs) {
+  if (cs && cs->done) return;
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int mu = blockIdx.y;
+  int x[4];
+  site_coords(g, s, x);
+  mat<T> o, oi, u, t;
+  load_herm_mat(o, Om, s, g.V);
+  load_herm_mat(oi, Omi, hop(g, s, x, mu, 1), g.V);
+  load(u, U, mu, s, g.V);
+  mul(t, o, u);
+  mul(u, t, oi);
+  store(U, mu, s, g.V, u);
+}
+
+// ----------------------------------------------------------- observables
+// Per site: the six plaquettes P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^{-1} U_nu(x)^{-1}
+// (Tr P / 3 and Tr P + Tr P^{-1} for S_W), (1/3) Tr U U^+ of the four links,
+// max |det U - 1| (FP64), nonfinite count and, with the clover field,
+// q_L(x) = kappa [Tr F01 F23 - Tr F02 F13 + Tr F03 F12].
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_obs(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                    const typename vec2_of<T>::type* __restrict__ F,
+                                                    int with_q, double* partials, double* q_site) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  double v[NQ_OBS];
+#pragma unroll
+  for (int q = 0; q < NQ_OBS; ++q) v[q] = 0.0;
+  if (s < g.V) {
+    int x[4];
+    site_coords(g, s, x);
+    bool ok = true;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      mat<T> u;
+      load(u, U, mu, s, g.V);
+      ok = ok && finite_mat(u);
+      v[4] += (double)norm2(u) * (1.0 / 3.0);
+      mat<double> ud;
+      convert(ud, u);
+      cx<double> d = det(ud);
+      v[7] = fmax(v[7], hypot(d.re - 1.0, d.im));
+    }
+#pragma unroll
+    for (int p = 0; p < 6; ++p) {
+      const int mu = plane_mu(p), nu = plane_nu(p);
+      mat<T> a, b, A, B, Ai, Bi;
+      load(a, U, mu, s, g.V);
+      load(b, U, nu, hop(g, s, x, mu, 1), g.V);
+      mul(A, a, b);
+      load(a, U, nu, s, g.V);
+      load(b, U, mu, hop(g, s, x, nu, 1), g.V);
+      mul(B, a, b);
+      adj(Bi, B);
+      adj(Ai, A);
+      cx<T> tp = trace_mul(A, Bi);   // Tr P
+      cx<T> tpi = trace_mul(B, Ai);  // Tr P^{-1}
+      v[0] += (double)tp.re * (1.0 / 3.0);
+      v[1] += (double)tp.im * (1.0 / 3.0);
+      v[2] += (double)tp.re + (double)tpi.re;
+      v[3] += (double)tp.im + (double)tpi.im;
+    }
+    if (with_q) {
+      mat<T> F1, F2;
+      cx<double> q = {0.0, 0.0};
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        load(F1, F, p, s, g.V);
+        load(F2, F, 5 - p, s, g.V);
+        cx<T> t = trace_mul(F1, F2);
+        double sg = (p == 1) ? -1.0 : 1.0;
+        q.re += sg * (double)t.re;
+        q.im += sg * (double)t.im;
+      }
+      q.re *= KAPPA_Q;
+      q.im *= KAPPA_Q;
+      v[5] = q.re;
+      v[6] = q.im;
+      if (q_site) {
+        q_site[2 * (size_t)s] = q.re;
+        q_site[2 * (size_t)s + 1] = q.im;
+      }
+    }
+    v[8] = ok ? 0.0 : 1.0;
+  }
+  block_reduce_store<NQ_OBS, 7>(v, partials);
+}
+
+__global__ void k_obs_final(Geo g, const double* partials, int nb, double beta, double th_re,
+                            double th_im, ObsOut* out) {
+  __shared__ double tot[NQ_OBS];
+  reduce_partials<NQ_OBS, 7>(partials, nb, tot);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double V = (double)g.V, np = 6.0 * V;
+  out->plaq_re = tot[0] / np;
+  out->plaq_im = tot[1] / np;
+  out->un = tot[4] / (4.0 * V);
+  out->q_re = tot[5];
+  out->q_im = tot[6];
+  out->sw_re = beta * np - beta / 6.0 * tot[2];
+  out->sw_im = -beta / 6.0 * tot[3];
+  // S = S_W - i theta Q
+  out->s_re = out->sw_re + th_re * tot[6] + th_im * tot[5];
+  out->s_im = out->sw_im - th_re * tot[5] + th_im * tot[6];
+  out->max_det_dev = tot[7];
+  out->nonfinite = tot[8];
+}
+
+}  // namespace
+
+int reduce_blocks(int V) { return (V + RED_THREADS - 1) / RED_THREADS; }
+
+cudaError_t launch_cold(int prec, const GeoH& h, void* U, cudaStream_t st) {
+  Geo g = to_geo(h);
+  if (prec == 0) k_cold<double><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (double2*)U);
+  else k_cold<float><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (float2*)U);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hot(int prec, const GeoH& h, void* U, uint64_t seed, cudaStream_t st) {
+  Geo g = to_geo(h);
+  if (prec == 0) k_hot<double><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (double2*)U, seed);
+  else k_hot<float><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (float2*)U, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gauge_omega(int prec, const GeoH& h, void* Om, void* Omi, uint64_t seed,
+                               double sigma, cudaStream_t st) {
+  Geo g = to_geo(h);
+  if (prec == 0)
+    k_gauge_omega<double><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (double*)Om, (double*)Omi, seed, sigma);
+  else
+    k_gauge_omega<float><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (float*)Om, (float*)Omi, seed, sigma);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_aos_to_soa(int prec, const GeoH& h, const double* aos, void* U, int nplanes,
+                              cudaStream_t st) {
+  Geo g = to_geo(h);
+  size_t n = (size_t)g.V * nplanes * 9;
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (prec == 0) k_aos_to_soa<double><<<blocks, 256, 0, st>>>(g, aos, (double2*)U, nplanes);
+  else k_aos_to_soa<float><<<blocks, 256, 0, st>>>(g, aos, (float2*)U, nplanes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_soa_to_aos(int prec, const GeoH& h, const void* U, double* aos, int nplanes,
+                              cudaStream_t st) {
+  Geo g = to_geo(h);
+  size_t n = (size_t)g.V * nplanes * 9;
+  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (prec == 0) k_soa_to_aos<double><<<blocks, 256, 0, st>>>(g, (const double2*)U, aos, nplanes);
+  else k_soa_to_aos<float><<<blocks, 256, 0, st>>>(g, (const float2*)U, aos, nplanes);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clover(int prec, const GeoH& h, const void* U, void* F, double sre, double sim,
+                          cudaStream_t st) {
+  Geo g = to_geo(h);
+  if (prec == 0)
+    k_clover<double><<<grid_sites(g.V, 6), RED_THREADS, 0, st>>>(g, (const double2*)U, (double2*)F, sre, sim);
+  else
+    k_clover<float><<<grid_sites(g.V, 6), RED_THREADS, 0, st>>>(g, (const float2*)U, (float2*)F, sre, sim);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cool_grad(int prec, const GeoH& h, const void* U, void* f, double* partials,
+                             const CoolState* cs, cudaStream_t st) {
+  Geo g = to_geo(h);
+  if (prec == 0)
+    k_cool_grad<double><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const double2*)U, (double*)f, partials, cs);
+  else
+    k_cool_grad<float><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const float2*)U, (float*)f, partials, cs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cool_adapt(const GeoH& h, const double* partials, CoolArgs a, CoolState* cs,
+                              int first, cudaStream_t st) {
+  Geo g = to_geo(h);
+  k_cool_adapt<<<1, 256, 0, st>>>(g, partials, reduce_blocks(g.V), a, cs, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cool_omega(int prec, const GeoH& h, const void* f, void* Om, void* Omi, double eps,
+                              const CoolState* cs, cudaStream_t st) {
+  Geo g = to_geo(h);
+  if (prec == 0)
+    k_cool_omega<double><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const double*)f, (double*)Om, (double*)Omi, eps, cs);
+  else
+    k_cool_omega<float><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const float*)f, (float*)Om, (float*)Omi, eps, cs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cool_apply(int prec, const GeoH& h, void* U, const void* Om, const void* Omi,
+                              const CoolState* cs, cudaStream_t st) {
+  Geo g = to_geo(h);
+  if (prec == 0)
+    k_cool_apply<double><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (double2*)U, (const double*)Om, (const double*)Omi, cs);
+  else
+    k_cool_apply<float><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (float2*)U, (const float*)Om, (const float*)Omi, cs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_obs(int prec, const GeoH& h, const void* U, const void* F, int with_q,
+                       double* partials, double* q_site, cudaStream_t st) {
+  Geo g = to_geo(h);
+  if (prec == 0)
+    k_obs<double><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const double2*)U, (const double2*)F, with_q, partials, q_site);
+  else
+    k_obs<float><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const float2*)U, (const float2*)F, with_q, partials, q_site);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_obs_final(const GeoH& h, const double* partials, double beta, double th_re,
+                             double th_im, ObsOut* out, cudaStream_t st) {
+  Geo g = to_geo(h);
+  k_obs_final<<<1, 256, 0, st>>>(g, partials, reduce_blocks(g.V), beta, th_re, th_im, out);
+  return cudaGetLastError();
+}
+
+}  // namespace clgc

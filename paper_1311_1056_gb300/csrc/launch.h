@@ -1,0 +1,73 @@
+// launch.h -- host-side launchers of the CL / gauge-cooling kernels (internal
+// interface between the C-ABI runtime and the kernel translation units).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace clgc {
+
+struct GeoH {
+  int L[4];
+  int V;
+};
+
+// Packed results of the cooling rule, resident on the device.
+struct CoolState {
+  double alpha_ad;       // alpha / D of the sweep about to run
+  double alpha_ad_last;  // of the last applied sweep
+  double un_prev;        // unitarity norm before the last applied sweep
+  double un_before, un_after, D;
+  int sweeps, done, k, nonfinite;
+};
+
+struct CoolArgs {
+  double eps, alpha, tol_rel, d_floor, d_guard;
+  int mode, n_min, n_max, forced_sweeps;
+};
+
+// Observables accumulated on the device (FP64), one record per call.
+struct ObsOut {
+  double plaq_re, plaq_im, un, q_re, q_im, sw_re, sw_im, s_re, s_im, max_det_dev;
+  double nonfinite;
+};
+
+enum { NQ_OBS = 9, NQ_COOL = 4, RED_THREADS = 128 };
+
+int reduce_blocks(int V);  // number of per-block partial records for V sites
+
+// prec: 0 = FP64 links, 1 = FP32 links.  All pointers are device pointers;
+// link fields are SoA (see lattice.cuh), `partials` holds reduce_blocks(V)
+// records of NQ_* doubles.
+cudaError_t launch_cold(int prec, const GeoH& g, void* U, cudaStream_t st);
+cudaError_t launch_hot(int prec, const GeoH& g, void* U, uint64_t seed, cudaStream_t st);
+// Omega_x = exp(-sigma g_a lambda_a) per site (Philox stream 1) into Om/Omi.
+cudaError_t launch_gauge_omega(int prec, const GeoH& g, void* Om, void* Omi, uint64_t seed,
+                               double sigma, cudaStream_t st);
+cudaError_t launch_aos_to_soa(int prec, const GeoH& g, const double* aos, void* U, int nplanes,
+                              cudaStream_t st);
+cudaError_t launch_soa_to_aos(int prec, const GeoH& g, const void* U, double* aos, int nplanes,
+                              cudaStream_t st);
+// F^ = scale * F_{mu nu}(x), six planes.
+cudaError_t launch_clover(int prec, const GeoH& g, const void* U, void* F, double scale_re,
+                          double scale_im, cudaStream_t st);
+// One CL update (mode 0) or the drift matrix only (mode 1).
+cudaError_t launch_cl_update(int prec, bool theta, int mode, const GeoH& g, const void* U,
+                             const void* F, void* out, double beta, double eps, uint64_t seed,
+                             uint32_t step, cudaStream_t st);
+// Cooling: gradient f (8 per site) + partial sums; the rule; Omega; apply.
+cudaError_t launch_cool_grad(int prec, const GeoH& g, const void* U, void* f, double* partials,
+                             const CoolState* cs, cudaStream_t st);
+cudaError_t launch_cool_adapt(const GeoH& g, const double* partials, CoolArgs a, CoolState* cs,
+                              int first, cudaStream_t st);
+cudaError_t launch_cool_omega(int prec, const GeoH& g, const void* f, void* Om, void* Omi,
+                              double eps, const CoolState* cs, cudaStream_t st);
+cudaError_t launch_cool_apply(int prec, const GeoH& g, void* U, const void* Om, const void* Omi,
+                              const CoolState* cs, cudaStream_t st);
+// Observables: per-site pass (F must hold the unscaled clover field when
+// with_q) then the final fixed-order reduction into *out.
+cudaError_t launch_obs(int prec, const GeoH& g, const void* U, const void* F, int with_q,
+                       double* partials, double* q_site, cudaStream_t st);
+cudaError_t launch_obs_final(const GeoH& g, const double* partials, double beta, double th_re,
+                             double th_im, ObsOut* out, cudaStream_t st);
+
+}  // namespace clgc

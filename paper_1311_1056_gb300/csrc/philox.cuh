@@ -1,0 +1,80 @@
+// philox.cuh -- counter-based noise for the CL update and the random starts.
+//
+// Philox4x32-10 as published by Salmon, Moraes, Dror and Shaw, "Parallel
+// random numbers: as easy as 1, 2, 3" (SC'11): ten rounds of two 32x32->64
+// multiplies with the Weyl key schedule.  Keys and counters:
+//   key     = (seed & 0xffffffff, seed >> 32)
+//   counter = (site, step, slot | stream << 8, j)
+// stream 0 = CL noise (slot = mu), 1 = random gauge transformation (slot 0),
+// 2 = hot start (slot = mu).  Counter j gives one Box-Muller pair from the
+// uniforms u = (k + 1/2) 2^-52, k = (w0 >> 6) 2^26 + (w1 >> 6), which lie in (0,1).
+// The noise of a link is a function of (seed, step, site, mu) only, so a
+// replay, a CUDA graph or a different launch shape draws the same numbers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace clgc {
+
+enum { STREAM_CL = 0, STREAM_GAUGE = 1, STREAM_HOT = 2 };
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    uint32_t lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    uint32_t lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k.x, lo1, hi0 ^ c.w ^ k.y, lo0);
+    k.x += 0x9E3779B9u;
+    k.y += 0xBB67AE85u;
+  }
+  return c;
+}
+
+__device__ __forceinline__ double uniform52(uint32_t hi, uint32_t lo) {
+  double k = fma((double)(hi >> 6), 67108864.0, (double)(lo >> 6));
+  return (k + 0.5) * (1.0 / 4503599627370496.0);
+}
+
+__device__ __forceinline__ uint4 philox_words(uint64_t seed, uint32_t step, uint32_t site,
+                                              uint32_t slot, uint32_t stream, uint32_t j) {
+  return philox4x32_10(make_uint4(site, step, slot | (stream << 8), j),
+                       make_uint2((uint32_t)seed, (uint32_t)(seed >> 32)));
+}
+
+// 2*NP standard normal numbers, Box-Muller in FP64.
+template <int NP>
+__device__ __forceinline__ void normals_f64(double* g, uint64_t seed, uint32_t step, uint32_t site,
+                                            uint32_t slot, uint32_t stream) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    uint4 w = philox_words(seed, step, site, slot, stream, (uint32_t)j);
+    double u1 = uniform52(w.x, w.y), u2 = uniform52(w.z, w.w);
+    double rad = sqrt(-2.0 * log(u1));
+    double s, c;
+    sincospi(2.0 * u2, &s, &c);
+    g[2 * j] = rad * c;
+    g[2 * j + 1] = rad * s;
+  }
+}
+
+// The same numbers to float precision, with no FP64 instruction: the uniforms
+// keep the top 24 bits of the first word of each pair, u = (k + 1/2) 2^-24,
+// which agrees with the 52-bit uniform to float rounding.  Used by the
+// FP32-storage form, whose links carry FP32 precision anyway.
+template <int NP>
+__device__ __forceinline__ void normals_f32(float* g, uint64_t seed, uint32_t step, uint32_t site,
+                                            uint32_t slot, uint32_t stream) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    uint4 w = philox_words(seed, step, site, slot, stream, (uint32_t)j);
+    float u1 = ((float)(w.x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    float u2 = ((float)(w.z >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    float rad = sqrtf(-2.0f * logf(u1));
+    float s, c;
+    sincospif(2.0f * u2, &s, &c);
+    g[2 * j] = rad * c;
+    g[2 * j + 1] = rad * s;
+  }
+}
+
+}  // namespace clgc

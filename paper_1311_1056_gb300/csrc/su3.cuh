@@ -1,0 +1,196 @@
+// su3.cuh -- 3x3 complex matrix algebra for the CL / gauge-cooling kernels.
+//
+// Templated on the real type T (double for the FP64 form, float for the
+// FP32-storage form).  Every product is written as explicit fused
+// multiply-adds so the FP64 instruction count of a kernel can be read off the
+// code: a complex multiply-accumulate is 4 FMA, a 3x3 matrix product 108.
+//
+// Matrices are row-major, element k = 3*row + col.  Inverses of SL(3,C)
+// matrices are taken as adjugates (det = 1 is kept by the re-projection after
+// every CL update, Sec. 2: det U = 1 on SL(N,C)).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace clgc {
+
+template <typename T>
+struct cx {
+  T re, im;
+};
+
+template <typename T>
+struct mat {
+  cx<T> e[9];
+};
+
+template <typename T> struct vec2_of;
+template <> struct vec2_of<double> { typedef double2 type; };
+template <> struct vec2_of<float> { typedef float2 type; };
+
+template <typename T>
+__device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
+  cx<T> r;
+  r.re = a.re * b.re;
+  r.re = fma(-a.im, b.im, r.re);
+  r.im = a.re * b.im;
+  r.im = fma(a.im, b.re, r.im);
+  return r;
+}
+// acc + a*b
+template <typename T>
+__device__ __forceinline__ cx<T> cfma(cx<T> a, cx<T> b, cx<T> acc) {
+  acc.re = fma(a.re, b.re, acc.re);
+  acc.re = fma(-a.im, b.im, acc.re);
+  acc.im = fma(a.re, b.im, acc.im);
+  acc.im = fma(a.im, b.re, acc.im);
+  return acc;
+}
+// acc - a*b
+template <typename T>
+__device__ __forceinline__ cx<T> cfms(cx<T> a, cx<T> b, cx<T> acc) {
+  acc.re = fma(-a.re, b.re, acc.re);
+  acc.re = fma(a.im, b.im, acc.re);
+  acc.im = fma(-a.re, b.im, acc.im);
+  acc.im = fma(-a.im, b.re, acc.im);
+  return acc;
+}
+template <typename T>
+__device__ __forceinline__ cx<T> cadd(cx<T> a, cx<T> b) {
+  return cx<T>{a.re + b.re, a.im + b.im};
+}
+template <typename T>
+__device__ __forceinline__ cx<T> csub(cx<T> a, cx<T> b) {
+  return cx<T>{a.re - b.re, a.im - b.im};
+}
+
+template <typename T>
+__device__ __forceinline__ void set_zero(mat<T>& a) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) a.e[k] = cx<T>{T(0), T(0)};
+}
+template <typename T>
+__device__ __forceinline__ void set_ident(mat<T>& a) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) a.e[k] = cx<T>{(k % 4 == 0) ? T(1) : T(0), T(0)};
+}
+
+// c = a * b
+template <typename T>
+__device__ __forceinline__ void mul(mat<T>& c, const mat<T>& a, const mat<T>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<T> s = cmul(a.e[3 * i], b.e[j]);
+      s = cfma(a.e[3 * i + 1], b.e[3 + j], s);
+      s = cfma(a.e[3 * i + 2], b.e[6 + j], s);
+      c.e[3 * i + j] = s;
+    }
+}
+// c += a * b  (SIGN = +1) or c -= a * b (SIGN = -1)
+template <int SIGN, typename T>
+__device__ __forceinline__ void mul_acc(mat<T>& c, const mat<T>& a, const mat<T>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<T> s = c.e[3 * i + j];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        s = (SIGN > 0) ? cfma(a.e[3 * i + k], b.e[3 * k + j], s)
+                       : cfms(a.e[3 * i + k], b.e[3 * k + j], s);
+      c.e[3 * i + j] = s;
+    }
+}
+// c += s * a  (SIGN = +1) or c -= s * a, s real
+template <int SIGN, typename T>
+__device__ __forceinline__ void axpy(mat<T>& c, T s, const mat<T>& a) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    c.e[k].re = fma(SIGN > 0 ? s : -s, a.e[k].re, c.e[k].re);
+    c.e[k].im = fma(SIGN > 0 ? s : -s, a.e[k].im, c.e[k].im);
+  }
+}
+
+// Adjugate: adj(a) a = det(a) 1; for det a = 1 it is the inverse.
+template <typename T>
+__device__ __forceinline__ void adj(mat<T>& r, const mat<T>& a) {
+  const cx<T>* m = a.e;
+  r.e[0] = cfms(m[5], m[7], cmul(m[4], m[8]));
+  r.e[1] = cfms(m[1], m[8], cmul(m[2], m[7]));
+  r.e[2] = cfms(m[2], m[4], cmul(m[1], m[5]));
+  r.e[3] = cfms(m[3], m[8], cmul(m[5], m[6]));
+  r.e[4] = cfms(m[2], m[6], cmul(m[0], m[8]));
+  r.e[5] = cfms(m[0], m[5], cmul(m[2], m[3]));
+  r.e[6] = cfms(m[4], m[6], cmul(m[3], m[7]));
+  r.e[7] = cfms(m[0], m[7], cmul(m[1], m[6]));
+  r.e[8] = cfms(m[1], m[3], cmul(m[0], m[4]));
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> det(const mat<T>& a) {
+  const cx<T>* m = a.e;
+  cx<T> c0 = cfms(m[5], m[7], cmul(m[4], m[8]));
+  cx<T> c1 = cfms(m[3], m[8], cmul(m[5], m[6]));
+  cx<T> c2 = cfms(m[4], m[6], cmul(m[3], m[7]));
+  return cfma(m[2], c2, cfma(m[1], c1, cmul(m[0], c0)));
+}
+
+template <typename T>
+__device__ __forceinline__ cx<T> trace(const mat<T>& a) {
+  return cx<T>{a.e[0].re + a.e[4].re + a.e[8].re, a.e[0].im + a.e[4].im + a.e[8].im};
+}
+
+// Re Tr(a b) and Im Tr(a b) without forming the product.
+template <typename T>
+__device__ __forceinline__ cx<T> trace_mul(const mat<T>& a, const mat<T>& b) {
+  cx<T> s = cmul(a.e[0], b.e[0]);
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+      if (i + k > 0) s = cfma(a.e[3 * i + k], b.e[3 * k + i], s);
+  return s;
+}
+
+// sum_ij |a_ij|^2 = Tr a a^+
+template <typename T>
+__device__ __forceinline__ T norm2(const mat<T>& a) {
+  T s = T(0);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) s = fma(a.e[k].re, a.e[k].re, fma(a.e[k].im, a.e[k].im, s));
+  return s;
+}
+
+template <typename D, typename S>
+__device__ __forceinline__ void convert(mat<D>& d, const mat<S>& s) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) d.e[k] = cx<D>{(D)s.e[k].re, (D)s.e[k].im};
+}
+
+// SoA field access: element k of matrix (plane, site) at ((plane*9 + k)*V + site).
+template <typename T>
+__device__ __forceinline__ void load(mat<T>& a, const typename vec2_of<T>::type* __restrict__ f,
+                                     int plane, int site, int V) {
+  const typename vec2_of<T>::type* p = f + (size_t)plane * 9 * V + site;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    typename vec2_of<T>::type v = __ldg(p + (size_t)k * V);
+    a.e[k] = cx<T>{v.x, v.y};
+  }
+}
+template <typename T>
+__device__ __forceinline__ void store(typename vec2_of<T>::type* __restrict__ f, int plane,
+                                      int site, int V, const mat<T>& a) {
+  typename vec2_of<T>::type* p = f + (size_t)plane * 9 * V + site;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    typename vec2_of<T>::type v;
+    v.x = a.e[k].re;
+    v.y = a.e[k].im;
+    p[(size_t)k * V] = v;
+  }
+}
+
+}  // namespace clgc
