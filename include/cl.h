@@ -189,6 +189,37 @@ cl_status cl_synchronize(cl_lattice* lat);
 /* Release every device buffer of the lattice (NULL is ignored). */
 void cl_free(cl_lattice* lat);
 
+/* Observables of caller-owned device links with no device allocation.
+ *
+ * For callers that cannot allocate device memory: programs whose device
+ * memory belongs to their own pool or arena (every byte accounted for), and
+ * latency-critical loops that cannot afford cudaMalloc/cudaFree, which may
+ * synchronise the device.  The paper has no counterpart: this is a systems
+ * variant of cl_observables.
+ *
+ * dev_links: device AoS FP64 links (layout above, V*4*18 doubles), read only.
+ * L: extents, each >= 1, with V <= CL_NOALLOC_MAX_SITES (else CL_ERR_INVALID).
+ * dev_out: device, 10 doubles written in cl_obs field order (plaquette re/im,
+ *   unitarity norm, Q re/im, S_W re/im, S re/im, max |det U - 1|).
+ * cuda_stream: the stream to enqueue on (NULL = legacy default stream).
+ * Nothing is synchronised and no link value is checked for NaN/Inf.
+ *
+ * The per-block partial sums live in one fixed device array inside the
+ * library (CL_NOALLOC_MAX_BLOCKS records of 9 doubles, 147,456 bytes), which
+ * every GPU that loads the library holds until the process exits; launches
+ * use at most that many blocks, whatever V.  The first call on each device
+ * looks up the array's device address (cudaGetSymbolAddress), so make that
+ * first call before any stream capture.  All calls share the array: calls
+ * that overlap on the GPU (other streams or host threads) race on it.  Errors:
+ * CL_ERR_INVALID (NULL, extents, volume, device index beyond
+ * CL_NOALLOC_MAX_DEVICES), CL_ERR_CUDA; text in cl_last_error(). */
+#define CL_NOALLOC_MAX_BLOCKS 2048
+#define CL_NOALLOC_MAX_DEVICES 64
+#define CL_NOALLOC_MAX_SITES (1LL << 30)
+cl_status cl_observables_noalloc(const double* dev_links, const int L[4], double beta,
+                                 double theta_re, double theta_im, double* dev_out,
+                                 void* cuda_stream);
+
 const char* cl_status_str(cl_status s);
 /* Text of the last error on this host thread ("" if none). */
 const char* cl_last_error(void);

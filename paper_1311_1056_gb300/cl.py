@@ -86,6 +86,8 @@ SIGNATURES = {
     "cl_get_timing": (ctypes.c_int, [_P, _dp, ctypes.POINTER(ctypes.c_int64)]),
     "cl_synchronize": (ctypes.c_int, [_P]),
     "cl_free": (None, [_P]),
+    "cl_observables_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
+                                              ctypes.c_double, ctypes.c_double, _P, _P]),
     "cl_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "cl_last_error": (ctypes.c_char_p, []),
     "cl_version": (ctypes.c_int, []),
@@ -237,6 +239,16 @@ def cl_synchronize(lat):
 def cl_free(lat):
     if lat:
         load().cl_free(lat)
+
+
+def cl_observables_noalloc(dev_links, L, beta, theta, dev_out, stream=0):
+    """Observables of caller-owned device links (float64 AoS, 2*V*4*9 values)
+    into caller-owned device memory (10 float64), with no device allocation
+    in the library; enqueued on `stream`, nothing synchronised."""
+    theta = complex(theta)
+    Larr = (ctypes.c_int * 4)(*[int(v) for v in L])
+    _check(load().cl_observables_noalloc(_P(dev_links), Larr, beta, theta.real, theta.imag,
+                                         _P(dev_out), _P(stream or None)), "cl_observables_noalloc")
 
 
 def cl_status_str(s):

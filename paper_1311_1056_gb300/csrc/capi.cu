@@ -34,6 +34,11 @@ cl_status fail(cl_status s, const std::string& msg) {
 
 }  // namespace
 
+namespace clgc {
+// Error text for entry points defined in other translation units.
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace clgc
+
 struct cl_lattice {
   cl_params p;
   GeoH g;
