@@ -106,7 +106,9 @@ typedef struct {
 /* Create a lattice on the current CUDA device and initialise its links
  * (start, then the optional random gauge transformation).  cuda_stream is a
  * cudaStream_t (may be NULL).  On success *out owns the device memory
- * (about V * (2 link fields + clover field + cooling scratch) bytes).
+ * (per site: 64 complex 3x3 matrices -- links, a second link buffer,
+ * inverses, plaquettes, their differences, the clover field and the drift
+ * contributions -- plus cooling scratch: 9.4 KB in FP64, 4.7 KB in FP32).
  * Errors: CL_ERR_INVALID (NULL, extents < 1, V*6*9 beyond int range),
  * CL_ERR_OOM, CL_ERR_CUDA. */
 cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice** out);
@@ -170,14 +172,15 @@ cl_status cl_qdensity(cl_lattice* lat, double* host_q);
  * (arrays of CL_NPHASE entries, either may be NULL).  Timing adds two event
  * records per launch and is off by default. */
 enum {
-  CL_PHASE_CLOVER = 0,     /* clover field of the theta drift */
-  CL_PHASE_UPDATE = 1,     /* drift + noise + exponential update */
+  CL_PHASE_CLOVER = 0,     /* link inverses, plaquettes, clover field */
+  CL_PHASE_UPDATE = 1,     /* drift gather + noise + exponential update */
   CL_PHASE_COOL_GRAD = 2,  /* cooling gradient f_ax + partial sums */
   CL_PHASE_COOL_RULE = 3,  /* adaptive rule (one block) */
   CL_PHASE_COOL_OMEGA = 4, /* Omega_x, Omega_x^{-1} */
   CL_PHASE_COOL_APPLY = 5, /* U <- Omega U Omega^{-1} */
   CL_PHASE_OBS = 6,        /* observables */
-  CL_NPHASE = 7
+  CL_PHASE_FORCE = 7,      /* per-plaquette drift contributions */
+  CL_NPHASE = 8
 };
 cl_status cl_set_timing(cl_lattice* lat, int on);
 cl_status cl_get_timing(cl_lattice* lat, double* ms, int64_t* launches);

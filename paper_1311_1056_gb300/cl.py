@@ -218,7 +218,7 @@ def cl_launch_count(lat):
     return v.value
 
 
-PHASES = ("clover", "update", "cool_grad", "cool_rule", "cool_omega", "cool_apply", "obs")
+PHASES = ("clover", "update", "cool_grad", "cool_rule", "cool_omega", "cool_apply", "obs", "force")
 
 
 def cl_set_timing(lat, on):

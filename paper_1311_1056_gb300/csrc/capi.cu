@@ -47,6 +47,10 @@ struct cl_lattice {
   cudaStream_t st;
   void* U;     // links, SoA [4][9][V]
   void* Un;    // second link buffer (CL update target)
+  void* Ui;    // link inverses [4][9][V]
+  void* Pq;    // plaquettes [6][9][V]
+  void* Dq;    // P - P^{-1} [6][9][V]
+  void* C;     // per-plaquette drift contributions [24][9][V]
   void* F;     // clover field, SoA [6][9][V]
   void* f;     // cooling gradient [8][V] (real)
   void* Om;    // packed Hermitian Omega [9][V]
@@ -121,15 +125,32 @@ cl_status ensure_stage(cl_lattice* l) {
 
 bool theta_nonzero(const cl_lattice* l) { return l->p.theta_re != 0.0 || l->p.theta_im != 0.0; }
 
+// Link inverses, plaquettes and D = P - P^{-1}, then (theta != 0) the clover
+// field scaled by (sre + i sim), then the per-plaquette drift contributions.
+cudaError_t do_force(cl_lattice* l, bool th, double sre, double sim) {
+  cudaError_t e = timed(l, CL_PHASE_CLOVER, [&] { return launch_link_inverse(l->prec, l->g, l->U, l->Ui, l->st); });
+  if (e == cudaSuccess)
+    e = timed(l, CL_PHASE_CLOVER, [&] { return launch_plaq(l->prec, l->g, l->U, l->Ui, l->Pq, l->Dq, l->st); });
+  if (e == cudaSuccess && th)
+    e = timed(l, CL_PHASE_CLOVER, [&] {
+      return launch_clover_rot(l->prec, l->g, l->U, l->Ui, l->Dq, l->F, sre, sim, l->st);
+    });
+  if (e == cudaSuccess)
+    e = timed(l, CL_PHASE_FORCE, [&] {
+      return launch_plaq_force(l->prec, th, l->g, l->U, l->Ui, l->Pq, l->Dq, l->F, l->C, l->p.beta, l->st);
+    });
+  return e;
+}
+
 cl_status do_steps(cl_lattice* l, double eps, int n) {
   const bool th = theta_nonzero(l);
   // F^ = -i theta kappa F: -i (a + ib) kappa = kappa b - i kappa a
   const double sre = KAPPA_Q * l->p.theta_im, sim = -KAPPA_Q * l->p.theta_re;
   for (int i = 0; i < n; ++i) {
-    if (th) CK(timed(l, CL_PHASE_CLOVER, [&] { return launch_clover(l->prec, l->g, l->U, l->F, sre, sim, l->st); }));
+    CK(do_force(l, th, sre, sim));
     CK(timed(l, CL_PHASE_UPDATE, [&] {
-      return launch_cl_update(l->prec, th, 0, l->g, l->U, l->F, l->Un, l->p.beta, eps, l->p.seed,
-                              (uint32_t)l->step, l->st);
+      return launch_update_gather(l->prec, 0, l->g, l->U, l->C, l->Un, eps, l->p.seed,
+                                  (uint32_t)l->step, l->st);
     }));
     std::swap(l->U, l->Un);
     l->step++;
@@ -182,7 +203,9 @@ cl_status do_cool(cl_lattice* l, const cl_cool_params* cp) {
 }
 
 cl_status do_obs(cl_lattice* l, ObsOut* dst, double* q_site) {
-  CK(timed(l, CL_PHASE_OBS, [&] { return launch_clover(l->prec, l->g, l->U, l->F, 1.0, 0.0, l->st); }));
+  CK(timed(l, CL_PHASE_OBS, [&] { return launch_link_inverse(l->prec, l->g, l->U, l->Ui, l->st); }));
+  CK(timed(l, CL_PHASE_OBS, [&] { return launch_plaq(l->prec, l->g, l->U, l->Ui, l->Pq, l->Dq, l->st); }));
+  CK(timed(l, CL_PHASE_OBS, [&] { return launch_clover_rot(l->prec, l->g, l->U, l->Ui, l->Dq, l->F, 1.0, 0.0, l->st); }));
   CK(timed(l, CL_PHASE_OBS, [&] { return launch_obs(l->prec, l->g, l->U, l->F, 1, l->partials, q_site, l->st); }));
   CK(timed(l, CL_PHASE_OBS, [&] {
     return launch_obs_final(l->g, l->partials, l->p.beta, l->p.theta_re, l->p.theta_im, dst, l->st);
@@ -248,6 +271,10 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
   const size_t Vs = (size_t)V;
   alloc(&l->U, l->esz * 4 * 9 * Vs);
   alloc(&l->Un, l->esz * 4 * 9 * Vs);
+  alloc(&l->Ui, l->esz * 4 * 9 * Vs);
+  alloc(&l->Pq, l->esz * 6 * 9 * Vs);
+  alloc(&l->Dq, l->esz * 6 * 9 * Vs);
+  alloc(&l->C, l->esz * 24 * 9 * Vs);
   alloc(&l->F, l->esz * 6 * 9 * Vs);
   alloc(&l->f, real_size(l) * 8 * Vs);
   alloc(&l->Om, real_size(l) * 9 * Vs);
@@ -426,12 +453,8 @@ cl_status cl_drift(cl_lattice* l, double* host_aos) {
   cl_status s = ensure_stage(l);
   if (s != CL_OK) return s;
   const bool th = theta_nonzero(l);
-  if (th) {
-    CK(launch_clover(l->prec, l->g, l->U, l->F, KAPPA_Q * l->p.theta_im, -KAPPA_Q * l->p.theta_re, l->st));
-    l->launches++;
-  }
-  CK(launch_cl_update(l->prec, th, 1, l->g, l->U, l->F, l->Un, l->p.beta, 0.0, l->p.seed,
-                      (uint32_t)l->step, l->st));
+  CK(do_force(l, th, KAPPA_Q * l->p.theta_im, -KAPPA_Q * l->p.theta_re));
+  CK(launch_update_gather(l->prec, 1, l->g, l->U, l->C, l->Un, 0.0, l->p.seed, (uint32_t)l->step, l->st));
   CK(launch_soa_to_aos(l->prec, l->g, l->Un, l->stage, 4, l->st));
   l->launches += 2;
   CK(cudaMemcpyAsync(host_aos, l->stage, sizeof(double) * 18 * 4 * (size_t)l->g.V,
@@ -503,7 +526,7 @@ cl_status cl_synchronize(cl_lattice* l) {
 
 void cl_free(cl_lattice* l) {
   if (!l) return;
-  void* bufs[] = {l->U, l->Un, l->F, l->f, l->Om, l->Omi, l->partials, l->cs, l->obs,
+  void* bufs[] = {l->U, l->Un, l->Ui, l->Pq, l->Dq, l->C, l->F, l->f, l->Om, l->Omi, l->partials, l->cs, l->obs,
                   l->stage, l->qsite};
   if (l->st) cudaStreamSynchronize(l->st);
   for (void* b : bufs)

@@ -1,28 +1,31 @@
-// k_update.cuh -- the CL step: Wilson staple drift + clover theta drift,
-// Philox noise, FP64 exponential update and det re-projection, one thread
-// per link.
+// k_update.cuh -- the CL step: plaquettes, clover field, per-plaquette drift
+// contributions, and the per-link gather + noise + FP64 exponential update
+// with det re-projection.
 //
 // Action (Sec. 5, eq. "eq:st"): S = S_W - i theta sum_x q_L(x) with the
 // Wilson action continued holomorphically (U^+ -> U^{-1}) and
 //   q_L(x) = kappa [Tr F01 F23 - Tr F02 F13 + Tr F03 F12](x),  kappa = -1/(256 pi^2),
 // where F_{mu nu}(x) = sum over the four clover leaves L at x of (L - L^{-1})
-// (this is the paper's signed eps-tilde sum regrouped by plane).
+// (the paper's signed eps-tilde sum regrouped by plane).
 //
-// Drift matrix X_S of link l = (x, mu), defined by D_a S = i Tr(lambda_a X_S)
-// with D_a the left derivative U -> exp(i a lambda_a) U.  For each of the six
-// plaquettes through l written as P = U_l w1 w2 w3 (sgn = +1: the one based
-// at x in the (mu, nu) plane, sgn = -1: the one based at x - nu), with corners
-// c0 = x, c1 = x+mu, c2, c3 in the order of the loop:
-//   Wilson:  X += -(beta/6) (U_l W - W^{-1} U_l^{-1}),  W = w1 w2 w3
-//   theta :  X += sigma [U_l T1 + T2 U_l^{-1}] with G_k = F^(c_k) of the
-//            complementary plane (F^ = -i theta kappa F, done by the clover
-//            kernel) and
-//     T1 = W G0 + G1 W + w1 G2 w2 w3 + w1 w2 G3 w3
-//     T2 = G0 W^{-1} + W^{-1} G1 + (w2 w3)^{-1} G2 w1^{-1} + w3^{-1} G3 (w1 w2)^{-1}
-//   sigma = sgn * (pair sign: +1, -1, +1 for 01|23, 02|13, 03|12)
-//               * (+1 if mu < nu, else -1: F_{nu mu} = -F_{mu nu}).
-// T1 and T2 are the product rule for the leaf (and its inverse) at each
-// corner with the dual field inserted at that corner.
+// Drift matrix X_S of a link, D_a S = i Tr(lambda_a X_S), D_a the left
+// derivative U -> exp(i a lambda_a) U.  Every term of S is a function of
+// plaquettes, so X_S is a sum over the six plaquettes through the link, and
+// each plaquette serves its four links at once.  For the plaquette based at x
+// in plane (mu < nu), P = a b c d with a = U_mu(x), b = U_nu(x+mu),
+// c = U_mu(x+nu)^{-1}, d = U_nu(x)^{-1} = u^{-1}, corners c0 = x, c1 = x+mu,
+// c2 = x+mu+nu, c3 = x+nu, D = P - P^{-1}, and the dual fields
+// G_k = s F^_{comp}(c_k) (F^ = -i theta kappa F, s = +1, -1, +1 for the pairs
+// 01|23, 02|13, 03|12) carried to c0:
+//   G1^ = a G1 a^{-1}, G2^ = (ab) G2 (ab)^{-1}, G3r = u G3 u^{-1}, G3^ = P G3r P^{-1},
+//   G^ = G0 + G1^ + G2^ + G3^,   K = G^ P + P^{-1} G^,   [A, B] = AB - BA,
+// the product rule over the four leaves of the plaquette (one per corner) and
+// the Wilson term -(beta/6) Tr(P + P^{-1}) give, each in its own link's frame,
+//   U_mu(x)    : K + [D, G0] - (beta/6) D
+//   U_nu(x)    : -K + (beta/6) D
+//   U_nu(x+mu) : a^{-1} (K + [D, G0] + [D, G1^] - (beta/6) D) a
+//   U_mu(x+nu) : u^{-1} (-K + [D, G3r] + (beta/6) D) u
+// (about 22 matrix products per plaquette for all four links).
 //
 // Update (the CL step of the method, Sec. 2 and its refs):
 //   K_a = -D_a S,  A = i lambda_a (eps K_a + sqrt(eps) eta_a)
@@ -44,21 +47,7 @@ struct UpdArgs {
   uint32_t step;
 };
 
-// Raw link or its inverse (adjugate), whichever the loop needs.
-template <typename T>
-__device__ __forceinline__ void load_link(mat<T>& m, const typename vec2_of<T>::type* U, int mu,
-                                          int s, int V, bool inverse) {
-  if (inverse) {
-    mat<T> t;
-    load(t, U, mu, s, V);
-    adj(m, t);
-  } else {
-    load(m, U, mu, s, V);
-  }
-}
-
-// Sign flip on the integer pipe (no FP64 instruction): every theta term
-// contains exactly one factor G, so sigma = -1 is applied by negating G.
+// Sign flip on the integer pipe (no floating-point instruction).
 __device__ __forceinline__ double flip(double x, unsigned long long m) {
   return __longlong_as_double(__double_as_longlong(x) ^ (long long)m);
 }
@@ -76,95 +65,257 @@ __device__ __forceinline__ void load_signed(mat<T>& G, const typename vec2_of<T>
   }
 }
 
-// The products are regrouped to share factors (a23 = w2 w3, i23 = a23^{-1}):
-//   T1 = w1 Y + G1 W,       Y = a23 G0 + G2 a23 + w2 (G3 w3)
-//   T2 = Z w1^{-1} + W^{-1} G1,  Z = G0 i23 + i23 G2 + (w3^{-1} G3) w2^{-1}
-// so that U_l T1 + T2 U_l^{-1} is accumulated as S1 += T1, S2 += T2 and
-// X = U_l S1 + S2 U_l^{-1} at the end (14 matrix products per plaquette).
-// The six plaquettes run as a loop (not unrolled): one body's working set
-// fits the register file; unrolled, the FP64 form spills tens of KB.
-template <typename T, bool THETA>
-__device__ __forceinline__ void drift_matrix(mat<T>& X, mat<T>& Ul, const Geo& g, int s,
-                                             const int x[4], const int mu,
-                                             const typename vec2_of<T>::type* __restrict__ U,
-                                             const typename vec2_of<T>::type* __restrict__ F,
-                                             T beta6) {
-  mat<T> S1, S2;
-  set_zero(S1);
-  set_zero(S2);
-  const int c1 = hop(g, s, x, mu, +1);
-#pragma unroll 1
-  for (int pl = 0; pl < 6; ++pl) {
-    const int nu = (pl >> 1) + ((pl >> 1) >= mu ? 1 : 0);
-    const int sgn = (pl & 1) ? -1 : 1;
-    const int p = mu < nu ? plane_index(mu, nu) : plane_index(nu, mu);
-    const int pc = 5 - p;
-    const int sigma = sgn * ((p == 1 || p == 4) ? -1 : 1) * (mu < nu ? 1 : -1);
-    const unsigned long long m = sigma < 0 ? 0x8000000000000000ull : 0ull;
-    const int c2 = hop(g, c1, x, nu, sgn);
-    const int c3 = hop(g, s, x, nu, sgn);
-    // loop from x: U_l, w1 to c2, w2 to c3, w3 back to x
-    //   sgn = +1: w1 = U_nu(x+mu), w2 = U_mu(x+nu)^{-1}, w3 = U_nu(x)^{-1}
-    //   sgn = -1: w1 = U_nu(x+mu-nu)^{-1}, w2 = U_mu(x-nu)^{-1}, w3 = U_nu(x-nu)
-    const int w1site = sgn > 0 ? c1 : c2, w3site = sgn > 0 ? s : c3;
-    mat<T> a23, i23, Y, G, t;
-    {
-      mat<T> w2, w3;
-      load_link(w2, U, mu, c3, g.V, true);
-      load_link(w3, U, nu, w3site, g.V, sgn > 0);
-      mul(a23, w2, w3);
-      if (THETA) {
-        load_signed(G, F, pc, s, g.V, m);
-        mul(Y, a23, G);
-        load_signed(G, F, pc, c2, g.V, m);
-        mul_acc<+1>(Y, G, a23);
-        load_signed(G, F, pc, c3, g.V, m);
-        mul(t, G, w3);
-        mul_acc<+1>(Y, w2, t);
-      }
-    }
-    {
-      mat<T> w1, W, Wi;
-      load_link(w1, U, nu, w1site, g.V, sgn < 0);
-      mul(W, w1, a23);
-      if (THETA) adj(i23, a23);
-      if (THETA) mul_acc<+1>(S1, w1, Y);
-      adj(Wi, W);
-      axpy<-1>(S1, beta6, W);
-      axpy<+1>(S2, beta6, Wi);
-      if (THETA) {
-        load_signed(G, F, pc, c1, g.V, m);
-        mul_acc<+1>(S1, G, W);
-        mul_acc<+1>(S2, Wi, G);
-      }
-    }
-    if (THETA) {
-      mat<T>& Z = Y;
-      load_signed(G, F, pc, s, g.V, m);
-      mul(Z, G, i23);
-      load_signed(G, F, pc, c2, g.V, m);
-      mul_acc<+1>(Z, i23, G);
-      {
-        mat<T> w3i;
-        load_link(w3i, U, nu, w3site, g.V, sgn < 0);
-        load_signed(G, F, pc, c3, g.V, m);
-        mul(t, w3i, G);
-      }
-      {
-        mat<T> w2i;
-        load_link(w2i, U, mu, c3, g.V, false);
-        mul_acc<+1>(Z, t, w2i);
-      }
-      mat<T>& w1i = t;
-      load_link(w1i, U, nu, w1site, g.V, sgn > 0);
-      mul_acc<+1>(S2, Z, w1i);
-    }
+// Plain (coherent) loads, for data this kernel itself wrote.
+template <typename T>
+__device__ __forceinline__ void load_rw(mat<T>& a, const typename vec2_of<T>::type* f, int plane,
+                                        int site, int V) {
+  const typename vec2_of<T>::type* p = f + (size_t)plane * 9 * V + site;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    typename vec2_of<T>::type v = p[(size_t)k * V];
+    a.e[k] = cx<T>{v.x, v.y};
   }
-  load(Ul, U, mu, s, g.V);
-  mat<T> Uli;
-  adj(Uli, Ul);
-  mul(X, Ul, S1);
-  mul_acc<+1>(X, S2, Uli);
+}
+
+// c += [a, b] = a b - b a
+template <typename T>
+__device__ __forceinline__ void commutator_acc(mat<T>& c, const mat<T>& a, const mat<T>& b) {
+  mul_acc<+1>(c, a, b);
+  mul_acc<-1>(c, b, a);
+}
+
+template <typename T>
+__device__ __forceinline__ void scaled(mat<T>& r, T c, const mat<T>& a) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    r.e[k].re = c * a.e[k].re;
+    r.e[k].im = c * a.e[k].im;
+  }
+}
+
+// ---------------------------------------------------------------- inverses
+// Ui = adj(U) = U^{-1} for every link (det U = 1 by the re-projection).
+template <typename T>
+__global__ void __launch_bounds__(128) k_link_inverse(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                      typename vec2_of<T>::type* __restrict__ Ui) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  mat<T> u, ui;
+  load(u, U, blockIdx.y, s, g.V);
+  adj(ui, u);
+  store(Ui, blockIdx.y, s, g.V, ui);
+}
+
+// ------------------------------------------------------------- plaquettes
+// P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^{-1} U_nu(x)^{-1} and
+// D = P - P^{-1}, six planes per site.
+template <typename T>
+__global__ void __launch_bounds__(128) k_plaq(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                              const typename vec2_of<T>::type* __restrict__ Ui,
+                                              typename vec2_of<T>::type* __restrict__ Pq,
+                                              typename vec2_of<T>::type* __restrict__ Dq) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int p = blockIdx.y, mu = plane_mu(p), nu = plane_nu(p);
+  int x[4];
+  site_coords(g, s, x);
+  mat<T> a, b, A, B, P;
+  load(a, U, mu, s, g.V);
+  load(b, U, nu, hop(g, s, x, mu, 1), g.V);
+  mul(A, a, b);
+  load(a, Ui, mu, hop(g, s, x, nu, 1), g.V);
+  load(b, Ui, nu, s, g.V);
+  mul(B, a, b);
+  mul(P, A, B);
+  store(Pq, p, s, g.V, P);
+  adj(A, P);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) P.e[k] = csub(P.e[k], A.e[k]);
+  store(Dq, p, s, g.V, P);
+}
+
+// ------------------------------------------------------------ clover field
+// F_{mu nu}(x) = sum of (L - L^{-1}) over the four leaves at x; each leaf is a
+// neighbouring plaquette carried to x:
+//   L1 = P(x),  L2 = U_mu(x-mu)^{-1} P(x-mu) U_mu(x-mu),
+//   L4 = U_nu(x-nu)^{-1} P(x-nu) U_nu(x-nu),
+//   L3 = W^{-1} P(x-mu-nu) W with W = U_mu(x-mu-nu) U_nu(x-nu),
+// so F = D(x) + the three carried D's.  Stored times a complex scale.
+template <typename T>
+__global__ void __launch_bounds__(128) k_clover_rot(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                    const typename vec2_of<T>::type* __restrict__ Ui,
+                                                    const typename vec2_of<T>::type* __restrict__ Dq,
+                                                    typename vec2_of<T>::type* __restrict__ F,
+                                                    double sre, double sim) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int p = blockIdx.y, mu = plane_mu(p), nu = plane_nu(p);
+  int x[4];
+  site_coords(g, s, x);
+  const int xmm = hop(g, s, x, mu, -1), xmn = hop(g, s, x, nu, -1);
+  const int xmm_mn = hop2(g, s, x, mu, -1, nu, -1);
+  mat<T> acc, w, wi, d, t;
+  load(acc, Dq, p, s, g.V);
+  // L2
+  load(wi, Ui, mu, xmm, g.V);
+  load(d, Dq, p, xmm, g.V);
+  mul(t, wi, d);
+  load(w, U, mu, xmm, g.V);
+  mul_acc<+1>(acc, t, w);
+  // L4
+  load(wi, Ui, nu, xmn, g.V);
+  load(d, Dq, p, xmn, g.V);
+  mul(t, wi, d);
+  load(w, U, nu, xmn, g.V);
+  mul_acc<+1>(acc, t, w);
+  // L3
+  {
+    mat<T> a, b;
+    load(a, Ui, nu, xmn, g.V);
+    load(b, Ui, mu, xmm_mn, g.V);
+    mul(wi, a, b);
+    load(d, Dq, p, xmm_mn, g.V);
+    mul(t, wi, d);
+    load(a, U, mu, xmm_mn, g.V);
+    load(b, U, nu, xmn, g.V);
+    mul(w, a, b);
+    mul_acc<+1>(acc, t, w);
+  }
+  cx<T> sc = {(T)sre, (T)sim};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc.e[k] = cmul(acc.e[k], sc);
+  store(F, p, s, g.V, acc);
+}
+
+// ----------------------------------------------------- plaquette drift
+// Contributions of the plaquette (x, p) to its four links, into
+// C[4p + slot]: slot 0 U_mu(x), 1 U_nu(x), 2 U_nu(x+mu), 3 U_mu(x+nu).
+// Partial sums are parked in the output slots and completed once K is known
+// (the thread re-reads only what it wrote itself).
+template <typename T, bool THETA>
+__global__ void __launch_bounds__(128) k_plaq_force(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                    const typename vec2_of<T>::type* __restrict__ Ui,
+                                                    const typename vec2_of<T>::type* __restrict__ Pq,
+                                                    const typename vec2_of<T>::type* __restrict__ Dq,
+                                                    const typename vec2_of<T>::type* __restrict__ F,
+                                                    typename vec2_of<T>::type* C, T beta6) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int p = blockIdx.y, mu = plane_mu(p), nu = plane_nu(p), pc = 5 - p;
+  const unsigned long long m = (p == 1 || p == 4) ? 0x8000000000000000ull : 0ull;
+  int x[4];
+  site_coords(g, s, x);
+  const int c1 = hop(g, s, x, mu, 1), c3 = hop(g, s, x, nu, 1);
+  mat<T> D, M, t;
+  load(D, Dq, p, s, g.V);
+  if (!THETA) {
+    mat<T> a;
+    scaled(M, -beta6, D);
+    store(C, 4 * p + 0, s, g.V, M);
+    load(a, Ui, mu, s, g.V);
+    mul(t, a, M);
+    load(a, U, mu, s, g.V);
+    mul(M, t, a);
+    store(C, 4 * p + 2, s, g.V, M);
+    scaled(M, beta6, D);
+    store(C, 4 * p + 1, s, g.V, M);
+    load(a, Ui, nu, s, g.V);
+    mul(t, a, M);
+    load(a, U, nu, s, g.V);
+    mul(M, t, a);
+    store(C, 4 * p + 3, s, g.V, M);
+    return;
+  }
+  mat<T> Gh, G, q;
+  // corner c0: slot 0 partial = [D, G0] - (beta/6) D
+  load_signed(Gh, F, pc, s, g.V, m);
+  scaled(M, -beta6, D);
+  commutator_acc(M, D, Gh);
+  store(C, 4 * p + 0, s, g.V, M);
+  // corner c1: G1^ = a G1 a^{-1}; slot 2 partial (c0 frame) = slot 0 partial + [D, G1^]
+  {
+    mat<T> a;
+    load_signed(G, F, pc, c1, g.V, m);
+    load(a, U, mu, s, g.V);
+    mul(t, a, G);
+    load(a, Ui, mu, s, g.V);
+    mul(q, t, a);
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Gh.e[k] = cadd(Gh.e[k], q.e[k]);
+  commutator_acc(M, D, q);
+  store(C, 4 * p + 2, s, g.V, M);
+  // corner c2: G2^ = (ab) G2 (ab)^{-1}
+  {
+    mat<T> a, b, ab;
+    load(a, U, mu, s, g.V);
+    load(b, U, nu, c1, g.V);
+    mul(ab, a, b);
+    load_signed(G, F, pc, hop(g, c1, x, nu, 1), g.V, m);
+    mul(t, ab, G);
+    load(a, Ui, mu, s, g.V);
+    load(b, Ui, nu, c1, g.V);
+    mul(ab, b, a);
+    mul_acc<+1>(Gh, t, ab);
+  }
+  // corner c3: G3r = u G3 u^{-1}, G3^ = P G3r P^{-1}; slot 3 partial = [D, G3r] + (beta/6) D
+  {
+    mat<T> u;
+    load_signed(G, F, pc, c3, g.V, m);
+    load(u, U, nu, s, g.V);
+    mul(t, u, G);
+    load(u, Ui, nu, s, g.V);
+    mul(q, t, u);
+  }
+  scaled(M, beta6, D);
+  commutator_acc(M, D, q);
+  store(C, 4 * p + 3, s, g.V, M);
+  mat<T> P, Pi;
+  load(P, Pq, p, s, g.V);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Pi.e[k] = csub(P.e[k], D.e[k]);
+  mul(t, P, q);
+  mul_acc<+1>(Gh, t, Pi);
+  // K = G^ P + P^{-1} G^
+  mat<T>& K = q;
+  mul(K, Gh, P);
+  mul_acc<+1>(K, Pi, Gh);
+  // slot 1: -K + (beta/6) D
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    M.e[k].re = fma(beta6, D.e[k].re, -K.e[k].re);
+    M.e[k].im = fma(beta6, D.e[k].im, -K.e[k].im);
+  }
+  store(C, 4 * p + 1, s, g.V, M);
+  // slot 0: K + partial
+  load_rw(M, C, 4 * p + 0, s, g.V);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) M.e[k] = cadd(M.e[k], K.e[k]);
+  store(C, 4 * p + 0, s, g.V, M);
+  // slot 2: a^{-1} (K + partial) a
+  {
+    mat<T> a;
+    load_rw(M, C, 4 * p + 2, s, g.V);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) M.e[k] = cadd(M.e[k], K.e[k]);
+    load(a, Ui, mu, s, g.V);
+    mul(t, a, M);
+    load(a, U, mu, s, g.V);
+    mul(M, t, a);
+    store(C, 4 * p + 2, s, g.V, M);
+  }
+  // slot 3: u^{-1} (-K + partial) u
+  {
+    mat<T> u;
+    load_rw(M, C, 4 * p + 3, s, g.V);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) M.e[k] = csub(M.e[k], K.e[k]);
+    load(u, Ui, nu, s, g.V);
+    mul(t, u, M);
+    load(u, U, nu, s, g.V);
+    mul(M, t, u);
+    store(C, 4 * p + 3, s, g.V, M);
+  }
 }
 
 // Noise matrix sum_a eta_a lambda_a (Hermitian) into the imaginary part of A,
@@ -185,15 +336,34 @@ __device__ __forceinline__ void add_noise(mat<double>& A, const double* e, doubl
   A.e[7].re = fma(-se, e[6], A.e[7].re); A.e[7].im = fma(se, e[5], A.e[7].im);
 }
 
-template <typename T, bool THETA, int MODE>
-__device__ __forceinline__ void cl_link(const Geo& g, int s, const int MU,
-                                        const typename vec2_of<T>::type* U,
-                                        const typename vec2_of<T>::type* F,
-                                        typename vec2_of<T>::type* out, const UpdArgs& a) {
+// ------------------------------------------------ gather + exponential update
+// X of link (x, mu) = sum of its six plaquette contributions: for nu != mu,
+// mu < nu: slot 0 of (x, p) and slot 3 of (x - nu, p); mu > nu: slot 1 of
+// (x, p) and slot 2 of (x - nu, p), p the plane of (mu, nu).
+template <typename T, int MODE>
+__global__ void __launch_bounds__(128) k_update_gather(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                       const typename vec2_of<T>::type* __restrict__ C,
+                                                       typename vec2_of<T>::type* __restrict__ out,
+                                                       UpdArgs a) {
+  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  const int MU = blockIdx.y;
   int x[4];
   site_coords(g, s, x);
-  mat<T> X, Ul;
-  drift_matrix<T, THETA>(X, Ul, g, s, x, MU, U, F, (T)(a.beta / 6.0));
+  mat<T> X, t;
+  set_zero(X);
+#pragma unroll
+  for (int nu = 0; nu < 4; ++nu) {
+    if (nu == MU) continue;
+    const int p = MU < nu ? plane_index(MU, nu) : plane_index(nu, MU);
+    const int sl_here = MU < nu ? 0 : 1, sl_back = MU < nu ? 3 : 2;
+    load(t, C, 4 * p + sl_here, s, g.V);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X.e[k] = cadd(X.e[k], t.e[k]);
+    load(t, C, 4 * p + sl_back, hop(g, s, x, nu, -1), g.V);
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X.e[k] = cadd(X.e[k], t.e[k]);
+  }
   if (MODE == MODE_DRIFT) {
     store(out, MU, s, g.V, X);
     return;
@@ -222,8 +392,9 @@ __device__ __forceinline__ void cl_link(const Geo& g, int s, const int MU,
   add_noise(A, eta, a.sqrt_eps * 1.41421356237309504880);  // eta = sqrt(2) * normal
   mat<double> E;
   expm_traceless(E, A);
-  mat<T> Et, Un;
+  mat<T> Et, Ul, Un;
   convert(Et, E);
+  load(Ul, U, MU, s, g.V);
   mul(Un, Et, Ul);
   mat<double> Und;
   convert(Und, Un);
@@ -232,16 +403,6 @@ __device__ __forceinline__ void cl_link(const Geo& g, int s, const int MU,
 #pragma unroll
   for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], zt);
   store(out, MU, s, g.V, Un);
-}
-
-template <typename T, bool THETA, int MODE>
-__global__ void __launch_bounds__(128) k_cl_update(Geo g, const typename vec2_of<T>::type* __restrict__ U,
-                                                   const typename vec2_of<T>::type* __restrict__ F,
-                                                   typename vec2_of<T>::type* __restrict__ out,
-                                                   UpdArgs a) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.V) return;
-  cl_link<T, THETA, MODE>(g, s, (int)blockIdx.y, U, F, out, a);
 }
 
 }  // namespace clgc

@@ -1,45 +1,99 @@
-// k_update_f64.cu -- instantiation of the CL update kernel for double links.
+// k_update_f64.cu -- the CL-step kernels (k_update.cuh) for double links.
 #include "k_update.cuh"
 #include "launch.h"
 
 namespace clgc {
 
-cudaError_t launch_cl_update_f64(bool theta, int mode, const GeoH& h, const void* U, const void* F,
-                                void* out, double beta, double eps, uint64_t seed, uint32_t step,
-                                cudaStream_t st) {
-  typedef vec2_of<double>::type V2;
+namespace {
+typedef vec2_of<double>::type V2;
+inline dim3 grid(int V, int planes) { return dim3((unsigned)((V + 127) / 128), (unsigned)planes); }
+}  // namespace
+
+cudaError_t launch_link_inverse_f64(const GeoH& h, const void* U, void* Ui, cudaStream_t st) {
+  Geo g = make_geo(h.L, h.V);
+  k_link_inverse<double><<<grid(g.V, 4), 128, 0, st>>>(g, (const V2*)U, (V2*)Ui);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plaq_f64(const GeoH& h, const void* U, const void* Ui, void* Pq, void* Dq,
+                           cudaStream_t st) {
+  Geo g = make_geo(h.L, h.V);
+  k_plaq<double><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (V2*)Pq, (V2*)Dq);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_clover_rot_f64(const GeoH& h, const void* U, const void* Ui, const void* Dq,
+                                 void* F, double sre, double sim, cudaStream_t st) {
+  Geo g = make_geo(h.L, h.V);
+  k_clover_rot<double><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+                                                  (V2*)F, sre, sim);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_plaq_force_f64(bool theta, const GeoH& h, const void* U, const void* Ui,
+                                 const void* Pq, const void* Dq, const void* F, void* C,
+                                 double beta, cudaStream_t st) {
+  Geo g = make_geo(h.L, h.V);
+  const double b6 = (double)(beta / 6.0);
+  if (theta)
+    k_plaq_force<double, true><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
+                                                          (const V2*)Dq, (const V2*)F, (V2*)C, b6);
+  else
+    k_plaq_force<double, false><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
+                                                           (const V2*)Dq, (const V2*)F, (V2*)C, b6);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_update_gather_f64(int mode, const GeoH& h, const void* U, const void* C, void* out,
+                                    double eps, uint64_t seed, uint32_t step, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
   UpdArgs a;
-  a.beta = beta;
+  a.beta = 0.0;
   a.eps = eps;
   a.sqrt_eps = sqrt(eps);
   a.seed = seed;
   a.step = step;
-  dim3 grid((unsigned)((g.V + 127) / 128), 4);
-  const V2* u = (const V2*)U;
-  const V2* f = (const V2*)F;
-  V2* o = (V2*)out;
-  if (theta) {
-    if (mode == MODE_DRIFT) k_cl_update<double, true, MODE_DRIFT><<<grid, 128, 0, st>>>(g, u, f, o, a);
-    else k_cl_update<double, true, MODE_UPDATE><<<grid, 128, 0, st>>>(g, u, f, o, a);
-  } else {
-    if (mode == MODE_DRIFT) k_cl_update<double, false, MODE_DRIFT><<<grid, 128, 0, st>>>(g, u, f, o, a);
-    else k_cl_update<double, false, MODE_UPDATE><<<grid, 128, 0, st>>>(g, u, f, o, a);
-  }
+  if (mode == MODE_DRIFT)
+    k_update_gather<double, MODE_DRIFT><<<grid(g.V, 4), 128, 0, st>>>(g, (const V2*)U, (const V2*)C, (V2*)out, a);
+  else
+    k_update_gather<double, MODE_UPDATE><<<grid(g.V, 4), 128, 0, st>>>(g, (const V2*)U, (const V2*)C, (V2*)out, a);
   return cudaGetLastError();
 }
 
 }  // namespace clgc
 
+// ------------------------------------------------ precision dispatch
 namespace clgc {
-cudaError_t launch_cl_update_f32(bool theta, int mode, const GeoH& h, const void* U, const void* F,
-                                void* out, double beta, double eps, uint64_t seed, uint32_t step,
-                                cudaStream_t st);
+cudaError_t launch_link_inverse_f32(const GeoH&, const void*, void*, cudaStream_t);
+cudaError_t launch_plaq_f32(const GeoH&, const void*, const void*, void*, void*, cudaStream_t);
+cudaError_t launch_clover_rot_f32(const GeoH&, const void*, const void*, const void*, void*, double,
+                                  double, cudaStream_t);
+cudaError_t launch_plaq_force_f32(bool, const GeoH&, const void*, const void*, const void*,
+                                  const void*, const void*, void*, double, cudaStream_t);
+cudaError_t launch_update_gather_f32(int, const GeoH&, const void*, const void*, void*, double,
+                                     uint64_t, uint32_t, cudaStream_t);
 
-cudaError_t launch_cl_update(int prec, bool theta, int mode, const GeoH& h, const void* U,
-                             const void* F, void* out, double beta, double eps, uint64_t seed,
-                             uint32_t step, cudaStream_t st) {
-  if (prec == 0) return launch_cl_update_f64(theta, mode, h, U, F, out, beta, eps, seed, step, st);
-  return launch_cl_update_f32(theta, mode, h, U, F, out, beta, eps, seed, step, st);
+cudaError_t launch_link_inverse(int prec, const GeoH& h, const void* U, void* Ui, cudaStream_t st) {
+  return prec == 0 ? launch_link_inverse_f64(h, U, Ui, st) : launch_link_inverse_f32(h, U, Ui, st);
+}
+cudaError_t launch_plaq(int prec, const GeoH& h, const void* U, const void* Ui, void* Pq, void* Dq,
+                        cudaStream_t st) {
+  return prec == 0 ? launch_plaq_f64(h, U, Ui, Pq, Dq, st) : launch_plaq_f32(h, U, Ui, Pq, Dq, st);
+}
+cudaError_t launch_clover_rot(int prec, const GeoH& h, const void* U, const void* Ui, const void* Dq,
+                              void* F, double sre, double sim, cudaStream_t st) {
+  return prec == 0 ? launch_clover_rot_f64(h, U, Ui, Dq, F, sre, sim, st)
+                   : launch_clover_rot_f32(h, U, Ui, Dq, F, sre, sim, st);
+}
+cudaError_t launch_plaq_force(int prec, bool theta, const GeoH& h, const void* U, const void* Ui,
+                              const void* Pq, const void* Dq, const void* F, void* C, double beta,
+                              cudaStream_t st) {
+  return prec == 0 ? launch_plaq_force_f64(theta, h, U, Ui, Pq, Dq, F, C, beta, st)
+                   : launch_plaq_force_f32(theta, h, U, Ui, Pq, Dq, F, C, beta, st);
+}
+cudaError_t launch_update_gather(int prec, int mode, const GeoH& h, const void* U, const void* C,
+                                 void* out, double eps, uint64_t seed, uint32_t step, cudaStream_t st) {
+  return prec == 0 ? launch_update_gather_f64(mode, h, U, C, out, eps, seed, step, st)
+                   : launch_update_gather_f32(mode, h, U, C, out, eps, seed, step, st);
 }
 }  // namespace clgc

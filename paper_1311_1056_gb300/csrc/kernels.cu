@@ -218,58 +218,6 @@ __global__ void k_soa_to_aos(Geo g, const typename vec2_of<T>::type* __restrict_
   aos[2 * idx + 1] = (double)v.y;
 }
 
-// ------------------------------------------------------------ clover field
-// F_{mu nu}(x) = sum over the four leaves L at x, oriented mu -> nu, of (L - L^{-1}):
-//   L1 = U_mu(x) U_nu(x+mu) [U_nu(x) U_mu(x+nu)]^{-1}
-//   L2 = U_nu(x) [U_nu(x-mu) U_mu(x-mu+nu)]^{-1} U_mu(x-mu)
-//   L3 = [U_nu(x-mu-nu) U_mu(x-mu)]^{-1} U_mu(x-mu-nu) U_nu(x-nu)
-//   L4 = U_nu(x-nu)^{-1} U_mu(x-nu) U_nu(x-nu+mu) U_mu(x)^{-1}
-// Stored times a complex scale (-i theta kappa for the drift, 1 for q_L).
-template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_clover(Geo g, const typename vec2_of<T>::type* __restrict__ U,
-                                                       typename vec2_of<T>::type* __restrict__ F,
-                                                       double sre, double sim) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
-  if (s >= g.V) return;
-  const int p = blockIdx.y, mu = plane_mu(p), nu = plane_nu(p);
-  int x[4];
-  site_coords(g, s, x);
-  const int xpm = hop(g, s, x, mu, 1), xmm = hop(g, s, x, mu, -1);
-  const int xpn = hop(g, s, x, nu, 1), xmn = hop(g, s, x, nu, -1);
-  const int xmm_pn = hop2(g, s, x, mu, -1, nu, 1), xmm_mn = hop2(g, s, x, mu, -1, nu, -1);
-  const int xpm_mn = hop2(g, s, x, mu, 1, nu, -1);
-  mat<T> acc, a, b, A, B, L, Li;
-  set_zero(acc);
-  // L1
-  load(a, U, mu, s, g.V); load(b, U, nu, xpm, g.V); mul(A, a, b);
-  load(a, U, nu, s, g.V); load(b, U, mu, xpn, g.V); mul(B, a, b);
-  adj(a, B); mul(L, A, a); adj(Li, L);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) acc.e[k] = cadd(acc.e[k], csub(L.e[k], Li.e[k]));
-  // L2
-  load(a, U, nu, xmm, g.V); load(b, U, mu, xmm_pn, g.V); mul(B, a, b); adj(A, B);
-  load(a, U, nu, s, g.V); mul(B, a, A);
-  load(b, U, mu, xmm, g.V); mul(L, B, b); adj(Li, L);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) acc.e[k] = cadd(acc.e[k], csub(L.e[k], Li.e[k]));
-  // L3
-  load(a, U, nu, xmm_mn, g.V); load(b, U, mu, xmm, g.V); mul(B, a, b); adj(A, B);
-  load(a, U, mu, xmm_mn, g.V); load(b, U, nu, xmn, g.V); mul(B, a, b);
-  mul(L, A, B); adj(Li, L);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) acc.e[k] = cadd(acc.e[k], csub(L.e[k], Li.e[k]));
-  // L4
-  load(a, U, mu, xmn, g.V); load(b, U, nu, xpm_mn, g.V); mul(B, a, b);
-  load(a, U, nu, xmn, g.V); adj(A, a); mul(a, A, B);
-  load(b, U, mu, s, g.V); adj(A, b); mul(L, a, A); adj(Li, L);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) acc.e[k] = cadd(acc.e[k], csub(L.e[k], Li.e[k]));
-  cx<T> sc = {(T)sre, (T)sim};
-#pragma unroll
-  for (int k = 0; k < 9; ++k) acc.e[k] = cmul(acc.e[k], sc);
-  store(F, p, s, g.V, acc);
-}
-
 // --------------------------------------------------------------- cooling
 // f_ax = 2 Tr[lambda_a G_x], G_x = sum_mu (U_{x,mu} U_{x,mu}^+ - U_{x-mu,mu}^+ U_{x-mu,mu})
 // (Sec. 2, eq. "eq:24"); per block: sum |f|, sum f^2, sum (1/3) Tr U U^+ of
@@ -574,16 +522,6 @@ cudaError_t launch_soa_to_aos(int prec, const GeoH& h, const void* U, double* ao
   unsigned blocks = (unsigned)((n + 255) / 256);
   if (prec == 0) k_soa_to_aos<double><<<blocks, 256, 0, st>>>(g, (const double2*)U, aos, nplanes);
   else k_soa_to_aos<float><<<blocks, 256, 0, st>>>(g, (const float2*)U, aos, nplanes);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_clover(int prec, const GeoH& h, const void* U, void* F, double sre, double sim,
-                          cudaStream_t st) {
-  Geo g = to_geo(h);
-  if (prec == 0)
-    k_clover<double><<<grid_sites(g.V, 6), RED_THREADS, 0, st>>>(g, (const double2*)U, (double2*)F, sre, sim);
-  else
-    k_clover<float><<<grid_sites(g.V, 6), RED_THREADS, 0, st>>>(g, (const float2*)U, (float2*)F, sre, sim);
   return cudaGetLastError();
 }
 

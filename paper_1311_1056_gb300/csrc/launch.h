@@ -47,13 +47,21 @@ cudaError_t launch_aos_to_soa(int prec, const GeoH& g, const double* aos, void* 
                               cudaStream_t st);
 cudaError_t launch_soa_to_aos(int prec, const GeoH& g, const void* U, double* aos, int nplanes,
                               cudaStream_t st);
-// F^ = scale * F_{mu nu}(x), six planes.
-cudaError_t launch_clover(int prec, const GeoH& g, const void* U, void* F, double scale_re,
-                          double scale_im, cudaStream_t st);
-// One CL update (mode 0) or the drift matrix only (mode 1).
-cudaError_t launch_cl_update(int prec, bool theta, int mode, const GeoH& g, const void* U,
-                             const void* F, void* out, double beta, double eps, uint64_t seed,
-                             uint32_t step, cudaStream_t st);
+// The CL step (k_update.cuh): link inverses Ui; plaquettes P and D = P - P^{-1}
+// (six planes); the clover field F^ = scale * F_{mu nu}(x) built from the D's;
+// the per-plaquette drift contributions C (24 planes: 4 links x 6 planes);
+// then per link the gather of its six contributions followed by the update
+// (mode 0) or by storing the drift matrix X_S (mode 1).
+cudaError_t launch_link_inverse(int prec, const GeoH& g, const void* U, void* Ui, cudaStream_t st);
+cudaError_t launch_plaq(int prec, const GeoH& g, const void* U, const void* Ui, void* Pq, void* Dq,
+                        cudaStream_t st);
+cudaError_t launch_clover_rot(int prec, const GeoH& g, const void* U, const void* Ui, const void* Dq,
+                              void* F, double scale_re, double scale_im, cudaStream_t st);
+cudaError_t launch_plaq_force(int prec, bool theta, const GeoH& g, const void* U, const void* Ui,
+                              const void* Pq, const void* Dq, const void* F, void* C, double beta,
+                              cudaStream_t st);
+cudaError_t launch_update_gather(int prec, int mode, const GeoH& g, const void* U, const void* C,
+                                 void* out, double eps, uint64_t seed, uint32_t step, cudaStream_t st);
 // Cooling: gradient f (8 per site) + partial sums; the rule; Omega; apply.
 cudaError_t launch_cool_grad(int prec, const GeoH& g, const void* U, void* f, double* partials,
                              const CoolState* cs, cudaStream_t st);
