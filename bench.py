@@ -43,23 +43,39 @@ ALG_BYTES = {"fp64": 1152 + 10 * 1280, "fp32": 576 + 10 * 704}
 CPU_SAMPLE_L = (8, 8, 8, 8)
 
 
-# FP64 flops per launch unit of each kernel, counted from the kernel source
-# (FMA = 2 flops, transcendental library calls not counted): see flop_model().
-def flop_model(prec, theta_on=True):
-    mul, mul_acc, adj, axpy, cmul, cfma = 198, 216, 126, 36, 6, 8
-    # one plaquette of the drift: theta on -> 6 mul, 8 mul_acc, 5 adj, 2 axpy
-    plaq = (6 * mul + 8 * mul_acc + 5 * adj + 2 * axpy) if theta_on else (2 * mul + 3 * adj + 2 * axpy)
-    drift = 6 * plaq + mul + mul_acc + adj
-    n_taylor = 15
-    expm = mul + 6 + 72 + 36 + 7 + 2 * cfma * n_taylor + 9 * (cmul + cfma) + 6
-    upd_fp64 = 12 + 19 + 38 + 48 + expm + 64 + 36  # exponent, noise, exp, det, cube root
-    if prec == "fp64":
-        per_link = drift + upd_fp64 + mul + 9 * cmul
+# Floating-point operations per site of each kernel of the step, counted
+# from the kernel source (FMA = 2 flops; the transcendental calls of the
+# Box-Muller noise are not counted).  Building blocks: 3x3 complex product
+# 198, product-accumulate 216, adjugate 126, Hermitian-times-general 162.
+# ncu's executed-instruction counters agree within 1 % on these sources
+# (profiles/ncu_fp64_counts_24x4.md).  "pipe" is the unit the kernel loads:
+# the FP64 pipe in the FP64 form; in the FP32-storage form only the
+# exponentials, the re-projection and the cooling Omega stay on it.
+MUL, MULACC, ADJ, HERM = 198, 216, 126, 162
+
+
+def flop_model(prec, theta_on=True, n_taylor=15):
+    expm = MUL + 6 + 72 + 36 + 16 * n_taylor + 9 * (6 + 8) + 6  # Cayley-Hamilton + Horner
+    det_root = 64 + 35                                           # det + cube-root series
+    if theta_on:
+        force = 6 * (13 * MUL + 9 * MULACC + 162)                # per-plaquette drift, 6 planes
     else:
-        per_link = upd_fp64  # the drift, E*U and the rescaling run in FP32
-    # cooling Omega (per site): H^2 ~33, det ~16, 2 Horner series, 2 assemblies
-    omega = 8 + 33 + 2 + 16 + 2 * 2 * 2 * 8 + 2 * 18 * 2
-    return {"update_per_link": per_link, "omega_per_site": omega}
+        force = 6 * (4 * MUL + 36)
+    m = {
+        "force": force,
+        "clover": 4 * ADJ + 6 * (3 * MUL + ADJ + 18) + (6 * (3 * (MUL + MULACC) + 54) if theta_on else 0),
+        "cool_grad": 914,
+        "cool_omega": 209,
+        "cool_apply": 4 * 2 * HERM,
+    }
+    if prec == "fp64":
+        m["update"] = 4 * (12 * 18 + 32 + 38 + expm + MUL + det_root + 54)
+        pipe = {k: "fp64" for k in m}
+    else:
+        m["update"] = 4 * (expm - 36 + det_root)                 # FP64 part only
+        pipe = {k: "fp32" for k in m}
+        pipe["update"] = pipe["cool_omega"] = "fp64"
+    return m, pipe
 
 
 def fp64_peak_tflops(sm_max_mhz):
@@ -238,27 +254,25 @@ def e2e_measure(cl, torch, lat, V, one_step, steps):
 
 
 def roofline_of(prec_name, V, phases, sm_max_mhz, theta_on=True):
-    fm = flop_model(prec_name, theta_on)
-    dom = max(phases, key=lambda k: phases[k][0])
+    """Roofline of the kernel that dominates the step (a single-kernel phase)."""
+    fm, pipe = flop_model(prec_name, theta_on)
+    single = {k: v for k, v in phases.items() if k in ("force", "update", "cool_grad", "cool_omega",
+                                                       "cool_apply")}
+    dom = max(single, key=lambda k: single[k][0])
     ms_tot, n = phases[dom]
     per = ms_tot / max(n, 1)
-    peak = fp64_peak_tflops(sm_max_mhz)
-    if dom == "update":
-        flops = fm["update_per_link"] * 4 * V
-    elif dom == "cool_omega":
-        flops = fm["omega_per_site"] * V
+    flops = fm[dom] * V
+    if pipe[dom] == "fp64":
+        peak = fp64_peak_tflops(sm_max_mhz)
+        src = "152 SMs x 2 FP64 FMA/clk x %d MHz (FP64 is not in MEASURED_PEAKS.json)" % sm_max_mhz
     else:
-        flops = None
-    out = {"kernel": dom, "bound": "alu", "pipe": "fp64", "unit": "TFLOP/s", "peak": round(peak, 4),
-           "peak_source": "152 SMs x 2 FP64 FMA/clk x %d MHz (FP64 not in MEASURED_PEAKS.json)" % sm_max_mhz,
-           "avg_launch_ms": round(per, 4), "launches": n,
-           "traffic": dram_traffic(dom, prec_name)}
-    if flops is not None:
-        ach = flops / (per * 1e-3) / 1e12
-        out.update({"achieved": round(ach, 4), "frac": round(ach / peak, 4), "flops_per_launch": flops})
-    else:
-        out.update({"achieved": None, "frac": None})
-    return out
+        peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+        src = "152 SMs x 128 FP32 FMA/clk x %d MHz" % sm_max_mhz
+    ach = flops / (per * 1e-3) / 1e12
+    return {"kernel": dom, "bound": "alu", "pipe": pipe[dom], "achieved": round(ach, 4),
+            "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+            "traffic": dram_traffic(dom, prec_name), "flops_per_launch": flops,
+            "avg_launch_ms": round(per, 4), "launches": n, "peak_source": src}
 
 
 def native(args):

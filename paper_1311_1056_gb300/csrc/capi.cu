@@ -52,7 +52,7 @@ struct cl_lattice {
   void* Dq;    // P - P^{-1} [6][9][V]
   void* C;     // per-plaquette drift contributions [24][9][V]
   void* F;     // clover field, SoA [6][9][V]
-  void* f;     // cooling gradient [8][V] (real)
+  void* f;     // cooling gradient [8][V] (FP64 in both forms)
   void* Om;    // packed Hermitian Omega [9][V]
   void* Omi;   // and its inverse
   double* partials;
@@ -276,7 +276,7 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
   alloc(&l->Dq, l->esz * 6 * 9 * Vs);
   alloc(&l->C, l->esz * 24 * 9 * Vs);
   alloc(&l->F, l->esz * 6 * 9 * Vs);
-  alloc(&l->f, real_size(l) * 8 * Vs);
+  alloc(&l->f, sizeof(double) * 8 * Vs);
   alloc(&l->Om, real_size(l) * 9 * Vs);
   alloc(&l->Omi, real_size(l) * 9 * Vs);
   alloc((void**)&l->partials, sizeof(double) * NQ_OBS * (size_t)reduce_blocks(l->g.V));
@@ -468,15 +468,8 @@ cl_status cl_cool_gradient(cl_lattice* l, double* host_f) {
   CK(launch_cool_grad(l->prec, l->g, l->U, l->f, l->partials, nullptr, l->st));
   l->launches++;
   const size_t n = 8 * (size_t)l->g.V;
-  if (l->prec == 0) {
-    CK(cudaMemcpyAsync(host_f, l->f, sizeof(double) * n, cudaMemcpyDeviceToHost, l->st));
-    CK(cudaStreamSynchronize(l->st));
-  } else {
-    std::vector<float> t(n);
-    CK(cudaMemcpyAsync(t.data(), l->f, sizeof(float) * n, cudaMemcpyDeviceToHost, l->st));
-    CK(cudaStreamSynchronize(l->st));
-    for (size_t i = 0; i < n; ++i) host_f[i] = t[i];
-  }
+  CK(cudaMemcpyAsync(host_f, l->f, sizeof(double) * n, cudaMemcpyDeviceToHost, l->st));
+  CK(cudaStreamSynchronize(l->st));
   return CL_OK;
 }
 

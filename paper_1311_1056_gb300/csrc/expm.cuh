@@ -42,8 +42,9 @@ __device__ __forceinline__ int taylor_terms(float r) {
   return n;
 }
 
-// exp(A) for traceless complex A, FP64.
-__device__ __forceinline__ void expm_traceless(mat<double>& E, const mat<double>& A) {
+// exp(A) for traceless complex A, FP64.  r_hint >= 0 is the Frobenius norm
+// of A when the caller has it (e.g. from an FP32 copy); < 0 computes it.
+__device__ __forceinline__ void expm_traceless(mat<double>& E, const mat<double>& A, float r_hint = -1.f) {
   mat<double> A2;
   mul(A2, A, A);
   cx<double> c1 = trace(A2);
@@ -52,18 +53,18 @@ __device__ __forceinline__ void expm_traceless(mat<double>& E, const mat<double>
   cx<double> c0 = trace_mul(A2, A);
   c0.re *= (1.0 / 3.0);
   c0.im *= (1.0 / 3.0);
-  double r2 = norm2(A);
-  float r = sqrtf((float)r2);
+  float r = r_hint >= 0.f ? r_hint : sqrtf((float)norm2(A));
   int s = 0;
   double sc = 1.0;  // scaling 2^-s
+  cx<double> b0 = c0, b1 = c1;  // det and Tr(B^2)/2 of B = A 2^-s
   if (r > 1.0f) {
     s = (int)ceilf(log2f(r));
     sc = ldexp(1.0, -s);
     r = (float)(r * sc);
+    const double sc2 = sc * sc;
+    b0 = cx<double>{c0.re * sc2 * sc, c0.im * sc2 * sc};
+    b1 = cx<double>{c1.re * sc2, c1.im * sc2};
   }
-  double sc2 = sc * sc;
-  cx<double> b0 = {c0.re * sc2 * sc, c0.im * sc2 * sc};  // det(A 2^-s)
-  cx<double> b1 = {c1.re * sc2, c1.im * sc2};            // Tr((A 2^-s)^2)/2
   int N = taylor_terms(r);
   cx<double> a = {c_invfact[N], 0.0}, b = {0.0, 0.0}, c = {0.0, 0.0};
   for (int k = N - 1; k >= 0; --k) {
@@ -88,11 +89,12 @@ __device__ __forceinline__ void expm_traceless(mat<double>& E, const mat<double>
     b = nb;
     c = nc;
   }
-  // back to powers of A: b B = (b sc) A, c B^2 = (c sc^2) A^2
-  b.re *= sc;
-  b.im *= sc;
-  c.re *= sc2;
-  c.im *= sc2;
+  if (s > 0) {  // back to powers of A: b B = (b sc) A, c B^2 = (c sc^2) A^2
+    b.re *= sc;
+    b.im *= sc;
+    c.re *= sc * sc;
+    c.im *= sc * sc;
+  }
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
     cx<double> v = cmul(b, A.e[k]);
@@ -146,12 +148,14 @@ __device__ __forceinline__ void expm_hermitian_pair(herm& om, herm& omi, const h
   float r = sqrtf((float)(2.0 * c1));
   int s = 0;
   double sc = 1.0;
+  double b1 = c1, b0 = c0;
   if (r > 1.0f) {
     s = (int)ceilf(log2f(r));
     sc = ldexp(1.0, -s);
     r = (float)(r * sc);
+    b1 = c1 * sc * sc;
+    b0 = c0 * sc * sc * sc;
   }
-  double b1 = c1 * sc * sc, b0 = c0 * sc * sc * sc;
   int N = taylor_terms(r);
   // exp(B) = a + bB + cB^2 and exp(-B) = ap - bp B + cp B^2 (det(-B) = -det B)
   double a = c_invfact[N], b = 0.0, c = 0.0;
@@ -178,10 +182,13 @@ __device__ __forceinline__ void expm_hermitian_pair(herm& om, herm& omi, const h
     nc = fma(cp * cp, b1, fma(2.0 * ap, cp, bp * bp));
     ap = na; bp = nb; cp = nc;
   }
-  b *= sc;
-  c *= sc * sc;
-  bp *= -sc;
-  cp *= sc * sc;
+  if (s > 0) {
+    b *= sc;
+    c *= sc * sc;
+    bp *= sc;
+    cp *= sc * sc;
+  }
+  bp = -bp;  // exp(-H) = ap - bp H + cp H^2
   om.d0 = fma(c, h2.d0, fma(b, h.d0, a));
   om.d1 = fma(c, h2.d1, fma(b, h.d1, a));
   om.d2 = fma(c, h2.d2, fma(b, h.d2, a));

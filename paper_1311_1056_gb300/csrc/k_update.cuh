@@ -98,12 +98,13 @@ __device__ __forceinline__ void scaled(mat<T>& r, T c, const mat<T>& a) {
 template <typename T>
 __global__ void __launch_bounds__(128) k_link_inverse(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                       typename vec2_of<T>::type* __restrict__ Ui) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mu = blockIdx.x % 4;
+  const int s = (blockIdx.x / 4) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   mat<T> u, ui;
-  load(u, U, blockIdx.y, s, g.V);
+  load(u, U, mu, s, g.V);
   adj(ui, u);
-  store(Ui, blockIdx.y, s, g.V, ui);
+  store(Ui, mu, s, g.V, ui);
 }
 
 // ------------------------------------------------------------- plaquettes
@@ -114,9 +115,9 @@ __global__ void __launch_bounds__(128) k_plaq(Geo g, const typename vec2_of<T>::
                                               const typename vec2_of<T>::type* __restrict__ Ui,
                                               typename vec2_of<T>::type* __restrict__ Pq,
                                               typename vec2_of<T>::type* __restrict__ Dq) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p);
+  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
-  const int p = blockIdx.y, mu = plane_mu(p), nu = plane_nu(p);
   int x[4];
   site_coords(g, s, x);
   mat<T> a, b, A, B, P;
@@ -147,40 +148,32 @@ __global__ void __launch_bounds__(128) k_clover_rot(Geo g, const typename vec2_o
                                                     const typename vec2_of<T>::type* __restrict__ Dq,
                                                     typename vec2_of<T>::type* __restrict__ F,
                                                     double sre, double sim) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p);
+  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
-  const int p = blockIdx.y, mu = plane_mu(p), nu = plane_nu(p);
   int x[4];
   site_coords(g, s, x);
   const int xmm = hop(g, s, x, mu, -1), xmn = hop(g, s, x, nu, -1);
   const int xmm_mn = hop2(g, s, x, mu, -1, nu, -1);
-  mat<T> acc, w, wi, d, t;
+  mat<T> acc, w, d, t;
   load(acc, Dq, p, s, g.V);
-  // L2
-  load(wi, Ui, mu, xmm, g.V);
+  // L2 = U_mu(x-mu)^{-1} D(x-mu) U_mu(x-mu)
+  load(w, Ui, mu, xmm, g.V);
   load(d, Dq, p, xmm, g.V);
-  mul(t, wi, d);
+  mul(t, w, d);
   load(w, U, mu, xmm, g.V);
   mul_acc<+1>(acc, t, w);
-  // L4
-  load(wi, Ui, nu, xmn, g.V);
+  // L3 + L4 = U_nu(x-nu)^{-1} [D(x-nu) + U_mu(x-mu-nu)^{-1} D(x-mu-nu) U_mu(x-mu-nu)] U_nu(x-nu)
+  load(w, Ui, mu, xmm_mn, g.V);
+  load(d, Dq, p, xmm_mn, g.V);
+  mul(t, w, d);
+  load(w, U, mu, xmm_mn, g.V);
   load(d, Dq, p, xmn, g.V);
-  mul(t, wi, d);
+  mul_acc<+1>(d, t, w);
+  load(w, Ui, nu, xmn, g.V);
+  mul(t, w, d);
   load(w, U, nu, xmn, g.V);
   mul_acc<+1>(acc, t, w);
-  // L3
-  {
-    mat<T> a, b;
-    load(a, Ui, nu, xmn, g.V);
-    load(b, Ui, mu, xmm_mn, g.V);
-    mul(wi, a, b);
-    load(d, Dq, p, xmm_mn, g.V);
-    mul(t, wi, d);
-    load(a, U, mu, xmm_mn, g.V);
-    load(b, U, nu, xmn, g.V);
-    mul(w, a, b);
-    mul_acc<+1>(acc, t, w);
-  }
   cx<T> sc = {(T)sre, (T)sim};
 #pragma unroll
   for (int k = 0; k < 9; ++k) acc.e[k] = cmul(acc.e[k], sc);
@@ -199,9 +192,9 @@ __global__ void __launch_bounds__(128) k_plaq_force(Geo g, const typename vec2_o
                                                     const typename vec2_of<T>::type* __restrict__ Dq,
                                                     const typename vec2_of<T>::type* __restrict__ F,
                                                     typename vec2_of<T>::type* C, T beta6) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p), pc = 5 - p;
+  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
-  const int p = blockIdx.y, mu = plane_mu(p), nu = plane_nu(p), pc = 5 - p;
   const unsigned long long m = (p == 1 || p == 4) ? 0x8000000000000000ull : 0ull;
   int x[4];
   site_coords(g, s, x);
@@ -320,9 +313,10 @@ __global__ void __launch_bounds__(128) k_plaq_force(Geo g, const typename vec2_o
 
 // Noise matrix sum_a eta_a lambda_a (Hermitian) into the imaginary part of A,
 // scaled by sqrt(eps): A += i sqrt(eps) H.
-__device__ __forceinline__ void add_noise(mat<double>& A, const double* e, double se) {
-  const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
-  double h00 = e[2] + e[7] * r3, h11 = -e[2] + e[7] * r3, h22 = -2.0 * e[7] * r3;
+template <typename R>
+__device__ __forceinline__ void add_noise(mat<R>& A, const R* e, R se) {
+  const R r3 = (R)0.57735026918962576451;  // 1/sqrt(3)
+  R h00 = e[2] + e[7] * r3, h11 = -e[2] + e[7] * r3, h22 = (R)-2 * e[7] * r3;
   // i * (hr + i hi) = -hi + i hr
   A.e[0].im = fma(se, h00, A.e[0].im);
   A.e[4].im = fma(se, h11, A.e[4].im);
@@ -336,6 +330,19 @@ __device__ __forceinline__ void add_noise(mat<double>& A, const double* e, doubl
   A.e[7].re = fma(-se, e[6], A.e[7].re); A.e[7].im = fma(se, e[5], A.e[7].im);
 }
 
+// A = 2 eps (X - Tr X / 3) + i sqrt(eps) sqrt(2) g_a lambda_a in the real type R.
+template <typename R>
+__device__ __forceinline__ void exponent(mat<R>& A, const R* g, R eps, R sqrt_eps) {
+  const R tr_re = (A.e[0].re + A.e[4].re + A.e[8].re) * (R)(1.0 / 3.0);
+  const R tr_im = (A.e[0].im + A.e[4].im + A.e[8].im) * (R)(1.0 / 3.0);
+  A.e[0].re -= tr_re; A.e[4].re -= tr_re; A.e[8].re -= tr_re;
+  A.e[0].im -= tr_im; A.e[4].im -= tr_im; A.e[8].im -= tr_im;
+  const R e2 = (R)2 * eps;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) { A.e[k].re *= e2; A.e[k].im *= e2; }
+  add_noise(A, g, sqrt_eps * (R)1.41421356237309504880);  // eta = sqrt(2) * normal
+}
+
 // ------------------------------------------------ gather + exponential update
 // X of link (x, mu) = sum of its six plaquette contributions: for nu != mu,
 // mu < nu: slot 0 of (x, p) and slot 3 of (x - nu, p); mu > nu: slot 1 of
@@ -345,9 +352,9 @@ __global__ void __launch_bounds__(128) k_update_gather(Geo g, const typename vec
                                                        const typename vec2_of<T>::type* __restrict__ C,
                                                        typename vec2_of<T>::type* __restrict__ out,
                                                        UpdArgs a) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int MU = blockIdx.x % 4;
+  const int s = (blockIdx.x / 4) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
-  const int MU = blockIdx.y;
   int x[4];
   site_coords(g, s, x);
   mat<T> X, t;
@@ -368,30 +375,27 @@ __global__ void __launch_bounds__(128) k_update_gather(Geo g, const typename vec
     store(out, MU, s, g.V, X);
     return;
   }
-  // exponent A = 2 eps (X - Tr X/3) + i sqrt(eps) eta_a lambda_a, in FP64
+  // exponent A = 2 eps (X - Tr X/3) + i sqrt(eps) eta_a lambda_a; exp in FP64.
+  // The FP64 form builds A in FP64; the FP32-storage form builds it in FP32
+  // (X and the noise carry FP32 information only) and widens it for the exp.
   mat<double> A;
-  convert(A, X);
-  {
-    double tr_re = (A.e[0].re + A.e[4].re + A.e[8].re) * (1.0 / 3.0);
-    double tr_im = (A.e[0].im + A.e[4].im + A.e[8].im) * (1.0 / 3.0);
-    A.e[0].re -= tr_re; A.e[4].re -= tr_re; A.e[8].re -= tr_re;
-    A.e[0].im -= tr_im; A.e[4].im -= tr_im; A.e[8].im -= tr_im;
-    const double e2 = 2.0 * a.eps;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) { A.e[k].re *= e2; A.e[k].im *= e2; }
-  }
-  double eta[8];
+  float rA = -1.f;
   if (sizeof(T) == 8) {
+    double eta[8];
     normals_f64<4>(eta, a.seed, a.step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
+    convert(A, X);
+    exponent<double>(A, eta, a.eps, a.sqrt_eps);
   } else {
     float ef[8];
     normals_f32<4>(ef, a.seed, a.step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) eta[k] = (double)ef[k];
+    mat<float> Af;
+    convert(Af, X);
+    exponent<float>(Af, ef, (float)a.eps, (float)a.sqrt_eps);
+    rA = sqrtf(norm2(Af));
+    convert(A, Af);
   }
-  add_noise(A, eta, a.sqrt_eps * 1.41421356237309504880);  // eta = sqrt(2) * normal
   mat<double> E;
-  expm_traceless(E, A);
+  expm_traceless(E, A, rA);
   mat<T> Et, Ul, Un;
   convert(Et, E);
   load(Ul, U, MU, s, g.V);

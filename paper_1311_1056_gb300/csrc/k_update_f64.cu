@@ -6,7 +6,9 @@ namespace clgc {
 
 namespace {
 typedef vec2_of<double>::type V2;
-inline dim3 grid(int V, int planes) { return dim3((unsigned)((V + 127) / 128), (unsigned)planes); }
+// 1-D grid, plane (or direction) fastest: the blocks resident at one time
+// cover every plane of a range of sites, so shared neighbours stay in cache.
+inline dim3 grid(int V, int planes) { return dim3((unsigned)(((V + 127) / 128) * planes)); }
 }  // namespace
 
 cudaError_t launch_link_inverse_f64(const GeoH& h, const void* U, void* Ui, cudaStream_t st) {

@@ -18,6 +18,10 @@ Geo to_geo(const GeoH& h) { return make_geo(h.L, h.V); }
 inline dim3 grid_sites(int V, int planes = 1) {
   return dim3((unsigned)((V + RED_THREADS - 1) / RED_THREADS), (unsigned)planes);
 }
+// 1-D grid with the direction fastest (see k_update_f64.cu).
+inline dim3 grid_sites_1d(int V, int planes) {
+  return dim3((unsigned)(((V + RED_THREADS - 1) / RED_THREADS) * planes));
+}
 
 // Fixed-order block reduction of NQ doubles (slot MAXSLOT takes the max);
 // one record per block into partials.
@@ -224,22 +228,19 @@ __global__ void k_soa_to_aos(Geo g, const typename vec2_of<T>::type* __restrict_
 // the links at x, nonfinite count.
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename vec2_of<T>::type* __restrict__ U,
-                                                          T* __restrict__ f, double* partials,
+                                                          double* __restrict__ f, double* partials,
                                                           const CoolState* cs) {
   if (cs && cs->done) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
   double v[NQ_COOL] = {0.0, 0.0, 0.0, 0.0};
-  if (s < g.V) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
     int x[4];
     site_coords(g, s, x);
     T g00 = 0, g11 = 0, g22 = 0;
     cx<T> g01 = {0, 0}, g02 = {0, 0}, g12 = {0, 0};
-    T un = 0;
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       mat<T> u;
       load(u, U, mu, s, g.V);
-      un += norm2(u);
       // + U U^+ : (i,j) = sum_k U_ik conj(U_jk)
 #pragma unroll
       for (int k = 0; k < 3; ++k) {
@@ -251,6 +252,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename
         g02 = cfma(r0, cx<T>{r2.re, -r2.im}, g02);
         g12 = cfma(r1, cx<T>{r2.re, -r2.im}, g12);
       }
+    }
+    // sum over the four links at x of Tr U U^+ = the diagonal accumulated so far
+    const T un = g00 + g11 + g22;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      mat<T> u;
       load(u, U, mu, hop(g, s, x, mu, -1), g.V);
       // - U^+ U : (i,j) = sum_k conj(U_ki) U_kj
 #pragma unroll
@@ -274,17 +281,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename
     fa[5] = 4 * g12.re;
     fa[6] = -4 * g12.im;
     fa[7] = 2 * r3 * (g00 + g11 - 2 * g22);
-    bool ok = true;
+    bool ok = isfinite(un);
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-      f[(size_t)a * g.V + s] = fa[a];
-      double d = (double)fa[a];
+      const double d = (double)fa[a];
+      f[(size_t)a * g.V + s] = d;
       v[0] += fabs(d);
       v[1] = fma(d, d, v[1]);
       ok = ok && isfinite(fa[a]);
     }
-    v[2] = (double)un * (1.0 / 3.0);
-    v[3] = ok ? 0.0 : 1.0;
+    v[2] += (double)un * (1.0 / 3.0);
+    v[3] += ok ? 0.0 : 1.0;
   }
   block_reduce_store<NQ_COOL, -1>(v, partials);
 }
@@ -348,14 +355,14 @@ __global__ void k_cool_adapt(Geo g, const double* partials, int nb, CoolArgs a, 
 
 // Omega_x = exp(-eps alpha_ad f_ax lambda_a) and its inverse, FP64.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_cool_omega(Geo g, const T* __restrict__ f, T* Om, T* Omi,
+__global__ void __launch_bounds__(RED_THREADS) k_cool_omega(Geo g, const double* __restrict__ f, T* Om, T* Omi,
                                                            double eps, const CoolState* cs) {
   if (cs->done) return;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   double fa[8];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) fa[a] = (double)__ldg(f + (size_t)a * g.V + s);
+  for (int a = 0; a < 8; ++a) fa[a] = __ldg(f + (size_t)a * g.V + s);
   herm h = herm_from_algebra(fa, -eps * cs->alpha_ad), om, omi;
   expm_hermitian_pair(om, omi, h);
   store_herm(Om, s, g.V, om);
@@ -369,17 +376,17 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_apply(Geo g, typename vec2
                                                            const T* __restrict__ Omi,
                                                            const CoolState* cs) {
   if (cs && cs->done) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  const int mu = blockIdx.x % 4;
+  const int s = (blockIdx.x / 4) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
-  int mu = blockIdx.y;
   int x[4];
   site_coords(g, s, x);
   mat<T> o, oi, u, t;
   load_herm_mat(o, Om, s, g.V);
   load_herm_mat(oi, Omi, hop(g, s, x, mu, 1), g.V);
   load(u, U, mu, s, g.V);
-  mul(t, o, u);
-  mul(u, t, oi);
+  mul_herm_left(t, o, u);
+  mul_herm_right(u, t, oi);
   store(U, mu, s, g.V, u);
 }
 
@@ -392,11 +399,10 @@ template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_obs(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                     const typename vec2_of<T>::type* __restrict__ F,
                                                     int with_q, double* partials, double* q_site) {
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
   double v[NQ_OBS];
 #pragma unroll
   for (int q = 0; q < NQ_OBS; ++q) v[q] = 0.0;
-  if (s < g.V) {
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
     int x[4];
     site_coords(g, s, x);
     bool ok = true;
@@ -444,14 +450,14 @@ __global__ void __launch_bounds__(RED_THREADS) k_obs(Geo g, const typename vec2_
       }
       q.re *= KAPPA_Q;
       q.im *= KAPPA_Q;
-      v[5] = q.re;
-      v[6] = q.im;
+      v[5] += q.re;
+      v[6] += q.im;
       if (q_site) {
         q_site[2 * (size_t)s] = q.re;
         q_site[2 * (size_t)s + 1] = q.im;
       }
     }
-    v[8] = ok ? 0.0 : 1.0;
+    v[8] += ok ? 0.0 : 1.0;
   }
   block_reduce_store<NQ_OBS, 7>(v, partials);
 }
@@ -479,7 +485,12 @@ __global__ void k_obs_final(Geo g, const double* partials, int nb, double beta, 
 
 }  // namespace
 
-int reduce_blocks(int V) { return (V + RED_THREADS - 1) / RED_THREADS; }
+// Reduction kernels loop over sites with at most RED_MAX_BLOCKS blocks, so
+// the one-block rule reads few records; the split depends on V only.
+int reduce_blocks(int V) {
+  int b = (V + RED_THREADS - 1) / RED_THREADS;
+  return b < RED_MAX_BLOCKS ? b : RED_MAX_BLOCKS;
+}
 
 cudaError_t launch_cold(int prec, const GeoH& h, void* U, cudaStream_t st) {
   Geo g = to_geo(h);
@@ -529,9 +540,9 @@ cudaError_t launch_cool_grad(int prec, const GeoH& h, const void* U, void* f, do
                              const CoolState* cs, cudaStream_t st) {
   Geo g = to_geo(h);
   if (prec == 0)
-    k_cool_grad<double><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const double2*)U, (double*)f, partials, cs);
+    k_cool_grad<double><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const double2*)U, (double*)f, partials, cs);
   else
-    k_cool_grad<float><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const float2*)U, (float*)f, partials, cs);
+    k_cool_grad<float><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const float2*)U, (double*)f, partials, cs);
   return cudaGetLastError();
 }
 
@@ -548,7 +559,7 @@ cudaError_t launch_cool_omega(int prec, const GeoH& h, const void* f, void* Om, 
   if (prec == 0)
     k_cool_omega<double><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const double*)f, (double*)Om, (double*)Omi, eps, cs);
   else
-    k_cool_omega<float><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const float*)f, (float*)Om, (float*)Omi, eps, cs);
+    k_cool_omega<float><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const double*)f, (float*)Om, (float*)Omi, eps, cs);
   return cudaGetLastError();
 }
 
@@ -556,9 +567,9 @@ cudaError_t launch_cool_apply(int prec, const GeoH& h, void* U, const void* Om, 
                               const CoolState* cs, cudaStream_t st) {
   Geo g = to_geo(h);
   if (prec == 0)
-    k_cool_apply<double><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (double2*)U, (const double*)Om, (const double*)Omi, cs);
+    k_cool_apply<double><<<grid_sites_1d(g.V, 4), RED_THREADS, 0, st>>>(g, (double2*)U, (const double*)Om, (const double*)Omi, cs);
   else
-    k_cool_apply<float><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (float2*)U, (const float*)Om, (const float*)Omi, cs);
+    k_cool_apply<float><<<grid_sites_1d(g.V, 4), RED_THREADS, 0, st>>>(g, (float2*)U, (const float*)Om, (const float*)Omi, cs);
   return cudaGetLastError();
 }
 
@@ -566,9 +577,9 @@ cudaError_t launch_obs(int prec, const GeoH& h, const void* U, const void* F, in
                        double* partials, double* q_site, cudaStream_t st) {
   Geo g = to_geo(h);
   if (prec == 0)
-    k_obs<double><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const double2*)U, (const double2*)F, with_q, partials, q_site);
+    k_obs<double><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const double2*)U, (const double2*)F, with_q, partials, q_site);
   else
-    k_obs<float><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const float2*)U, (const float2*)F, with_q, partials, q_site);
+    k_obs<float><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const float2*)U, (const float2*)F, with_q, partials, q_site);
   return cudaGetLastError();
 }
 

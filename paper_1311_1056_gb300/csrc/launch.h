@@ -31,7 +31,7 @@ struct ObsOut {
   double nonfinite;
 };
 
-enum { NQ_OBS = 9, NQ_COOL = 4, RED_THREADS = 128 };
+enum { NQ_OBS = 9, NQ_COOL = 4, RED_THREADS = 128, RED_MAX_BLOCKS = 1216 };
 
 int reduce_blocks(int V);  // number of per-block partial records for V sites
 
@@ -62,7 +62,8 @@ cudaError_t launch_plaq_force(int prec, bool theta, const GeoH& g, const void* U
                               cudaStream_t st);
 cudaError_t launch_update_gather(int prec, int mode, const GeoH& g, const void* U, const void* C,
                                  void* out, double eps, uint64_t seed, uint32_t step, cudaStream_t st);
-// Cooling: gradient f (8 per site) + partial sums; the rule; Omega; apply.
+// Cooling: gradient f (8 FP64 values per site, [a][V]) + partial sums; the
+// rule; Omega; apply.
 cudaError_t launch_cool_grad(int prec, const GeoH& g, const void* U, void* f, double* partials,
                              const CoolState* cs, cudaStream_t st);
 cudaError_t launch_cool_adapt(const GeoH& g, const double* partials, CoolArgs a, CoolState* cs,
