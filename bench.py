@@ -34,7 +34,7 @@ sys.path.insert(0, ROOT)
 
 WORKLOAD = dict(L=(32, 32, 32, 32), beta=6.2, theta=1.0, seed=1, eps=0.005, sweeps=10, alpha=1.0)
 WORKLOAD_NAME = ("32^4 SU(3) Wilson + clover theta, beta 6.2, theta 1.0, Haar hot start; "
-                 "1 CL step (eps 0.005) + 10 adaptive gauge-cooling sweeps (D2 = <|f|>, alpha 1)")
+                 "1 CL step (eps 0.005) + 10 gauge-cooling sweeps (alpha_ad = alpha / D_1, alpha 1)")
 METRIC = "CL+cooling site-updates/s"
 UNIT = "site-updates/s"
 # Bytes that must move per site-update (links read + written once per CL step
@@ -170,7 +170,7 @@ def cpu_baseline(seconds=10.0, L=CPU_SAMPLE_L):
     import oracle as O
     w = WORKLOAD
     U = O.hot_start(L, w["seed"])
-    cp = O.cool_params(w["eps"], w["alpha"], O.D2_MEANABS, forced_sweeps=w["sweeps"])
+    cp = O.cool_params(w["eps"], w["alpha"], O.D1, forced_sweeps=w["sweeps"])
     V = 1
     for v in L:
         V *= v
@@ -188,6 +188,22 @@ def cpu_baseline(seconds=10.0, L=CPU_SAMPLE_L):
                       "(1 CL step + %d sweeps), %.1f s" % (L[0], V, reps, w["sweeps"], el)}
 
 
+def rank_max(x, device="cpu"):
+    """Max of a float over all ranks (identity without a process group)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    if torch.distributed.is_available() and torch.distributed.is_initialized() \
+            and torch.distributed.get_world_size() > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(sites_per_rank, ms_max, world):
+    """Whole-job site-updates/s: every rank advances its own lattice (weak
+    scaling), the job takes as long as the slowest rank."""
+    return world * sites_per_rank / (ms_max * 1e-3)
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -202,7 +218,7 @@ def run_form(cl, torch, prec_name, args, rank, stream):
     V = L[0] * L[1] * L[2] * L[3]
     lat = cl.Lattice(L, beta=w["beta"], theta=w["theta"], prec=prec, seed=w["seed"] + rank,
                      start=cl.CL_START_HOT, stream=stream.cuda_stream)
-    cp = cl.make_cool(w["eps"], w["alpha"], cl.CL_D2_MEANABS, forced_sweeps=w["sweeps"])
+    cp = cl.make_cool(w["eps"], w["alpha"], cl.CL_D1, forced_sweeps=w["sweeps"])
 
     def one_step():
         cl.cl_step(lat.h, w["eps"], 1)
@@ -295,11 +311,8 @@ def native(args):
     sampler.start()
     lat, V, ms, launches, phases, obs, one_step = run_form(cl, torch, "fp64", args, rank, stream)
     clocks = sampler.stop()
-    ms_t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if ws > 1:
-        torch.distributed.all_reduce(ms_t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(ms_t.item())
-    value = ws * V / (ms_max * 1e-3)
+    ms_max = rank_max(ms, "cuda")
+    value = job_value(V, ms_max, ws)
     sm_max = (clocks or {}).get("sm_max_mhz") or peaks.get("sm_max_mhz", 2070.0)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -307,7 +320,8 @@ def native(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": WORKLOAD_NAME, "lattice": list(args.L or WORKLOAD["L"]),
                    "beta": WORKLOAD["beta"], "theta": WORKLOAD["theta"], "eps": WORKLOAD["eps"],
-                   "cooling": "D2 mean |f|, alpha 1, 10 sweeps per step (forced count)",
+                   "cooling": "alpha_ad = alpha / D_1 (normalised unitarity norm), alpha 1, "
+                              "10 sweeps per step (fixed count)",
                    "precision": "fp64 links and arithmetic",
                    "l2": "no flush: the link fields (604 MB fp64 / 302 MB fp32) exceed the 129 MB L2",
                    "parallelism": "replicas x%d (independent chains)" % ws},
@@ -323,16 +337,14 @@ def native(args):
         "clocks": clocks,
     }
     result["e2e"] = e2e_measure(cl, torch, lat, V, one_step, max(2, min(args.steps, 5)))
-    if ws > 1:
-        t = torch.tensor([result["e2e"]["ms_per_step"]], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        result["e2e"]["value"] = ws * V / (float(t.item()) * 1e-3)
+    result["e2e"]["value"] = job_value(V, rank_max(result["e2e"]["ms_per_step"], "cuda"), ws)
     lat.close()
     if not args.no_fp32:
         lat32, V32, ms32, l32, ph32, obs32, _ = run_form(cl, torch, "fp32", args, rank, stream)
         lat32.close()
+        ms32 = rank_max(ms32, "cuda")
         result["forms"] = {"fp32_storage": {
-            "value": ws * V32 / (ms32 * 1e-3), "ms_per_step": ms32, "gpu_launches": l32,
+            "value": job_value(V32, ms32, ws), "ms_per_step": ms32, "gpu_launches": l32,
             "dtype": "f32 links + f64 exp/reprojection/reductions",
             "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in ph32.items()},
             "roofline": roofline_of("fp32", V32, ph32, sm_max),
@@ -349,15 +361,16 @@ def native(args):
 
 
 def reference(args):
+    """The oracle arm; under torchrun only rank 0 runs it, the others return."""
     ws, rank, _ = dist_setup()
     if rank != 0:
-        return
+        return None
     import oracle as O
     w = WORKLOAD
     L = CPU_SAMPLE_L
     V = L[0] * L[1] * L[2] * L[3]
     U = O.hot_start(L, w["seed"])
-    cp = O.cool_params(w["eps"], w["alpha"], O.D2_MEANABS, forced_sweeps=w["sweeps"])
+    cp = O.cool_params(w["eps"], w["alpha"], O.D1, forced_sweeps=w["sweeps"])
     times = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()

@@ -106,9 +106,10 @@ typedef struct {
 /* Create a lattice on the current CUDA device and initialise its links
  * (start, then the optional random gauge transformation).  cuda_stream is a
  * cudaStream_t (may be NULL).  On success *out owns the device memory
- * (per site: 64 complex 3x3 matrices -- links, a second link buffer,
- * inverses, plaquettes, their differences, the clover field and the drift
- * contributions -- plus cooling scratch: 9.4 KB in FP64, 4.7 KB in FP32).
+ * (per site: 70 complex 3x3 matrices -- links, a second link buffer,
+ * inverses, plaquettes, their differences, the clover field, the drift
+ * contributions and their partial sums -- plus cooling scratch: 10.3 KB in
+ * FP64, 5.1 KB in FP32).
  * Errors: CL_ERR_INVALID (NULL, extents < 1, V*6*9 beyond int range),
  * CL_ERR_OOM, CL_ERR_CUDA. */
 cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice** out);
@@ -179,7 +180,7 @@ enum {
   CL_PHASE_COOL_OMEGA = 4, /* Omega_x, Omega_x^{-1} */
   CL_PHASE_COOL_APPLY = 5, /* U <- Omega U Omega^{-1} */
   CL_PHASE_OBS = 6,        /* observables */
-  CL_PHASE_FORCE = 7,      /* per-plaquette drift contributions */
+  CL_PHASE_FORCE = 7,      /* per-plaquette drift contributions (two kernels with theta) */
   CL_NPHASE = 8
 };
 cl_status cl_set_timing(cl_lattice* lat, int on);

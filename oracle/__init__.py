@@ -61,6 +61,8 @@ def lib():
             "or_drift_at": (cint, [ip, dp, dbl, dbl, dbl, cint, i64p, dp]),
             "or_cl_step": (cint, [ip, dp, dbl, dbl, dbl, dbl, u64, u32]),
             "or_cl_step_at": (cint, [ip, dp, dbl, dbl, dbl, dbl, u64, u32, cint, i64p, dp]),
+            "or_step_sweep_at": (cint, [ip, dp, dbl, dbl, dbl, dbl, u64, u32, dbl, dbl, cint, i64p,
+                                        dp, dp]),
             "or_cool_gradient": (cint, [ip, dp, dp]),
             "or_cool_sweep": (cint, [ip, dp, dbl, dbl]),
             "or_cool": (cint, [ip, dp, ctypes.POINTER(CoolParams), ctypes.POINTER(CoolReport)]),
@@ -247,6 +249,21 @@ def cl_step_at(L, U, beta, theta, eps, seed, step, links):
                                len(links), links.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                _dp(out)), "cl_step_at")
     return out
+
+
+def step_sweep_at(L, U, beta, theta, eps, seed, step, eps_cool, alpha_ad, links):
+    """U' after one CL step and U'' after one cooling sweep (alpha_ad fixed) at the given links."""
+    U = _links(U, L)
+    links = np.ascontiguousarray(links, np.int64)
+    a = np.zeros((len(links), 3, 3), np.complex128)
+    b = np.zeros((len(links), 3, 3), np.complex128)
+    theta = complex(theta)
+    Lp, _k = _L(L)
+    _check(lib().or_step_sweep_at(Lp, _dp(U), beta, theta.real, theta.imag, eps, seed, step,
+                                  eps_cool, alpha_ad, len(links),
+                                  links.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), _dp(a),
+                                  _dp(b)), "step_sweep_at")
+    return a, b
 
 
 def cool_gradient(L, U):

@@ -838,6 +838,52 @@ int or_cl_step_at(const int L[4], const double* U, double beta, double th_re, do
   return 0;
 }
 
+// One CL step followed by one cooling sweep at fixed alpha_ad, evaluated
+// only at the chosen links: the post-step links that the cooling
+// transformations at x and x+mu need (the links at and into those sites)
+// are built from their own drifts, then Omega_x U'_{x,mu} Omega_{x+mu}^{-1}.
+int or_step_sweep_at(const int L[4], const double* U, double beta, double th_re, double th_im,
+                     double eps, uint64_t seed, uint32_t step, double eps_cool, double alpha_ad,
+                     int n, const int64_t* links, double* after_step, double* after_sweep) {
+  Lat g;
+  if (!make_lat(L, g) || n < 0) return -1;
+  for (int i = 0; i < n; ++i)
+    if (links[i] < 0 || links[i] >= 4 * g.V) return -2;
+  std::vector<Mat> Uv;
+  load_links(g, U, Uv);
+  std::vector<Mat> Uinv = inverses(Uv);
+  std::vector<Quad> quads = all_quads();
+  cd theta(th_re, th_im);
+  auto stepped = [&](int64_t l) {
+    Mat X = drift_one(g, Uv, Uinv, beta, theta, quads, l);
+    return cl_update_link(Uv[l], X, eps, seed, step, l / 4, (int)(l % 4));
+  };
+  auto omega = [&](int64_t y, bool inv) {
+    Mat G = zero();
+    for (int mu = 0; mu < 4; ++mu) {
+      Mat Uf = stepped(4 * y + mu);
+      Mat Ub = stepped(4 * g.dn[4 * y + mu] + mu);
+      G = add(G, sub(mul(Uf, dagger(Uf)), mul(dagger(Ub), Ub)));
+    }
+    Mat H = zero();
+    for (int a = 1; a <= 8; ++a) {
+      double fa = (2.0 * trace(mul(gellmann(a), G))).real();
+      H = add(H, scale(gellmann(a), -eps_cool * alpha_ad * fa));
+    }
+    Mat O = expm(H);
+    return inv ? inverse(O) : O;
+  };
+#pragma omp parallel for schedule(dynamic)
+  for (int i = 0; i < n; ++i) {
+    int64_t l = links[i], x = l / 4;
+    int mu = (int)(l % 4);
+    Mat Us = stepped(l);
+    store(Us, after_step + 18 * i);
+    store(mul(mul(omega(x, false), Us), omega(g.up[4 * x + mu], true)), after_sweep + 18 * i);
+  }
+  return 0;
+}
+
 int or_cool_gradient(const int L[4], const double* U, double* f) {
   Lat g;
   if (!make_lat(L, g)) return -1;

@@ -78,6 +78,14 @@ int or_cl_step_at(const int L[4], const double* U, double beta,
                   double theta_re, double theta_im, double eps, uint64_t seed,
                   uint32_t step, int n, const int64_t* links, double* Unew);
 
+/* One CL step then one cooling sweep with fixed alpha_ad, evaluated only at
+ * n chosen links (for sampled checks on large lattices): after_step gets U'
+ * and after_sweep Omega_x U' Omega_{x+mu}^{-1}, 18 doubles per link. */
+int or_step_sweep_at(const int L[4], const double* U, double beta, double theta_re,
+                     double theta_im, double eps, uint64_t seed, uint32_t step, double eps_cool,
+                     double alpha_ad, int n, const int64_t* links, double* after_step,
+                     double* after_sweep);
+
 /* Gauge-cooling gradient f_ax = 2 Tr[lambda_a sum_mu (U U^+ - U^+_{x-mu} U_{x-mu})] (V*8). */
 int or_cool_gradient(const int L[4], const double* U, double* f);
 /* One cooling sweep with step eps*alpha_ad, all links at once. */

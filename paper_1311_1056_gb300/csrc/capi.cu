@@ -51,6 +51,7 @@ struct cl_lattice {
   void* Pq;    // plaquettes [6][9][V]
   void* Dq;    // P - P^{-1} [6][9][V]
   void* C;     // per-plaquette drift contributions [24][9][V]
+  void* Gq;    // partial sums of transported dual fields [6][9][V]
   void* F;     // clover field, SoA [6][9][V]
   void* f;     // cooling gradient [8][V] (FP64 in both forms)
   void* Om;    // packed Hermitian Omega [9][V]
@@ -88,8 +89,8 @@ cudaEvent_t take_event(cl_lattice* l) {
 // Launch through f(); with timing on, bracket it by two events on the
 // lattice's stream and remember them under `phase`.
 template <typename Fn>
-cudaError_t timed(cl_lattice* l, int phase, Fn f) {
-  l->launches++;
+cudaError_t timed(cl_lattice* l, int phase, Fn f, int kernels = 1) {
+  l->launches += kernels;
   if (!l->timing) return f();
   cudaEvent_t a = take_event(l), b = take_event(l);
   if (!a || !b) return cudaErrorMemoryAllocation;
@@ -137,8 +138,9 @@ cudaError_t do_force(cl_lattice* l, bool th, double sre, double sim) {
     });
   if (e == cudaSuccess)
     e = timed(l, CL_PHASE_FORCE, [&] {
-      return launch_plaq_force(l->prec, th, l->g, l->U, l->Ui, l->Pq, l->Dq, l->F, l->C, l->p.beta, l->st);
-    });
+      return launch_plaq_force(l->prec, th, l->g, l->U, l->Ui, l->Pq, l->Dq, l->F, l->Gq, l->C, l->p.beta,
+                               l->st);
+    }, (th && l->prec == 0) ? 2 : 1);
   return e;
 }
 
@@ -275,6 +277,7 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
   alloc(&l->Pq, l->esz * 6 * 9 * Vs);
   alloc(&l->Dq, l->esz * 6 * 9 * Vs);
   alloc(&l->C, l->esz * 24 * 9 * Vs);
+  alloc(&l->Gq, l->esz * 6 * 9 * Vs);
   alloc(&l->F, l->esz * 6 * 9 * Vs);
   alloc(&l->f, sizeof(double) * 8 * Vs);
   alloc(&l->Om, real_size(l) * 9 * Vs);
@@ -519,7 +522,7 @@ cl_status cl_synchronize(cl_lattice* l) {
 
 void cl_free(cl_lattice* l) {
   if (!l) return;
-  void* bufs[] = {l->U, l->Un, l->Ui, l->Pq, l->Dq, l->C, l->F, l->f, l->Om, l->Omi, l->partials, l->cs, l->obs,
+  void* bufs[] = {l->U, l->Un, l->Ui, l->Pq, l->Dq, l->C, l->Gq, l->F, l->f, l->Om, l->Omi, l->partials, l->cs, l->obs,
                   l->stage, l->qsite};
   if (l->st) cudaStreamSynchronize(l->st);
   for (void* b : bufs)

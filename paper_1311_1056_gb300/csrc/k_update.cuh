@@ -183,96 +183,114 @@ __global__ void __launch_bounds__(128) k_clover_rot(Geo g, const typename vec2_o
 // ----------------------------------------------------- plaquette drift
 // Contributions of the plaquette (x, p) to its four links, into
 // C[4p + slot]: slot 0 U_mu(x), 1 U_nu(x), 2 U_nu(x+mu), 3 U_mu(x+nu).
-// Partial sums are parked in the output slots and completed once K is known
-// (the thread re-reads only what it wrote itself).
-template <typename T, bool THETA>
-__global__ void __launch_bounds__(128) k_plaq_force(Geo g, const typename vec2_of<T>::type* __restrict__ U,
-                                                    const typename vec2_of<T>::type* __restrict__ Ui,
-                                                    const typename vec2_of<T>::type* __restrict__ Pq,
-                                                    const typename vec2_of<T>::type* __restrict__ Dq,
-                                                    const typename vec2_of<T>::type* __restrict__ F,
-                                                    typename vec2_of<T>::type* C, T beta6) {
-  const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p), pc = 5 - p;
+// With theta the work has two stages: a handles corners c0..c2 (G0 + G1^ +
+// G2^ and the slot 0 / slot 2 partials, parked in C); b adds corner c3, forms
+// K and completes the four slots.  In FP64 (36 registers per matrix) the
+// stages run as two kernels with the partial G^ parked in Gq, so neither
+// spills; in FP32 one kernel runs both.
+template <typename T>
+__global__ void __launch_bounds__(128) k_plaq_force_wilson(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                           const typename vec2_of<T>::type* __restrict__ Ui,
+                                                           const typename vec2_of<T>::type* __restrict__ Dq,
+                                                           typename vec2_of<T>::type* C, T beta6) {
+  const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p);
   const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
-  const unsigned long long m = (p == 1 || p == 4) ? 0x8000000000000000ull : 0ull;
-  int x[4];
-  site_coords(g, s, x);
-  const int c1 = hop(g, s, x, mu, 1), c3 = hop(g, s, x, nu, 1);
-  mat<T> D, M, t;
+  mat<T> D, M, t, a;
   load(D, Dq, p, s, g.V);
-  if (!THETA) {
-    mat<T> a;
-    scaled(M, -beta6, D);
-    store(C, 4 * p + 0, s, g.V, M);
-    load(a, Ui, mu, s, g.V);
-    mul(t, a, M);
-    load(a, U, mu, s, g.V);
-    mul(M, t, a);
-    store(C, 4 * p + 2, s, g.V, M);
-    scaled(M, beta6, D);
-    store(C, 4 * p + 1, s, g.V, M);
-    load(a, Ui, nu, s, g.V);
-    mul(t, a, M);
-    load(a, U, nu, s, g.V);
-    mul(M, t, a);
-    store(C, 4 * p + 3, s, g.V, M);
-    return;
-  }
-  mat<T> Gh, G, q;
+  scaled(M, -beta6, D);
+  store(C, 4 * p + 0, s, g.V, M);
+  load(a, Ui, mu, s, g.V);
+  mul(t, a, M);
+  load(a, U, mu, s, g.V);
+  mul(M, t, a);
+  store(C, 4 * p + 2, s, g.V, M);
+  scaled(M, beta6, D);
+  store(C, 4 * p + 1, s, g.V, M);
+  load(a, Ui, nu, s, g.V);
+  mul(t, a, M);
+  load(a, U, nu, s, g.V);
+  mul(M, t, a);
+  store(C, 4 * p + 3, s, g.V, M);
+}
+
+// Corners c0..c2: G^ (partial) into Gh, slot 0 and slot 2 partials into C.
+template <typename T>
+__device__ __forceinline__ void force_stage_a(mat<T>& Gh, const Geo& g, int s, const int x[4], int p,
+                                              const typename vec2_of<T>::type* __restrict__ U,
+                                              const typename vec2_of<T>::type* __restrict__ Ui,
+                                              const typename vec2_of<T>::type* __restrict__ Dq,
+                                              const typename vec2_of<T>::type* __restrict__ F,
+                                              typename vec2_of<T>::type* C, T beta6) {
+  const int mu = plane_mu(p), nu = plane_nu(p), pc = 5 - p;
+  const unsigned long long m = (p == 1 || p == 4) ? 0x8000000000000000ull : 0ull;
+  const int c1 = hop(g, s, x, mu, 1);
+  mat<T> D, M, t, q;
+  load(D, Dq, p, s, g.V);
   // corner c0: slot 0 partial = [D, G0] - (beta/6) D
   load_signed(Gh, F, pc, s, g.V, m);
   scaled(M, -beta6, D);
   commutator_acc(M, D, Gh);
   store(C, 4 * p + 0, s, g.V, M);
   // corner c1: G1^ = a G1 a^{-1}; slot 2 partial (c0 frame) = slot 0 partial + [D, G1^]
-  {
-    mat<T> a;
-    load_signed(G, F, pc, c1, g.V, m);
-    load(a, U, mu, s, g.V);
-    mul(t, a, G);
-    load(a, Ui, mu, s, g.V);
-    mul(q, t, a);
-  }
+  load_signed(t, F, pc, c1, g.V, m);
+  load(q, U, mu, s, g.V);
+  mul(D, q, t);  // a G1 (D is re-read below)
+  load(q, Ui, mu, s, g.V);
+  mul(t, D, q);  // G1^
 #pragma unroll
-  for (int k = 0; k < 9; ++k) Gh.e[k] = cadd(Gh.e[k], q.e[k]);
-  commutator_acc(M, D, q);
+  for (int k = 0; k < 9; ++k) Gh.e[k] = cadd(Gh.e[k], t.e[k]);
+  load(D, Dq, p, s, g.V);
+  commutator_acc(M, D, t);
   store(C, 4 * p + 2, s, g.V, M);
   // corner c2: G2^ = (ab) G2 (ab)^{-1}
-  {
-    mat<T> a, b, ab;
-    load(a, U, mu, s, g.V);
-    load(b, U, nu, c1, g.V);
-    mul(ab, a, b);
-    load_signed(G, F, pc, hop(g, c1, x, nu, 1), g.V, m);
-    mul(t, ab, G);
-    load(a, Ui, mu, s, g.V);
-    load(b, Ui, nu, c1, g.V);
-    mul(ab, b, a);
-    mul_acc<+1>(Gh, t, ab);
-  }
-  // corner c3: G3r = u G3 u^{-1}, G3^ = P G3r P^{-1}; slot 3 partial = [D, G3r] + (beta/6) D
-  {
-    mat<T> u;
-    load_signed(G, F, pc, c3, g.V, m);
-    load(u, U, nu, s, g.V);
-    mul(t, u, G);
-    load(u, Ui, nu, s, g.V);
-    mul(q, t, u);
-  }
+  load(M, U, mu, s, g.V);
+  load(q, U, nu, c1, g.V);
+  mul(D, M, q);  // ab
+  load_signed(q, F, pc, hop(g, c1, x, nu, 1), g.V, m);
+  mul(t, D, q);  // ab G2
+  load(M, Ui, mu, s, g.V);
+  load(q, Ui, nu, c1, g.V);
+  mul(D, q, M);  // (ab)^{-1}
+  mul_acc<+1>(Gh, t, D);
+}
+
+// Corner c3, K, and the four slots completed; Gh holds the stage-a sum.
+template <typename T>
+__device__ __forceinline__ void force_stage_b(mat<T>& Gh, const Geo& g, int s, const int x[4], int p,
+                                              const typename vec2_of<T>::type* __restrict__ U,
+                                              const typename vec2_of<T>::type* __restrict__ Ui,
+                                              const typename vec2_of<T>::type* __restrict__ Pq,
+                                              const typename vec2_of<T>::type* __restrict__ Dq,
+                                              const typename vec2_of<T>::type* __restrict__ F,
+                                              typename vec2_of<T>::type* C, T beta6) {
+  const int mu = plane_mu(p), nu = plane_nu(p), pc = 5 - p;
+  const unsigned long long m = (p == 1 || p == 4) ? 0x8000000000000000ull : 0ull;
+  const int c3 = hop(g, s, x, nu, 1);
+  mat<T> D, M, t, q;
+  // corner c3: G3r = u G3 u^{-1}; slot 3 partial = [D, G3r] + (beta/6) D
+  load_signed(q, F, pc, c3, g.V, m);
+  load(M, U, nu, s, g.V);
+  mul(t, M, q);
+  load(M, Ui, nu, s, g.V);
+  mul(q, t, M);
+  load(D, Dq, p, s, g.V);
   scaled(M, beta6, D);
   commutator_acc(M, D, q);
   store(C, 4 * p + 3, s, g.V, M);
-  mat<T> P, Pi;
+  // G^ += P G3r P^{-1}, with P^{-1} = P - D formed in place
+  mat<T>& P = M;
   load(P, Pq, p, s, g.V);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) Pi.e[k] = csub(P.e[k], D.e[k]);
   mul(t, P, q);
-  mul_acc<+1>(Gh, t, Pi);
-  // K = G^ P + P^{-1} G^
+#pragma unroll
+  for (int k = 0; k < 9; ++k) P.e[k] = csub(P.e[k], D.e[k]);  // P^{-1}
+  mul_acc<+1>(Gh, t, P);
+  // K = P^{-1} G^ + G^ P
   mat<T>& K = q;
-  mul(K, Gh, P);
-  mul_acc<+1>(K, Pi, Gh);
+  mul(K, P, Gh);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) P.e[k] = cadd(P.e[k], D.e[k]);  // P again
+  mul_acc<+1>(K, Gh, P);
   // slot 1: -K + (beta/6) D
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
@@ -286,29 +304,75 @@ __global__ void __launch_bounds__(128) k_plaq_force(Geo g, const typename vec2_o
   for (int k = 0; k < 9; ++k) M.e[k] = cadd(M.e[k], K.e[k]);
   store(C, 4 * p + 0, s, g.V, M);
   // slot 2: a^{-1} (K + partial) a
-  {
-    mat<T> a;
-    load_rw(M, C, 4 * p + 2, s, g.V);
+  load_rw(M, C, 4 * p + 2, s, g.V);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) M.e[k] = cadd(M.e[k], K.e[k]);
-    load(a, Ui, mu, s, g.V);
-    mul(t, a, M);
-    load(a, U, mu, s, g.V);
-    mul(M, t, a);
-    store(C, 4 * p + 2, s, g.V, M);
-  }
+  for (int k = 0; k < 9; ++k) M.e[k] = cadd(M.e[k], K.e[k]);
+  load(Gh, Ui, mu, s, g.V);
+  mul(t, Gh, M);
+  load(Gh, U, mu, s, g.V);
+  mul(M, t, Gh);
+  store(C, 4 * p + 2, s, g.V, M);
   // slot 3: u^{-1} (-K + partial) u
-  {
-    mat<T> u;
-    load_rw(M, C, 4 * p + 3, s, g.V);
+  load_rw(M, C, 4 * p + 3, s, g.V);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) M.e[k] = csub(M.e[k], K.e[k]);
-    load(u, Ui, nu, s, g.V);
-    mul(t, u, M);
-    load(u, U, nu, s, g.V);
-    mul(M, t, u);
-    store(C, 4 * p + 3, s, g.V, M);
-  }
+  for (int k = 0; k < 9; ++k) M.e[k] = csub(M.e[k], K.e[k]);
+  load(Gh, Ui, nu, s, g.V);
+  mul(t, Gh, M);
+  load(Gh, U, nu, s, g.V);
+  mul(M, t, Gh);
+  store(C, 4 * p + 3, s, g.V, M);
+}
+
+// Split form (FP64): stage a, G^ parked in Gq, stage b.
+template <typename T>
+__global__ void __launch_bounds__(128) k_plaq_force_a(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                      const typename vec2_of<T>::type* __restrict__ Ui,
+                                                      const typename vec2_of<T>::type* __restrict__ Dq,
+                                                      const typename vec2_of<T>::type* __restrict__ F,
+                                                      typename vec2_of<T>::type* __restrict__ Gq,
+                                                      typename vec2_of<T>::type* C, T beta6) {
+  const int p = blockIdx.x % 6;
+  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int x[4];
+  site_coords(g, s, x);
+  mat<T> Gh;
+  force_stage_a(Gh, g, s, x, p, U, Ui, Dq, F, C, beta6);
+  store(Gq, p, s, g.V, Gh);
+}
+template <typename T>
+__global__ void __launch_bounds__(128) k_plaq_force_b(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                      const typename vec2_of<T>::type* __restrict__ Ui,
+                                                      const typename vec2_of<T>::type* __restrict__ Pq,
+                                                      const typename vec2_of<T>::type* __restrict__ Dq,
+                                                      const typename vec2_of<T>::type* __restrict__ F,
+                                                      const typename vec2_of<T>::type* __restrict__ Gq,
+                                                      typename vec2_of<T>::type* C, T beta6) {
+  const int p = blockIdx.x % 6;
+  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int x[4];
+  site_coords(g, s, x);
+  mat<T> Gh;
+  load(Gh, Gq, p, s, g.V);
+  force_stage_b(Gh, g, s, x, p, U, Ui, Pq, Dq, F, C, beta6);
+}
+// Fused form (FP32, which needs no split to stay in registers).
+template <typename T>
+__global__ void __launch_bounds__(128) k_plaq_force_ab(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                       const typename vec2_of<T>::type* __restrict__ Ui,
+                                                       const typename vec2_of<T>::type* __restrict__ Pq,
+                                                       const typename vec2_of<T>::type* __restrict__ Dq,
+                                                       const typename vec2_of<T>::type* __restrict__ F,
+                                                       typename vec2_of<T>::type* C, T beta6) {
+  const int p = blockIdx.x % 6;
+  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int x[4];
+  site_coords(g, s, x);
+  mat<T> Gh;
+  force_stage_a(Gh, g, s, x, p, U, Ui, Dq, F, C, beta6);
+  force_stage_b(Gh, g, s, x, p, U, Ui, Pq, Dq, F, C, beta6);
 }
 
 // Noise matrix sum_a eta_a lambda_a (Hermitian) into the imaginary part of A,

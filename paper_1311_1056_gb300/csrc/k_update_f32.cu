@@ -33,16 +33,17 @@ cudaError_t launch_clover_rot_f32(const GeoH& h, const void* U, const void* Ui, 
 }
 
 cudaError_t launch_plaq_force_f32(bool theta, const GeoH& h, const void* U, const void* Ui,
-                                 const void* Pq, const void* Dq, const void* F, void* C,
+                                 const void* Pq, const void* Dq, const void* F, void* Gq, void* C,
                                  double beta, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
   const float b6 = (float)(beta / 6.0);
-  if (theta)
-    k_plaq_force<float, true><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
-                                                          (const V2*)Dq, (const V2*)F, (V2*)C, b6);
-  else
-    k_plaq_force<float, false><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
-                                                           (const V2*)Dq, (const V2*)F, (V2*)C, b6);
+  if (!theta) {
+    k_plaq_force_wilson<float><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+                                                         (V2*)C, b6);
+    return cudaGetLastError();
+  }
+  k_plaq_force_ab<float><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
+                                                      (const V2*)Dq, (const V2*)F, (V2*)C, b6);
   return cudaGetLastError();
 }
 

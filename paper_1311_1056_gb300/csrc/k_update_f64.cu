@@ -33,16 +33,19 @@ cudaError_t launch_clover_rot_f64(const GeoH& h, const void* U, const void* Ui, 
 }
 
 cudaError_t launch_plaq_force_f64(bool theta, const GeoH& h, const void* U, const void* Ui,
-                                 const void* Pq, const void* Dq, const void* F, void* C,
+                                 const void* Pq, const void* Dq, const void* F, void* Gq, void* C,
                                  double beta, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
   const double b6 = (double)(beta / 6.0);
-  if (theta)
-    k_plaq_force<double, true><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
-                                                          (const V2*)Dq, (const V2*)F, (V2*)C, b6);
-  else
-    k_plaq_force<double, false><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
-                                                           (const V2*)Dq, (const V2*)F, (V2*)C, b6);
+  if (!theta) {
+    k_plaq_force_wilson<double><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+                                                         (V2*)C, b6);
+    return cudaGetLastError();
+  }
+  k_plaq_force_a<double><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+                                                  (const V2*)F, (V2*)Gq, (V2*)C, b6);
+  k_plaq_force_b<double><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
+                                                  (const V2*)Dq, (const V2*)F, (const V2*)Gq, (V2*)C, b6);
   return cudaGetLastError();
 }
 
@@ -71,7 +74,7 @@ cudaError_t launch_plaq_f32(const GeoH&, const void*, const void*, void*, void*,
 cudaError_t launch_clover_rot_f32(const GeoH&, const void*, const void*, const void*, void*, double,
                                   double, cudaStream_t);
 cudaError_t launch_plaq_force_f32(bool, const GeoH&, const void*, const void*, const void*,
-                                  const void*, const void*, void*, double, cudaStream_t);
+                                  const void*, const void*, void*, void*, double, cudaStream_t);
 cudaError_t launch_update_gather_f32(int, const GeoH&, const void*, const void*, void*, double,
                                      uint64_t, uint32_t, cudaStream_t);
 
@@ -88,10 +91,10 @@ cudaError_t launch_clover_rot(int prec, const GeoH& h, const void* U, const void
                    : launch_clover_rot_f32(h, U, Ui, Dq, F, sre, sim, st);
 }
 cudaError_t launch_plaq_force(int prec, bool theta, const GeoH& h, const void* U, const void* Ui,
-                              const void* Pq, const void* Dq, const void* F, void* C, double beta,
-                              cudaStream_t st) {
-  return prec == 0 ? launch_plaq_force_f64(theta, h, U, Ui, Pq, Dq, F, C, beta, st)
-                   : launch_plaq_force_f32(theta, h, U, Ui, Pq, Dq, F, C, beta, st);
+                              const void* Pq, const void* Dq, const void* F, void* Gq, void* C,
+                              double beta, cudaStream_t st) {
+  return prec == 0 ? launch_plaq_force_f64(theta, h, U, Ui, Pq, Dq, F, Gq, C, beta, st)
+                   : launch_plaq_force_f32(theta, h, U, Ui, Pq, Dq, F, Gq, C, beta, st);
 }
 cudaError_t launch_update_gather(int prec, int mode, const GeoH& h, const void* U, const void* C,
                                  void* out, double eps, uint64_t seed, uint32_t step, cudaStream_t st) {

@@ -57,9 +57,11 @@ cudaError_t launch_plaq(int prec, const GeoH& g, const void* U, const void* Ui, 
                         cudaStream_t st);
 cudaError_t launch_clover_rot(int prec, const GeoH& g, const void* U, const void* Ui, const void* Dq,
                               void* F, double scale_re, double scale_im, cudaStream_t st);
+// (theta != 0 runs two kernels, parking partial sums of the transported dual
+// fields in Gq, six planes.)
 cudaError_t launch_plaq_force(int prec, bool theta, const GeoH& g, const void* U, const void* Ui,
-                              const void* Pq, const void* Dq, const void* F, void* C, double beta,
-                              cudaStream_t st);
+                              const void* Pq, const void* Dq, const void* F, void* Gq, void* C,
+                              double beta, cudaStream_t st);
 cudaError_t launch_update_gather(int prec, int mode, const GeoH& g, const void* U, const void* C,
                                  void* out, double eps, uint64_t seed, uint32_t step, cudaStream_t st);
 // Cooling: gradient f (8 FP64 values per site, [a][V]) + partial sums; the

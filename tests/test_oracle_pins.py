@@ -518,3 +518,15 @@ def test_golden_cfg0_is_current():
     assert stored["start"]["un"] > 1.05 and abs(stored["start"]["plaq_re"] - 1) < 1e-14
     assert stored["steps"][-1]["un"] < 1.001
     assert 0.5 < stored["steps"][-1]["plaq_re"] < 0.7
+
+
+def test_step_sweep_at_equals_full_lattice():
+    """The sampled step + sweep routine composes the full-lattice ones."""
+    L = (3, 2, 3, 2)
+    U = LI.sl3c_lattice(L, seed=23, spread=0.15)
+    links = LI.sample_links(LI.volume(L), 10, 4)
+    a, b = O.step_sweep_at(L, U, 5.9, 0.8 + 0.2j, 0.01, 7, 2, 0.01, 1.3, links)
+    Us = O.cl_step(L, U, 5.9, 0.8 + 0.2j, 0.01, 7, 2)
+    Uc = O.cool_sweep(L, Us, 0.01, 1.3)
+    np.testing.assert_allclose(a, Us.reshape(-1, 3, 3)[links], atol=1e-14)
+    np.testing.assert_allclose(b, Uc.reshape(-1, 3, 3)[links], atol=1e-13)
