@@ -126,6 +126,10 @@ cl_status cl_step(cl_lattice* lat, double eps, int n_steps);
  * synchronised).  With a report: CL_ERR_NONFINITE if the links hold a
  * NaN/Inf.  Errors: CL_ERR_INVALID (bad mode/bounds), CL_ERR_CUDA. */
 cl_status cl_cool(cl_lattice* lat, const cl_cool_params* cp, cl_cool_report* report);
+/* The report of the most recent cooling call on this lattice, whether it ran
+ * through cl_cool, cl_trajectory, a replayed step graph or a batch (waits for
+ * the lattice's stream).  Errors: CL_ERR_INVALID, CL_ERR_NONFINITE, CL_ERR_CUDA. */
+cl_status cl_cool_last_report(cl_lattice* lat, cl_cool_report* report);
 
 /* Observables of the current links (synchronises).  CL_ERR_NONFINITE when a
  * link holds a NaN/Inf (*out is still written). */
@@ -140,6 +144,44 @@ cl_status cl_observables(cl_lattice* lat, cl_obs* out);
 cl_status cl_trajectory(cl_lattice* lat, double eps, int n_steps, const cl_cool_params* cp,
                         int obs_every, cl_obs* obs_out, cl_cool_report* rep_out,
                         double runaway_un);
+
+/* A non-blocking CUDA stream owned by the caller (for cl_init_lattice when
+ * the caller has none of its own); destroy it after the lattices that use it
+ * (cl_stream_destroy waits for its work first).  Errors: CL_ERR_INVALID,
+ * CL_ERR_CUDA. */
+cl_status cl_stream_create(void** stream);
+cl_status cl_stream_destroy(void* stream);
+
+/* One step of the hot path as a CUDA graph.  cl_capture_step records [CL
+ * step, cooling with cp (NULL: none)] on the lattice's stream, which must not
+ * be the legacy default stream; nothing runs at capture.  cl_replay enqueues
+ * the recorded step n_steps times (one graph launch each; the Philox step
+ * counter lives on the device, so every replay draws fresh noise).  The
+ * cooling rule still decides on the device how many of the recorded n_max
+ * sweeps run.  Replays and ordinary calls may be mixed.
+ * Errors: CL_ERR_INVALID (NULL stream, bad eps/cp, nothing captured), CL_ERR_CUDA. */
+cl_status cl_capture_step(cl_lattice* lat, double eps, const cl_cool_params* cp);
+cl_status cl_replay(cl_lattice* lat, int n_steps);
+
+/* An ensemble of independent chains advanced together: one CUDA graph forks
+ * from an internal stream to every lattice's own stream, records one step of
+ * each chain (eps[i], and cooling cps[i] when with_cooling), and joins back,
+ * so one graph launch advances every chain by one step and the GPU runs the
+ * chains' kernels concurrently.  The lattices stay owned by the caller and
+ * must outlive the batch; while in a batch they are advanced with
+ * cl_batch_run (a lattice stepped on its own is detected and refused with
+ * CL_ERR_INVALID).  cl_batch_run orders itself after work already queued on
+ * the lattices' streams, and later per-lattice calls (observables, links,
+ * cooling report) order themselves after it; cl_batch_synchronize waits for
+ * the batch on the host.
+ * Errors: CL_ERR_INVALID (n < 1, NULL, shared lattices or streams, default
+ * stream), CL_ERR_CUDA. */
+typedef struct cl_batch cl_batch;
+cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
+                          const cl_cool_params* cps, int with_cooling, cl_batch** out);
+cl_status cl_batch_run(cl_batch* batch, int n_steps);
+cl_status cl_batch_synchronize(cl_batch* batch);
+void cl_batch_free(cl_batch* batch);
 
 /* Links as host AoS doubles (layout above), any precision (FP32 links are
  * widened).  host_aos holds V*4*18 doubles; pinned memory copies fastest.

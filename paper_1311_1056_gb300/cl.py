@@ -88,6 +88,17 @@ SIGNATURES = {
     "cl_free": (None, [_P]),
     "cl_observables_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, _P, _P]),
+    "cl_cool_last_report": (ctypes.c_int, [_P, ctypes.POINTER(cl_cool_report)]),
+    "cl_stream_create": (ctypes.c_int, [ctypes.POINTER(_P)]),
+    "cl_stream_destroy": (ctypes.c_int, [_P]),
+    "cl_capture_step": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(cl_cool_params)]),
+    "cl_replay": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cl_batch_create": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), _dp,
+                                       ctypes.POINTER(cl_cool_params), ctypes.c_int,
+                                       ctypes.POINTER(_P)]),
+    "cl_batch_run": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cl_batch_synchronize": (ctypes.c_int, [_P]),
+    "cl_batch_free": (None, [_P]),
     "cl_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "cl_last_error": (ctypes.c_char_p, []),
     "cl_version": (ctypes.c_int, []),
@@ -145,6 +156,54 @@ def cl_cool(lat, cp, want_report=True):
     rep = cl_cool_report()
     _check(load().cl_cool(lat, ctypes.byref(cp), ctypes.byref(rep) if want_report else None), "cl_cool")
     return rep.as_dict() if want_report else None
+
+
+def cl_cool_last_report(lat):
+    rep = cl_cool_report()
+    _check(load().cl_cool_last_report(lat, ctypes.byref(rep)), "cl_cool_last_report")
+    return rep.as_dict()
+
+
+def cl_stream_create():
+    h = _P()
+    _check(load().cl_stream_create(ctypes.byref(h)), "cl_stream_create")
+    return h.value
+
+
+def cl_stream_destroy(stream):
+    _check(load().cl_stream_destroy(_P(stream)), "cl_stream_destroy")
+
+
+def cl_capture_step(lat, eps, cp=None):
+    _check(load().cl_capture_step(lat, eps, ctypes.byref(cp) if cp is not None else None),
+           "cl_capture_step")
+
+
+def cl_replay(lat, n_steps):
+    _check(load().cl_replay(lat, n_steps), "cl_replay")
+
+
+def cl_batch_create(lats, eps, cps=None):
+    n = len(lats)
+    hs = (_P * n)(*[ctypes.cast(h, _P) for h in lats])
+    e = np.ascontiguousarray(np.broadcast_to(np.asarray(eps, dtype=np.float64), (n,)))
+    cp_arr = (cl_cool_params * n)(*cps) if cps is not None else None
+    b = _P()
+    _check(load().cl_batch_create(n, hs, e.ctypes.data_as(_dp), cp_arr, int(cps is not None),
+                                  ctypes.byref(b)), "cl_batch_create")
+    return b
+
+
+def cl_batch_run(batch, n_steps):
+    _check(load().cl_batch_run(batch, n_steps), "cl_batch_run")
+
+
+def cl_batch_synchronize(batch):
+    _check(load().cl_batch_synchronize(batch), "cl_batch_synchronize")
+
+
+def cl_batch_free(batch):
+    load().cl_batch_free(batch)
 
 
 def cl_observables(lat, check=True):
@@ -280,15 +339,52 @@ def make_cool(eps, alpha=1.0, mode=CL_D0, n_min=0, n_max=0, tol_rel=1e-3, d_floo
     return cl_cool_params(eps, alpha, mode, n_min, n_max, tol_rel, d_floor, d_guard, forced_sweeps)
 
 
+class Batch:
+    """Owning wrapper of cl_batch: one graph launch advances every chain by
+    one step.  The Lattice objects must outlive it and have distinct,
+    non-default streams (Lattice(..., own_stream=True))."""
+
+    def __init__(self, lats, eps, cps=None):
+        self.lats = list(lats)
+        self.h = None
+        self.h = cl_batch_create([l.h for l in self.lats], eps, cps)
+
+    def run(self, n_steps=1):
+        cl_batch_run(self.h, n_steps)
+
+    def synchronize(self):
+        cl_batch_synchronize(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            cl_batch_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Lattice:
     """Owning wrapper: frees the device lattice when closed or collected."""
 
     def __init__(self, L, beta=6.0, theta=0.0, prec=CL_FP64, seed=1, start=CL_START_COLD,
-                 gauge_sigma=0.0, stream=0):
+                 gauge_sigma=0.0, stream=0, own_stream=False):
         self.L = tuple(int(v) for v in L)
         self.V = int(np.prod(self.L))
         self.params = make_params(L, beta, theta, prec, seed, start, gauge_sigma)
-        self.h = cl_init_lattice(self.params, stream)
+        self.h = None
+        self._own = cl_stream_create() if own_stream else None
+        self.stream = self._own if own_stream else stream
+        self.h = cl_init_lattice(self.params, self.stream)
 
     def step(self, eps, n=1):
         cl_step(self.h, eps, n)
@@ -298,6 +394,18 @@ class Lattice:
 
     def observables(self):
         return cl_observables(self.h)
+
+    def last_cool_report(self):
+        return cl_cool_last_report(self.h)
+
+    def capture_step(self, eps, cp=None):
+        cl_capture_step(self.h, eps, cp)
+
+    def replay(self, n_steps=1):
+        cl_replay(self.h, n_steps)
+
+    def synchronize(self):
+        cl_synchronize(self.h)
 
     def trajectory(self, eps, n_steps, cp=None, obs_every=0, runaway_un=0.0):
         return cl_trajectory(self.h, eps, n_steps, cp, obs_every, runaway_un)
@@ -328,6 +436,9 @@ class Lattice:
         if getattr(self, "h", None):
             cl_free(self.h)
             self.h = None
+        if getattr(self, "_own", None):
+            cl_stream_destroy(self._own)
+            self._own = None
 
     def __enter__(self):
         return self

@@ -61,8 +61,13 @@ struct cl_lattice {
   ObsOut* obs;
   double* stage;  // AoS double staging, V*4*18 (allocated on first use)
   double* qsite;  // per-site q_L (on first use)
-  uint64_t step;
+  uint64_t step;       // host mirror of *step_dev
+  uint32_t* step_dev;  // Philox step counter read by the update kernel
   int64_t launches;
+  // step graphs (cl_capture_step): variant v starts from the link buffer in gU[v]
+  cudaGraphExec_t gexec[2];
+  void* gU[2];
+  int64_t glaunches;  // kernels in one captured step
   // optional per-phase CUDA-event timing (cl_set_timing)
   int timing;
   std::vector<cudaEvent_t>* ev_pool;
@@ -151,9 +156,10 @@ cl_status do_steps(cl_lattice* l, double eps, int n) {
   for (int i = 0; i < n; ++i) {
     CK(do_force(l, th, sre, sim));
     CK(timed(l, CL_PHASE_UPDATE, [&] {
-      return launch_update_gather(l->prec, 0, l->g, l->U, l->C, l->Un, eps, l->p.seed,
-                                  (uint32_t)l->step, l->st);
+      return launch_update_gather(l->prec, 0, l->g, l->U, l->C, l->Un, eps, l->p.seed, l->step_dev,
+                                  l->st);
     }));
+    CK(timed(l, CL_PHASE_UPDATE, [&] { return launch_step_bump(l->step_dev, l->st); }));
     std::swap(l->U, l->Un);
     l->step++;
   }
@@ -285,11 +291,13 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
   alloc((void**)&l->partials, sizeof(double) * NQ_OBS * (size_t)reduce_blocks(l->g.V));
   alloc((void**)&l->cs, sizeof(CoolState));
   alloc((void**)&l->obs, sizeof(ObsOut));
+  alloc((void**)&l->step_dev, sizeof(uint32_t));
   if (s != CL_OK) {
     cl_free(l);
     return s;
   }
   cudaError_t e = cudaMemsetAsync(l->cs, 0, sizeof(CoolState), l->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(l->step_dev, 0, sizeof(uint32_t), l->st);
   if (e == cudaSuccess)
     e = params->start == CL_START_HOT ? launch_hot(l->prec, l->g, l->U, params->seed, l->st)
                                       : launch_cold(l->prec, l->g, l->U, l->st);
@@ -319,6 +327,16 @@ cl_status cl_cool(cl_lattice* l, const cl_cool_params* cp, cl_cool_report* repor
   if (s != CL_OK) return s;
   s = do_cool(l, cp);
   if (s != CL_OK || !report) return s;
+  CoolState c;
+  CK(cudaMemcpyAsync(&c, l->cs, sizeof(c), cudaMemcpyDeviceToHost, l->st));
+  CK(cudaStreamSynchronize(l->st));
+  to_report(c, report);
+  if (c.nonfinite) return fail(CL_ERR_NONFINITE, "non-finite links during cooling");
+  return CL_OK;
+}
+
+cl_status cl_cool_last_report(cl_lattice* l, cl_cool_report* report) {
+  if (!l || !report) return fail(CL_ERR_INVALID, "NULL argument");
   CoolState c;
   CK(cudaMemcpyAsync(&c, l->cs, sizeof(c), cudaMemcpyDeviceToHost, l->st));
   CK(cudaStreamSynchronize(l->st));
@@ -447,7 +465,12 @@ cl_status cl_get_step(const cl_lattice* l, uint64_t* step) {
 
 cl_status cl_set_step(cl_lattice* l, uint64_t step) {
   if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  if (step > 0xffffffffull) return fail(CL_ERR_INVALID, "step beyond the 32-bit Philox counter word");
   l->step = step;
+  static thread_local uint32_t v;
+  v = (uint32_t)step;
+  CK(cudaMemcpyAsync(l->step_dev, &v, sizeof(uint32_t), cudaMemcpyHostToDevice, l->st));
+  CK(cudaStreamSynchronize(l->st));
   return CL_OK;
 }
 
@@ -457,7 +480,7 @@ cl_status cl_drift(cl_lattice* l, double* host_aos) {
   if (s != CL_OK) return s;
   const bool th = theta_nonzero(l);
   CK(do_force(l, th, KAPPA_Q * l->p.theta_im, -KAPPA_Q * l->p.theta_re));
-  CK(launch_update_gather(l->prec, 1, l->g, l->U, l->C, l->Un, 0.0, l->p.seed, (uint32_t)l->step, l->st));
+  CK(launch_update_gather(l->prec, 1, l->g, l->U, l->C, l->Un, 0.0, l->p.seed, l->step_dev, l->st));
   CK(launch_soa_to_aos(l->prec, l->g, l->Un, l->stage, 4, l->st));
   l->launches += 2;
   CK(cudaMemcpyAsync(host_aos, l->stage, sizeof(double) * 18 * 4 * (size_t)l->g.V,
@@ -493,6 +516,246 @@ cl_status cl_launch_count(const cl_lattice* l, int64_t* count) {
   return CL_OK;
 }
 
+// ------------------------------------------------------------- graphs
+namespace {
+
+// Enqueue one step of the hot path (CL step, then cooling when cp != NULL).
+cl_status enqueue_step(cl_lattice* l, double eps, const cl_cool_params* cp) {
+  cl_status s = do_steps(l, eps, 1);
+  if (s == CL_OK && cp) s = do_cool(l, cp);
+  return s;
+}
+
+cl_status check_step_args(const cl_lattice* l, double eps, const cl_cool_params* cp) {
+  if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  if (!l->st) return fail(CL_ERR_INVALID, "graphs need a non-default stream (cl_init_lattice)");
+  if (!(eps >= 0.0)) return fail(CL_ERR_INVALID, "bad eps");
+  return cp ? check_cool(cp) : CL_OK;
+}
+
+}  // namespace
+
+cl_status cl_capture_step(cl_lattice* l, double eps, const cl_cool_params* cp) {
+  cl_status s = check_step_args(l, eps, cp);
+  if (s != CL_OK) return s;
+  for (int v = 0; v < 2; ++v)
+    if (l->gexec[v]) {
+      cudaGraphExecDestroy(l->gexec[v]);
+      l->gexec[v] = nullptr;
+    }
+  const int timing = l->timing;
+  void* const U0 = l->U;
+  void* const Un0 = l->Un;
+  l->timing = 0;
+  // two variants: the update writes the other link buffer, so replays alternate
+  for (int v = 0; v < 2 && s == CL_OK; ++v) {
+    l->gU[v] = l->U;
+    const uint64_t step0 = l->step;
+    const int64_t n0 = l->launches;
+    cudaError_t e = cudaStreamBeginCapture(l->st, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+      s = fail(CL_ERR_CUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+      break;
+    }
+    s = enqueue_step(l, eps, cp);
+    l->glaunches = l->launches - n0;
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(l->st, &gr);
+    l->step = step0;
+    l->launches = n0;
+    if (s == CL_OK && e != cudaSuccess) s = fail(CL_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+    if (s == CL_OK) {
+      e = cudaGraphInstantiate(&l->gexec[v], gr, 0);
+      if (e != cudaSuccess) s = fail(CL_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    if (gr) cudaGraphDestroy(gr);
+  }
+  l->timing = timing;
+  // each variant swapped the buffers once: after two they are back in place
+  l->U = U0;
+  l->Un = Un0;
+  if (s != CL_OK)
+    for (int v = 0; v < 2; ++v)
+      if (l->gexec[v]) {
+        cudaGraphExecDestroy(l->gexec[v]);
+        l->gexec[v] = nullptr;
+      }
+  return s;
+}
+
+cl_status cl_replay(cl_lattice* l, int n_steps) {
+  if (!l || n_steps < 0) return fail(CL_ERR_INVALID, "bad arguments");
+  if (!l->gexec[0]) return fail(CL_ERR_INVALID, "no captured step (cl_capture_step)");
+  for (int i = 0; i < n_steps; ++i) {
+    const int v = (l->U == l->gU[0]) ? 0 : 1;
+    CK(cudaGraphLaunch(l->gexec[v], l->st));
+    l->launches += l->glaunches;
+    std::swap(l->U, l->Un);
+    l->step++;
+  }
+  return CL_OK;
+}
+
+struct cl_batch {
+  std::vector<cl_lattice*> lats;
+  cudaStream_t origin;
+  cudaEvent_t fork, done;
+  std::vector<cudaEvent_t> joins, ready;
+  cudaGraphExec_t exec[2];
+  std::vector<void*> startU[2];  // per lattice, the link buffer each variant starts from
+};
+
+void cl_batch_free(cl_batch* b) {
+  if (!b) return;
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  for (int v = 0; v < 2; ++v)
+    if (b->exec[v]) cudaGraphExecDestroy(b->exec[v]);
+  for (cudaEvent_t e : b->joins)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : b->ready)
+    if (e) cudaEventDestroy(e);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+
+cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
+                          const cl_cool_params* cps, int with_cooling, cl_batch** out) {
+  if (!out || n < 1 || !lats || !eps) return fail(CL_ERR_INVALID, "bad batch arguments");
+  *out = nullptr;
+  for (int i = 0; i < n; ++i) {
+    cl_status s = check_step_args(lats[i], eps[i], with_cooling ? &cps[i] : nullptr);
+    if (s != CL_OK) return s;
+    for (int j = 0; j < i; ++j)
+      if (lats[j] == lats[i] || lats[j]->st == lats[i]->st)
+        return fail(CL_ERR_INVALID, "batch lattices need distinct lattices on distinct streams");
+  }
+  cl_batch* b = new cl_batch();
+  b->lats.assign(lats, lats + n);
+  b->origin = nullptr;
+  b->fork = nullptr;
+  b->done = nullptr;
+  b->exec[0] = b->exec[1] = nullptr;
+  cl_status s = CL_OK;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  b->joins.assign(n, nullptr);
+  b->ready.assign(n, nullptr);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ready[i], cudaEventDisableTiming);
+  std::vector<void*> U0(n), Un0(n);
+  for (int i = 0; i < n; ++i) {
+    U0[i] = lats[i]->U;
+    Un0[i] = lats[i]->Un;
+  }
+  // the lattices' pending work must finish before the first replay
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamSynchronize(lats[i]->st);
+  if (e != cudaSuccess) s = fail(CL_ERR_CUDA, std::string("batch setup: ") + cudaGetErrorString(e));
+  std::vector<int> timing(n);
+  for (int i = 0; i < n; ++i) {
+    timing[i] = lats[i]->timing;
+    lats[i]->timing = 0;
+  }
+  for (int v = 0; v < 2 && s == CL_OK; ++v) {
+    std::vector<uint64_t> step0(n);
+    std::vector<int64_t> n0(n);
+    b->startU[v].resize(n);
+    e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->origin);
+    for (int i = 0; i < n && e == cudaSuccess && s == CL_OK; ++i) {
+      cl_lattice* l = lats[i];
+      b->startU[v][i] = l->U;
+      step0[i] = l->step;
+      n0[i] = l->launches;
+      e = cudaStreamWaitEvent(l->st, b->fork, 0);
+      if (e == cudaSuccess) s = enqueue_step(l, eps[i], with_cooling ? &cps[i] : nullptr);
+      l->glaunches = l->launches - n0[i];
+      if (e == cudaSuccess && s == CL_OK) e = cudaEventRecord(b->joins[i], l->st);
+      if (e == cudaSuccess && s == CL_OK) e = cudaStreamWaitEvent(b->origin, b->joins[i], 0);
+    }
+    cudaGraph_t gr = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(b->origin, &gr);
+    for (int i = 0; i < n; ++i) {
+      if (i < (int)step0.size()) {
+        lats[i]->step = step0[i];
+        lats[i]->launches = n0[i];
+      }
+    }
+    if (s == CL_OK && (e != cudaSuccess || e2 != cudaSuccess))
+      s = fail(CL_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
+    if (s == CL_OK) {
+      e = cudaGraphInstantiate(&b->exec[v], gr, 0);
+      if (e != cudaSuccess) s = fail(CL_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    if (gr) cudaGraphDestroy(gr);
+  }
+  for (int i = 0; i < n; ++i) {
+    lats[i]->timing = timing[i];
+    lats[i]->U = U0[i];
+    lats[i]->Un = Un0[i];
+  }
+  if (s != CL_OK) {
+    cl_batch_free(b);
+    return s;
+  }
+  *out = b;
+  return CL_OK;
+}
+
+cl_status cl_batch_run(cl_batch* b, int n_steps) {
+  if (!b || n_steps < 0) return fail(CL_ERR_INVALID, "bad arguments");
+  const int n = (int)b->lats.size();
+  if (n_steps == 0) return CL_OK;
+  // order against work already queued on the lattices' own streams
+  for (int i = 0; i < n; ++i) {
+    CK(cudaEventRecord(b->ready[i], b->lats[i]->st));
+    CK(cudaStreamWaitEvent(b->origin, b->ready[i], 0));
+  }
+  for (int k = 0; k < n_steps; ++k) {
+    int v = -1;
+    for (int w = 0; w < 2 && v < 0; ++w) {
+      bool ok = true;
+      for (int i = 0; i < n && ok; ++i) ok = b->lats[i]->U == b->startU[w][i];
+      if (ok) v = w;
+    }
+    if (v < 0) return fail(CL_ERR_INVALID, "a batch lattice was stepped outside the batch");
+    CK(cudaGraphLaunch(b->exec[v], b->origin));
+    for (cl_lattice* l : b->lats) {
+      std::swap(l->U, l->Un);
+      l->step++;
+      l->launches += l->glaunches;
+    }
+  }
+  // later calls on a lattice's own stream see the batch's result
+  CK(cudaEventRecord(b->done, b->origin));
+  for (cl_lattice* l : b->lats) CK(cudaStreamWaitEvent(l->st, b->done, 0));
+  return CL_OK;
+}
+
+cl_status cl_batch_synchronize(cl_batch* b) {
+  if (!b) return fail(CL_ERR_INVALID, "NULL batch");
+  CK(cudaStreamSynchronize(b->origin));
+  return CL_OK;
+}
+
+cl_status cl_stream_create(void** out) {
+  if (!out) return fail(CL_ERR_INVALID, "NULL argument");
+  *out = nullptr;
+  cudaStream_t st = nullptr;
+  CK(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  *out = (void*)st;
+  return CL_OK;
+}
+
+cl_status cl_stream_destroy(void* stream) {
+  if (!stream) return fail(CL_ERR_INVALID, "NULL stream");
+  CK(cudaStreamSynchronize((cudaStream_t)stream));
+  CK(cudaStreamDestroy((cudaStream_t)stream));
+  return CL_OK;
+}
+
 cl_status cl_set_timing(cl_lattice* l, int on) {
   if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
   CK(resolve_timing(l));
@@ -523,7 +786,9 @@ cl_status cl_synchronize(cl_lattice* l) {
 void cl_free(cl_lattice* l) {
   if (!l) return;
   void* bufs[] = {l->U, l->Un, l->Ui, l->Pq, l->Dq, l->C, l->Gq, l->F, l->f, l->Om, l->Omi, l->partials, l->cs, l->obs,
-                  l->stage, l->qsite};
+                  l->stage, l->qsite, l->step_dev};
+  for (int v = 0; v < 2; ++v)
+    if (l->gexec[v]) cudaGraphExecDestroy(l->gexec[v]);
   if (l->st) cudaStreamSynchronize(l->st);
   for (void* b : bufs)
     if (b) cudaFree(b);

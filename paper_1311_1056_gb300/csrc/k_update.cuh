@@ -44,7 +44,7 @@ enum { MODE_UPDATE = 0, MODE_DRIFT = 1 };
 struct UpdArgs {
   double beta, eps, sqrt_eps;
   uint64_t seed;
-  uint32_t step;
+  const uint32_t* step;  // device-resident Philox step counter (graph-replayable)
 };
 
 // Sign flip on the integer pipe (no floating-point instruction).
@@ -444,14 +444,15 @@ __global__ void __launch_bounds__(128) k_update_gather(Geo g, const typename vec
   // (X and the noise carry FP32 information only) and widens it for the exp.
   mat<double> A;
   float rA = -1.f;
+  const uint32_t step = __ldg(a.step);
   if (sizeof(T) == 8) {
     double eta[8];
-    normals_f64<4>(eta, a.seed, a.step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
+    normals_f64<4>(eta, a.seed, step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
     convert(A, X);
     exponent<double>(A, eta, a.eps, a.sqrt_eps);
   } else {
     float ef[8];
-    normals_f32<4>(ef, a.seed, a.step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
+    normals_f32<4>(ef, a.seed, step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
     mat<float> Af;
     convert(Af, X);
     exponent<float>(Af, ef, (float)a.eps, (float)a.sqrt_eps);

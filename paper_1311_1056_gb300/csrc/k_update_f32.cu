@@ -48,7 +48,7 @@ cudaError_t launch_plaq_force_f32(bool theta, const GeoH& h, const void* U, cons
 }
 
 cudaError_t launch_update_gather_f32(int mode, const GeoH& h, const void* U, const void* C, void* out,
-                                    double eps, uint64_t seed, uint32_t step, cudaStream_t st) {
+                                    double eps, uint64_t seed, const uint32_t* step, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
   UpdArgs a;
   a.beta = 0.0;

@@ -50,7 +50,7 @@ cudaError_t launch_plaq_force_f64(bool theta, const GeoH& h, const void* U, cons
 }
 
 cudaError_t launch_update_gather_f64(int mode, const GeoH& h, const void* U, const void* C, void* out,
-                                    double eps, uint64_t seed, uint32_t step, cudaStream_t st) {
+                                    double eps, uint64_t seed, const uint32_t* step, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
   UpdArgs a;
   a.beta = 0.0;
@@ -76,7 +76,7 @@ cudaError_t launch_clover_rot_f32(const GeoH&, const void*, const void*, const v
 cudaError_t launch_plaq_force_f32(bool, const GeoH&, const void*, const void*, const void*,
                                   const void*, const void*, void*, void*, double, cudaStream_t);
 cudaError_t launch_update_gather_f32(int, const GeoH&, const void*, const void*, void*, double,
-                                     uint64_t, uint32_t, cudaStream_t);
+                                     uint64_t, const uint32_t*, cudaStream_t);
 
 cudaError_t launch_link_inverse(int prec, const GeoH& h, const void* U, void* Ui, cudaStream_t st) {
   return prec == 0 ? launch_link_inverse_f64(h, U, Ui, st) : launch_link_inverse_f32(h, U, Ui, st);
@@ -97,8 +97,18 @@ cudaError_t launch_plaq_force(int prec, bool theta, const GeoH& h, const void* U
                    : launch_plaq_force_f32(theta, h, U, Ui, Pq, Dq, F, Gq, C, beta, st);
 }
 cudaError_t launch_update_gather(int prec, int mode, const GeoH& h, const void* U, const void* C,
-                                 void* out, double eps, uint64_t seed, uint32_t step, cudaStream_t st) {
+                                 void* out, double eps, uint64_t seed, const uint32_t* step, cudaStream_t st) {
   return prec == 0 ? launch_update_gather_f64(mode, h, U, C, out, eps, seed, step, st)
                    : launch_update_gather_f32(mode, h, U, C, out, eps, seed, step, st);
+}
+}  // namespace clgc
+
+namespace clgc {
+// Advances the device step counter after an update (one thread).
+__global__ void k_step_bump(uint32_t* step) { *step += 1u; }
+
+cudaError_t launch_step_bump(uint32_t* step, cudaStream_t st) {
+  k_step_bump<<<1, 1, 0, st>>>(step);
+  return cudaGetLastError();
 }
 }  // namespace clgc

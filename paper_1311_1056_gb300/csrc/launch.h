@@ -63,7 +63,10 @@ cudaError_t launch_plaq_force(int prec, bool theta, const GeoH& g, const void* U
                               const void* Pq, const void* Dq, const void* F, void* Gq, void* C,
                               double beta, cudaStream_t st);
 cudaError_t launch_update_gather(int prec, int mode, const GeoH& g, const void* U, const void* C,
-                                 void* out, double eps, uint64_t seed, uint32_t step, cudaStream_t st);
+                                 void* out, double eps, uint64_t seed, const uint32_t* step,
+                                 cudaStream_t st);
+// step += 1 on the device (the Philox step counter read by the update).
+cudaError_t launch_step_bump(uint32_t* step, cudaStream_t st);
 // Cooling: gradient f (8 FP64 values per site, [a][V]) + partial sums; the
 // rule; Omega; apply.
 cudaError_t launch_cool_grad(int prec, const GeoH& g, const void* U, void* f, double* partials,
