@@ -392,6 +392,170 @@ def reference(args):
     }))
 
 
+# ----------------------------------------------------------- batched ensemble
+BATCH = dict(eps=0.005, alpha=1.0, n_min=1, n_max=10, tol_rel=0.01)
+BATCH_NAME = ("ensemble of independent chains, L^4 with L uniform in {8, 12, 16}, beta ~ U[5.6, 6.2], "
+              "theta in {0, 0.5, 1, 1.5, 2}, cold start; each CL step (eps 0.005) followed by adaptive "
+              "cooling (alpha_ad = 1 / D_2, 1..10 sweeps, stop below 1 % relative progress)")
+
+
+def _run_chains(cl, torch, chains, prec, n_steps, batched, tune):
+    """Advance every chain by n_steps; returns (seconds, observables, reports,
+    launches, tuned blocks).  batched: one graph launch per step for all chains
+    (each chain on its own stream); otherwise one chain after the other with
+    eager calls."""
+    cp = cl.make_cool(BATCH["eps"], BATCH["alpha"], cl.CL_D2_MEANABS, n_min=BATCH["n_min"],
+                      n_max=BATCH["n_max"], tol_rel=BATCH["tol_rel"])
+    lats = [cl.Lattice(c["L"], beta=c["beta"], theta=c["theta"], prec=prec, seed=c["seed"],
+                       start=cl.CL_START_COLD, own_stream=True) for c in chains]
+    tuned = {}
+    if tune:
+        for c, lat in zip(chains, lats):
+            blocks, _ = lat.autotune(BATCH["eps"], cp, reps=3, use_cache=True)
+            tuned["%d^4 theta%s0" % (c["L"][0], "!=" if c["theta"] else "=")] = blocks
+    n0 = sum(l.launches() for l in lats)
+    torch.cuda.synchronize()
+    if batched:
+        b = cl.Batch(lats, BATCH["eps"], [cp] * len(lats))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        b.run(n_steps)
+        b.synchronize()
+        sec = time.perf_counter() - t0
+        b.close()
+    else:
+        t0 = time.perf_counter()
+        for lat in lats:
+            for _ in range(n_steps):
+                lat.step(BATCH["eps"], 1)
+                cl.cl_cool(lat.h, cp, want_report=False)
+            lat.synchronize()
+        sec = time.perf_counter() - t0
+    launches = sum(l.launches() for l in lats) - n0
+    obs = [l.observables() for l in lats]
+    reps = [l.last_cool_report() for l in lats]
+    for l in lats:
+        l.close()
+    return sec, obs, reps, launches, tuned
+
+
+def batch_mode(args):
+    # more hardware work queues than the default 8, so that the chains'
+    # streams do not serialise behind one another (read at CUDA init)
+    os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+    import numpy as np
+    import torch
+    from paper_1311_1056_gb300 import build, cl, workloads
+
+    build.build()
+    cl.load()
+    chains = workloads.ensemble(args.chains, seed=0)
+    n_steps = args.batch_steps
+    total = sum(workloads.sites(c) for c in chains) * n_steps
+    # warm-up (module load, graph upload, clocks): a short batched run of 4 chains
+    _run_chains(cl, torch, chains[:4], cl.CL_FP32_STORAGE, 3, True, False)
+    sampler = ClockSampler(0)
+    sampler.start()
+    arms = {}
+    arms["batched_fp32"] = _run_chains(cl, torch, chains, cl.CL_FP32_STORAGE, n_steps, True, True)
+    arms["batched_fp64"] = _run_chains(cl, torch, chains, cl.CL_FP64, n_steps, True, True)
+    arms["alone_fp32"] = _run_chains(cl, torch, chains, cl.CL_FP32_STORAGE, n_steps, False, False)
+    arms["alone_fp64"] = _run_chains(cl, torch, chains, cl.CL_FP64, n_steps, False, False)
+    clocks = sampler.stop()
+    ref_obs = arms["alone_fp64"][1]
+
+    def obs_err(obs):
+        out = {}
+        for k in ("plaq_re", "plaq_im", "un", "q_re", "q_im"):
+            d = [abs(a[k] - b[k]) for a, b in zip(obs, ref_obs)]
+            out[k] = {"max": float(max(d)), "median": float(np.median(d))}
+        return out
+
+    res = {}
+    for name, (sec, obs, reps, launches, tuned) in arms.items():
+        res[name] = {"value": total / sec, "seconds": round(sec, 4), "gpu_launches": launches,
+                     "mean_sweeps_last_step": float(np.mean([r["sweeps"] for r in reps])),
+                     "abs_err_vs_alone_fp64": obs_err(obs)}
+        if tuned:
+            res[name]["autotuned_blocks"] = tuned
+    line = {
+        "metric": "batched CL+cooling site-updates/s", "unit": UNIT,
+        "value": res["batched_fp32"]["value"], "higher_is_better": True, "n_gpus": 1,
+        "dtype": "f32 links, f64 exp/reductions", "data": "synthetic",
+        "config": {"workload": BATCH_NAME, "chains": len(chains), "steps": n_steps,
+                   "sites_per_step": total // n_steps,
+                   "sizes": {str(L): sum(1 for c in chains if c["L"][0] == L) for L in workloads.ENSEMBLE_SIZES}},
+        "speedup_vs_alone_fp64": res["batched_fp32"]["value"] / res["alone_fp64"]["value"],
+        "arms": res, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- serving
+SERVE_NAME = ("request trace: Poisson arrivals, L^4 with L = round(exp U[ln 4, ln 24]), beta ~ U[5.6, 6.2], "
+              "theta ~ U[0, 2], 100..2000 CL steps (eps 0.005) each followed by adaptive cooling "
+              "(alpha_ad = 1 / D_2, 1..10 sweeps); HBM budget 150 GB")
+
+
+def _serve_once(cl, trace, prec, slots, graphs, tune):
+    cp = cl.make_cool(BATCH["eps"], BATCH["alpha"], cl.CL_D2_MEANABS, n_min=BATCH["n_min"],
+                      n_max=BATCH["n_max"], tol_rel=BATCH["tol_rel"])
+    reqs = [cl.make_request(r["L"], r["beta"], r["theta"], BATCH["eps"], r["steps"], seed=r["seed"],
+                            start=cl.CL_START_COLD, tag=r["id"]) for r in trace]
+    arrivals = [r["t"] - trace[0]["t"] for r in trace]
+    cfg = cl.make_server_config(hbm_budget_bytes=150e9, max_slots=slots, prec=prec, chunk_steps=8,
+                                use_graphs=graphs, cool=cp, blocks_from_autotune=tune)
+    with cl.Server(cfg) as srv:
+        res = srv.run_trace(reqs, arrivals)
+        st = srv.stats()
+    return {r["tag"]: r for r in res}, st
+
+
+def serve_mode(args):
+    import numpy as np
+    from paper_1311_1056_gb300 import build, cl, workloads
+
+    build.build()
+    cl.load()
+    trace = workloads.trace(args.requests, rate=args.rate, seed=0)
+    work = sum(workloads.sites(r) * r["steps"] for r in trace)
+    # warm-up: a few small requests through both configurations
+    warm = workloads.trace(4, rate=1000.0, seed=1, steps=(20, 20), l_range=(4, 8))
+    _serve_once(cl, warm, cl.CL_FP32_STORAGE, args.slots, True, True)
+    _serve_once(cl, warm, cl.CL_FP64, 1, False, False)
+    sampler = ClockSampler(0)
+    sampler.start()
+    arms = {"served_fp32": _serve_once(cl, trace, cl.CL_FP32_STORAGE, args.slots, True, True),
+            "one_at_a_time_fp64": _serve_once(cl, trace, cl.CL_FP64, 1, False, False)}
+    clocks = sampler.stop()
+    ref = arms["one_at_a_time_fp64"][0]
+    out = {}
+    for name, (res, st) in arms.items():
+        lat = np.array([res[r["id"]]["t_done"] - res[r["id"]]["t_submit"] for r in trace])
+        span = max(v["t_done"] for v in res.values()) - min(v["t_submit"] for v in res.values())
+        errs = {}
+        for k in ("plaq_re", "un", "q_re"):
+            d = np.array([abs(res[i]["obs"][k] - ref[i]["obs"][k]) for i in res])
+            errs[k] = {"max": float(d.max()), "median": float(np.median(d))}
+        out[name] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
+                     "mean_s": float(lat.mean()), "makespan_s": span, "value": work / span,
+                     "requests_per_s": len(trace) / span, "peak_active": st["peak_active"],
+                     "peak_bytes": st["peak_bytes"],
+                     "nonfinite": sum(1 for v in res.values() if v["status"] != cl.CL_OK),
+                     "abs_err_vs_one_at_a_time_fp64": errs}
+    a, b = out["served_fp32"], out["one_at_a_time_fp64"]
+    line = {"metric": "served CL+cooling site-updates/s; p50/p99 latency", "unit": UNIT,
+            "value": a["value"], "higher_is_better": True, "n_gpus": 1,
+            "dtype": "f32 links, f64 exp/reductions", "data": "synthetic",
+            "config": {"workload": SERVE_NAME, "requests": len(trace), "rate_per_s": args.rate,
+                       "slots": args.slots, "chunk_steps": 8, "site_steps": work},
+            "p50_s": a["p50_s"], "p99_s": a["p99_s"],
+            "vs_one_at_a_time_fp64": {"throughput_x": a["value"] / b["value"], "p50_x": b["p50_s"] / a["p50_s"],
+                                      "p99_x": b["p99_s"] / a["p99_s"]},
+            "arms": out, "clocks": clocks}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -402,7 +566,19 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--mode", choices=["step", "batch", "serve"], default="step",
+                    help="step: the 32^4 single-chain step (default); batch: the chain ensemble; "
+                         "serve: the request trace")
+    ap.add_argument("--requests", type=int, default=100)
+    ap.add_argument("--rate", type=float, default=20.0)
+    ap.add_argument("--slots", type=int, default=64)
+    ap.add_argument("--chains", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=200)
     args = ap.parse_args()
+    if args.mode == "batch":
+        return batch_mode(args)
+    if args.mode == "serve":
+        return serve_mode(args)
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
     if args.impl == "reference":

@@ -106,13 +106,26 @@ typedef struct {
 /* Create a lattice on the current CUDA device and initialise its links
  * (start, then the optional random gauge transformation).  cuda_stream is a
  * cudaStream_t (may be NULL).  On success *out owns the device memory
- * (per site: 70 complex 3x3 matrices -- links, a second link buffer,
+ * (per site: 60 complex 3x3 matrices -- links, a second link buffer,
  * inverses, plaquettes, their differences, the clover field, the drift
- * contributions and their partial sums -- plus cooling scratch: 10.3 KB in
- * FP64, 5.1 KB in FP32).
+ * contributions and their partial sums -- plus cooling scratch: 8.8 KB in
+ * FP64, 4.5 KB in FP32; cl_lattice_bytes gives the exact figure).
  * Errors: CL_ERR_INVALID (NULL, extents < 1, V*6*9 beyond int range),
  * CL_ERR_OOM, CL_ERR_CUDA. */
 cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice** out);
+
+/* Re-initialise a lattice in place for a new chain with the same extents and
+ * precision (reuses its device memory): start field, step counter and
+ * cooling state from params, as cl_init_lattice; captured step graphs are
+ * dropped, tuned block sizes kept.  Waits for the lattice's stream first.
+ * Errors: CL_ERR_INVALID (other extents or precision), CL_ERR_CUDA. */
+cl_status cl_reset_lattice(cl_lattice* lat, const cl_params* params);
+
+/* Device bytes cl_init_lattice allocates for params (links, the second link
+ * buffer, link inverses, plaquettes, drift slots, clover field, cooling
+ * fields and reduction records; the optional staging buffer of the host link
+ * exchange is not included).  Errors: CL_ERR_INVALID. */
+cl_status cl_lattice_bytes(const cl_params* params, size_t* bytes);
 
 /* n_steps complex Langevin steps, no cooling (Sec. 2; the update
  * U' = exp(i lambda_a (eps K_a + sqrt(eps) eta_a)) U, K_a = -D_a S,
@@ -144,6 +157,34 @@ cl_status cl_observables(cl_lattice* lat, cl_obs* out);
 cl_status cl_trajectory(cl_lattice* lat, double eps, int n_steps, const cl_cool_params* cp,
                         int obs_every, cl_obs* obs_out, cl_cool_report* rep_out,
                         double runaway_un);
+
+/* Launch shapes.  Five kernel families take a tunable block size (threads
+ * per block; each thread owns one site or link, so the results do not depend
+ * on it): CL_TUNE_CLOVER (link inverses, plaquettes, clover field),
+ * CL_TUNE_FORCE (per-plaquette drift), CL_TUNE_UPDATE (noise + exponential
+ * update), CL_TUNE_OMEGA (cooling transformation), CL_TUNE_APPLY (cooling
+ * apply).  The reductions keep a fixed shape so that their summation order,
+ * and hence every result, is the same under any tuning.
+ * cl_set_blocks: blocks[CL_NTUNE], each 0 (default, 128) or a multiple of 32
+ *   in [32, 256]; takes effect for later launches (graphs already captured
+ *   keep the shape they were captured with).
+ * cl_get_blocks: the block sizes in effect.
+ * cl_autotune: times one CL step + 2 cooling sweeps (eps, cp with the sweep
+ *   count forced to 2) reps times for every candidate block size in
+ *   {32, 64, 128, 256}, sets the fastest per family and writes it to
+ *   blocks_out (may be NULL).  ms_out (may be NULL) receives the mean
+ *   per-step milliseconds, [4 candidates][CL_NTUNE].  The lattice is left as
+ *   it was (links, step counter, cooling state; snapshot in a temporary
+ *   device buffer of one link field).  With use_cache != 0 and ms_out NULL a
+ *   shape tuned before in this process (same device, precision, extents and
+ *   theta == 0 or not) is reused without timing.
+ * Errors: CL_ERR_INVALID, CL_ERR_OOM, CL_ERR_CUDA. */
+typedef enum { CL_TUNE_CLOVER = 0, CL_TUNE_FORCE = 1, CL_TUNE_UPDATE = 2, CL_TUNE_OMEGA = 3,
+               CL_TUNE_APPLY = 4, CL_NTUNE = 5 } cl_tune_family;
+cl_status cl_set_blocks(cl_lattice* lat, const int* blocks);
+cl_status cl_get_blocks(cl_lattice* lat, int* blocks);
+cl_status cl_autotune(cl_lattice* lat, double eps, const cl_cool_params* cp, int reps, int use_cache,
+                      int* blocks_out, double* ms_out);
 
 /* A non-blocking CUDA stream owned by the caller (for cl_init_lattice when
  * the caller has none of its own); destroy it after the lattices that use it
@@ -183,6 +224,81 @@ cl_status cl_batch_run(cl_batch* batch, int n_steps);
 cl_status cl_batch_synchronize(cl_batch* batch);
 void cl_batch_free(cl_batch* batch);
 
+/* ------------------------------------------------------------------ serving
+ * A request server: complex-Langevin trajectories (one chain each) admitted
+ * as they arrive and advanced concurrently on one GPU.  Every resident chain
+ * keeps its links, Philox step counter and cooling state in HBM and has its
+ * own stream with up to two chunks of chunk_steps steps queued ahead of the
+ * host; a chain that finishes frees its slot and the next queued request is
+ * admitted at once (continuous batching).  Admission is first come, first
+ * served, limited by max_slots resident chains and by hbm_budget_bytes of
+ * lattice memory (cl_lattice_bytes); idle lattices are kept for reuse by
+ * requests of the same extents and dropped, oldest first, when a new one
+ * needs the room.  A chain's result does not depend on what runs beside it:
+ * its noise is keyed by its own seed and step, and its kernels and
+ * reductions are the same as for a lone cl_step / cl_cool sequence.
+ * The server is driven by the calling thread (no threads of its own); one
+ * server must not be used from two threads at once. */
+typedef struct {
+  int L[4];
+  double beta, theta_re, theta_im;
+  double eps;          /* CL step size, also the cooling eps */
+  int n_steps;         /* CL steps (each followed by the cooling call) */
+  uint64_t seed;       /* Philox key of this chain */
+  cl_start start;
+  double gauge_sigma;  /* optional random SL(3,C) transformation of the start */
+  int64_t tag;         /* caller's identifier, returned in the result */
+} cl_request;
+
+typedef struct {
+  double hbm_budget_bytes;  /* admission limit on resident lattice memory */
+  int max_slots;            /* chains resident at once */
+  cl_precision prec;        /* storage form of every chain */
+  int chunk_steps;          /* steps per queued chunk */
+  int use_graphs;           /* 1: steps replay a captured graph; 0: eager launches */
+  int cool_enabled;         /* 1: each step is followed by cooling with `cool` */
+  cl_cool_params cool;      /* its eps is replaced by the request's eps */
+  int blocks_from_autotune; /* 1: tune block sizes per lattice shape (cached) */
+} cl_server_config;
+
+typedef struct {
+  int64_t tag;
+  cl_status status;          /* CL_OK or CL_ERR_NONFINITE */
+  int n_steps;
+  cl_obs obs;                /* observables after the last step */
+  cl_cool_report last_cool;  /* report of the last step's cooling */
+  double t_submit, t_admit, t_done;  /* server clock, seconds */
+} cl_result;
+
+typedef struct {
+  int64_t submitted, admitted, completed;
+  int active, queued, pooled, peak_active;
+  uint64_t bytes_in_use, peak_bytes;
+} cl_server_stats;
+
+typedef struct cl_server cl_server;
+/* Errors: CL_ERR_INVALID (bad configuration). */
+cl_status cl_server_create(const cl_server_config* cfg, cl_server** out);
+/* Seconds since cl_server_create (the clock of t_submit / t_admit / t_done). */
+double cl_server_clock(const cl_server* srv);
+/* Queue a request (nothing runs until the next poll).  t_submit < 0 stamps
+ * the current server clock.  Errors: CL_ERR_INVALID (bad request, or one
+ * larger than the whole budget). */
+cl_status cl_server_submit(cl_server* srv, const cl_request* req, double t_submit);
+/* Advance the server without blocking: retire finished chunks and chains,
+ * queue further chunks, admit waiting requests; then hand out up to max_out
+ * finished results (completion order) into out, their number in *n_out.
+ * Errors: CL_ERR_INVALID, CL_ERR_OOM, CL_ERR_CUDA. */
+cl_status cl_server_poll(cl_server* srv, cl_result* out, int max_out, int* n_out);
+cl_status cl_server_stats_get(const cl_server* srv, cl_server_stats* out);
+/* Replay a request trace in real time: request i is submitted when the
+ * server clock reaches (start of the call) + arrival_s[i] (sorted), and the
+ * call returns when all n have finished; results[] in completion order,
+ * t_submit = the scheduled arrival, so host lag counts as latency. */
+cl_status cl_server_run_trace(cl_server* srv, int n, const cl_request* reqs, const double* arrival_s,
+                              cl_result* results);
+void cl_server_free(cl_server* srv);
+
 /* Links as host AoS doubles (layout above), any precision (FP32 links are
  * widened).  host_aos holds V*4*18 doubles; pinned memory copies fastest.
  * Synchronises.  Errors: CL_ERR_INVALID (NULL), CL_ERR_OOM (staging), CL_ERR_CUDA. */
@@ -197,6 +313,19 @@ cl_status cl_set_links_device(cl_lattice* lat, const double* dev_aos);
 /* Philox step counter (number of CL steps taken; keys the noise). */
 cl_status cl_get_step(const cl_lattice* lat, uint64_t* step);
 cl_status cl_set_step(cl_lattice* lat, uint64_t step);
+
+/* Adaptive Langevin step size (the runaway control that goes with gauge
+ * cooling): with k_ref > 0 every later CL step first gathers the drift of all
+ * links and K_max = max over links of |K|, |K|^2 = sum_a |K_a|^2 =
+ * 2 |X_S - Tr X_S / 3|_F^2, then runs with eps_n = eps min(1, k_ref / K_max)
+ * in the drift and sqrt(eps_n) in the noise; the decision is taken on the
+ * device (graph-replayable).  The cooling that follows keeps its own eps.
+ * k_ref = 0 turns it off.  Errors: CL_ERR_INVALID (k_ref < 0 or NaN). */
+cl_status cl_set_adaptive_step(cl_lattice* lat, double k_ref);
+/* Langevin time t = sum of the step sizes taken since the start, and the
+ * eps_n and K_max of the last adaptive step (0 before one).  Waits for the
+ * lattice's stream; any pointer may be NULL.  Errors: CL_ERR_INVALID, CL_ERR_CUDA. */
+cl_status cl_get_langevin_time(cl_lattice* lat, double* t, double* eps_last, double* kmax_last);
 
 /* Drift matrix X_S of every link, D_a S = i Tr(lambda_a X_S) (Sec. 5 action),
  * as host AoS doubles (V*4*18).  Synchronises. */

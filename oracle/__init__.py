@@ -60,6 +60,8 @@ def lib():
             "or_drift": (cint, [ip, dp, dbl, dbl, dbl, dp]),
             "or_drift_at": (cint, [ip, dp, dbl, dbl, dbl, cint, i64p, dp]),
             "or_cl_step": (cint, [ip, dp, dbl, dbl, dbl, dbl, u64, u32]),
+            "or_cl_step_adaptive": (cint, [ip, dp, dbl, dbl, dbl, dbl, dbl, u64, u32,
+                                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)]),
             "or_cl_step_at": (cint, [ip, dp, dbl, dbl, dbl, dbl, u64, u32, cint, i64p, dp]),
             "or_step_sweep_at": (cint, [ip, dp, dbl, dbl, dbl, dbl, u64, u32, dbl, dbl, cint, i64p,
                                         dp, dp]),
@@ -69,6 +71,18 @@ def lib():
             "or_trajectory": (cint, [ip, dp, dbl, dbl, dbl, dbl, u64, u32, cint,
                                      ctypes.POINTER(CoolParams), cint, dp]),
             "or_num_threads": (cint, []),
+            "or_pauli": (None, [cint, dp]),
+            "or_pc_cold": (cint, [cint, dp]),
+            "or_pc_random_gauge": (cint, [cint, u64, dbl, dp]),
+            "or_pc_action": (cint, [cint, dp, dbl, dbl, dp]),
+            "or_pc_drift": (cint, [cint, dp, dbl, dbl, dp]),
+            "or_pc_step": (cint, [cint, dp, dbl, dbl, dbl, u64, u32]),
+            "or_pc_cool_gradient": (cint, [cint, dp, dp]),
+            "or_pc_cool_sweep": (cint, [cint, dp, dbl, dbl]),
+            "or_pc_cool": (cint, [cint, dp, ctypes.POINTER(CoolParams), ctypes.POINTER(CoolReport)]),
+            "or_pc_observables": (cint, [cint, dp, dp]),
+            "or_pc_trajectory": (cint, [cint, dp, dbl, dbl, dbl, u64, u32, cint,
+                                        ctypes.POINTER(CoolParams), dp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -239,6 +253,17 @@ def cl_step(L, U, beta, theta, eps, seed, step):
     return U
 
 
+def cl_step_adaptive(L, U, beta, theta, eps, k_ref, seed, step):
+    """Returns (U', eps_n, K_max)."""
+    U = _links(U, L).copy()
+    theta = complex(theta)
+    Lp, _k = _L(L)
+    e, k = ctypes.c_double(), ctypes.c_double()
+    _check(lib().or_cl_step_adaptive(Lp, _dp(U), beta, theta.real, theta.imag, eps, k_ref, seed, step,
+                                     ctypes.byref(e), ctypes.byref(k)), "cl_step_adaptive")
+    return U, e.value, k.value
+
+
 def cl_step_at(L, U, beta, theta, eps, seed, step, links):
     U = _links(U, L)
     links = np.ascontiguousarray(links, np.int64)
@@ -308,3 +333,94 @@ def trajectory(L, U, beta, theta, eps, seed, step0, n_steps, cool=None, obs_ever
     _check(lib().or_trajectory(Lp, _dp(U), beta, theta.real, theta.imag, eps, seed, step0,
                                n_steps, cp, obs_every, _dp(out)), "trajectory")
     return U, [dict(zip(TRAJ_NAMES, r.tolist())) for r in out[:nrec]]
+
+
+# ------------------------------------------------- SU(2) Polyakov chain
+# A chain is a complex128 array of shape (n, 2, 2); beta is complex.
+def pauli(a):
+    out = np.zeros((2, 2), np.complex128)
+    lib().or_pauli(a, _dp(out))
+    return out
+
+
+def _chain(U):
+    U = np.ascontiguousarray(U, dtype=np.complex128)
+    assert U.ndim == 3 and U.shape[1:] == (2, 2), U.shape
+    return U
+
+
+def pc_cold(n):
+    U = np.zeros((n, 2, 2), np.complex128)
+    _check(lib().or_pc_cold(n, _dp(U)), "pc_cold")
+    return U
+
+
+def pc_random_gauge(U, seed, sigma):
+    U = _chain(U).copy()
+    _check(lib().or_pc_random_gauge(len(U), seed, sigma, _dp(U)), "pc_random_gauge")
+    return U
+
+
+def pc_action(U, beta):
+    U = _chain(U)
+    b = complex(beta)
+    out = np.zeros(2)
+    _check(lib().or_pc_action(len(U), _dp(U), b.real, b.imag, _dp(out)), "pc_action")
+    return complex(out[0], out[1])
+
+
+def pc_drift(U, beta):
+    U = _chain(U)
+    b = complex(beta)
+    out = np.zeros((len(U), 3), np.complex128)
+    _check(lib().or_pc_drift(len(U), _dp(U), b.real, b.imag, _dp(out)), "pc_drift")
+    return out
+
+
+def pc_step(U, beta, eps, seed, step):
+    U = _chain(U).copy()
+    b = complex(beta)
+    _check(lib().or_pc_step(len(U), _dp(U), b.real, b.imag, eps, seed, step), "pc_step")
+    return U
+
+
+def pc_cool_gradient(U):
+    U = _chain(U)
+    out = np.zeros((len(U), 3))
+    _check(lib().or_pc_cool_gradient(len(U), _dp(U), _dp(out)), "pc_cool_gradient")
+    return out
+
+
+def pc_cool_sweep(U, eps, alpha_ad):
+    U = _chain(U).copy()
+    _check(lib().or_pc_cool_sweep(len(U), _dp(U), eps, alpha_ad), "pc_cool_sweep")
+    return U
+
+
+def pc_cool(U, params):
+    U = _chain(U).copy()
+    rep = CoolReport()
+    _check(lib().or_pc_cool(len(U), _dp(U), ctypes.byref(params), ctypes.byref(rep)), "pc_cool")
+    return U, {"sweeps": rep.sweeps, "alpha_ad_last": rep.alpha_ad_last,
+               "un_before": rep.un_before, "un_after": rep.un_after}
+
+
+PC_OBS_NAMES = ("tr_re", "tr_im", "un", "max_det_dev")
+
+
+def pc_observables(U):
+    U = _chain(U)
+    out = np.zeros(4)
+    _check(lib().or_pc_observables(len(U), _dp(U), _dp(out)), "pc_observables")
+    return dict(zip(PC_OBS_NAMES, out.tolist()))
+
+
+def pc_trajectory(U, beta, eps, seed, step0, n_steps, cool=None):
+    """Returns (U, records): after every step tr_re, tr_im, un, max_det_dev, sweeps."""
+    U = _chain(U).copy()
+    b = complex(beta)
+    rec = np.zeros((max(n_steps, 1), 5))
+    cp = ctypes.byref(cool) if cool is not None else None
+    _check(lib().or_pc_trajectory(len(U), _dp(U), b.real, b.imag, eps, seed, step0, n_steps, cp,
+                                  _dp(rec)), "pc_trajectory")
+    return U, rec[:n_steps]

@@ -9,6 +9,7 @@ import sys
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 SRC = os.path.join(HERE, "oracle.cpp")
+SRCS = [SRC, os.path.join(HERE, "pchain.cpp")]
 HDR = os.path.join(HERE, "oracle.h")
 LIB = os.path.join(HERE, "liboracle.so")
 
@@ -17,14 +18,14 @@ def needs_build() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    return any(os.path.getmtime(p) > t for p in (SRC, HDR))
+    return any(os.path.getmtime(p) > t for p in SRCS + [HDR])
 
 
 def build(force: bool = False) -> str:
     if force or needs_build():
         tmp = LIB + ".tmp.%d" % os.getpid()
         cmd = ["g++", "-std=c++17", "-O2", "-fcx-limited-range", "-fopenmp",
-               "-fPIC", "-shared", "-Wall", "-o", tmp, SRC]
+               "-fPIC", "-shared", "-Wall", "-o", tmp] + SRCS
         subprocess.run(cmd, check=True)
         os.replace(tmp, LIB)
     return LIB

@@ -823,6 +823,35 @@ int or_cl_step(const int L[4], double* U, double beta, double th_re, double th_i
   return 0;
 }
 
+// Adaptive Langevin step size (the runaway control that accompanies gauge
+// cooling): with the drift K_a = -D_a S = -i Tr(lambda_a X_S) of every link,
+// K_max = max over links of (sum_a |K_a|^2)^(1/2); the step runs with
+// eps_n = eps * min(1, k_ref / K_max) in both the drift and the noise term
+// (k_ref <= 0: eps_n = eps).
+int or_cl_step_adaptive(const int L[4], double* U, double beta, double th_re, double th_im,
+                        double eps, double k_ref, uint64_t seed, uint32_t step, double* eps_used,
+                        double* k_max) {
+  Lat g;
+  if (!make_lat(L, g)) return -1;
+  std::vector<Mat> Uv;
+  load_links(g, U, Uv);
+  std::vector<Mat> X;
+  drift_all(g, Uv, beta, cd(th_re, th_im), X);
+  double kmax = 0.0;
+  for (const Mat& x : X) {
+    double k2 = 0.0;
+    for (int a = 1; a <= 8; ++a) k2 += std::norm(-I1 * trace(mul(gellmann(a), x)));
+    kmax = std::max(kmax, std::sqrt(k2));
+  }
+  double e = eps;
+  if (k_ref > 0.0 && kmax > k_ref) e = eps * (k_ref / kmax);
+  cl_step_all(g, Uv, beta, cd(th_re, th_im), e, seed, step);
+  store_links(g, Uv, U);
+  if (eps_used) *eps_used = e;
+  if (k_max) *k_max = kmax;
+  return 0;
+}
+
 int or_cl_step_at(const int L[4], const double* U, double beta, double th_re, double th_im,
                   double eps, uint64_t seed, uint32_t step, int n, const int64_t* links,
                   double* Unew) {

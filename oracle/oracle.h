@@ -72,6 +72,13 @@ int or_drift_at(const int L[4], const double* U, double beta,
  * eta_a = sqrt(2) * normal from Philox stream 0, then U' <- U' / det(U')^(1/3). */
 int or_cl_step(const int L[4], double* U, double beta, double theta_re,
                double theta_im, double eps, uint64_t seed, uint32_t step);
+/* The CL step with the adaptive step size: K_max = max over links of
+ * (sum_a |K_a|^2)^(1/2), K_a = -i Tr(lambda_a X_S); the step uses
+ * eps_n = eps * min(1, k_ref / K_max) (k_ref <= 0: eps).  eps_used, k_max
+ * may be NULL. */
+int or_cl_step_adaptive(const int L[4], double* U, double beta, double theta_re,
+                        double theta_im, double eps, double k_ref, uint64_t seed, uint32_t step,
+                        double* eps_used, double* k_max);
 /* The updated matrices U' of n chosen links only (the input lattice is not
  * modified), for sampled checks on large lattices. */
 int or_cl_step_at(const int L[4], const double* U, double beta,
@@ -115,6 +122,32 @@ int or_trajectory(const int L[4], double* U, double beta, double theta_re,
                   double theta_im, double eps, uint64_t seed, uint32_t step0,
                   int n_steps, const or_cool_params* cool, int obs_every,
                   double* obs_out);
+
+/* ---- SU(2) Polyakov chain (Sec. 3, eq. "eq:s"): S = -(beta/2) Tr(U_1 ... U_N),
+ * complex beta = (br, bi).  A chain is n links, each a 2x2 complex matrix,
+ * row-major {re,im} (8 doubles).  Link k joins sites k and k+1 (periodic);
+ * the gauge transformation at site k is U_k <- Om_k U_k, U_{k-1} <- U_{k-1} Om_k^{-1}. */
+void or_pauli(int a /* 1..3 */, double* out8);
+int or_pc_cold(int n, double* U);
+/* U_k <- Om_k U_k Om_{k+1}^{-1}, Om_k = exp(i w_a sigma_a), w_a = i sigma g_a (Philox stream 4). */
+int or_pc_random_gauge(int n, uint64_t seed, double sigma, double* U);
+int or_pc_action(int n, const double* U, double br, double bi, double* out2);
+/* K_a(k) = -D_a S (3 complex per link: 6n doubles). */
+int or_pc_drift(int n, const double* U, double br, double bi, double* K);
+/* U_k' = exp(i sigma_a (eps K_a + sqrt(eps) eta_a)) U_k, eta = sqrt(2) normal
+ * (Philox stream 3, counter (k, step, 3 << 8, j)), then U' / det(U')^(1/2). */
+int or_pc_step(int n, double* U, double br, double bi, double eps, uint64_t seed, uint32_t step);
+/* f_ak = 2 Tr[sigma_a (U_k U_k^+ - U_{k-1}^+ U_{k-1})] (3n doubles). */
+int or_pc_cool_gradient(int n, const double* U, double* f);
+int or_pc_cool_sweep(int n, double* U, double eps, double alpha_ad);
+/* The adaptive cooling call with the SU(3) stop rule; D_1 = (1/2)<Tr U U^+>, D_2 = <|f_ak|>. */
+int or_pc_cool(int n, double* U, const or_cool_params* p, or_cool_report* rep);
+/* (1/2) Tr(U_1 ... U_N) re, im; (1/N) sum (1/2) Tr U U^+; max |det U - 1|. */
+int or_pc_observables(int n, const double* U, double* out4);
+/* n_steps of [CL step, cooling (cool may be NULL)]; rec (may be NULL) gets
+ * the 4 observables and the sweep count after every step (5 doubles). */
+int or_pc_trajectory(int n, double* U, double br, double bi, double eps, uint64_t seed,
+                     uint32_t step0, int n_steps, const or_cool_params* cool, double* rec);
 
 /* Number of OpenMP threads the oracle uses. */
 int or_num_threads(void);

@@ -21,6 +21,9 @@ CL_OK, CL_ERR_INVALID, CL_ERR_OOM, CL_ERR_CUDA, CL_ERR_NONFINITE, CL_ERR_RUNAWAY
 CL_FP64, CL_FP32_STORAGE = 0, 1
 CL_START_COLD, CL_START_HOT = 0, 1
 CL_D0, CL_D1, CL_D2_MEANABS, CL_D2_RMS = 0, 1, 2, 3
+CL_TUNE_CLOVER, CL_TUNE_FORCE, CL_TUNE_UPDATE, CL_TUNE_OMEGA, CL_TUNE_APPLY = range(5)
+CL_NTUNE = 5
+TUNE_CANDIDATES = (32, 64, 128, 256)
 
 
 class cl_params(ctypes.Structure):
@@ -48,6 +51,41 @@ class cl_obs(ctypes.Structure):
 class cl_cool_report(ctypes.Structure):
     _fields_ = [("sweeps", ctypes.c_int), ("alpha_ad_last", ctypes.c_double),
                 ("un_before", ctypes.c_double), ("un_after", ctypes.c_double)]
+
+    def as_dict(self):
+        return {n: getattr(self, n) for n, _ in self._fields_}
+
+
+class cl_request(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int * 4), ("beta", ctypes.c_double), ("theta_re", ctypes.c_double),
+                ("theta_im", ctypes.c_double), ("eps", ctypes.c_double), ("n_steps", ctypes.c_int),
+                ("seed", ctypes.c_uint64), ("start", ctypes.c_int), ("gauge_sigma", ctypes.c_double),
+                ("tag", ctypes.c_int64)]
+
+
+class cl_server_config(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_slots", ctypes.c_int),
+                ("prec", ctypes.c_int), ("chunk_steps", ctypes.c_int), ("use_graphs", ctypes.c_int),
+                ("cool_enabled", ctypes.c_int), ("cool", cl_cool_params),
+                ("blocks_from_autotune", ctypes.c_int)]
+
+
+class cl_result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_int64), ("status", ctypes.c_int), ("n_steps", ctypes.c_int),
+                ("obs", cl_obs), ("last_cool", cl_cool_report), ("t_submit", ctypes.c_double),
+                ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"tag": self.tag, "status": self.status, "n_steps": self.n_steps,
+                "obs": self.obs.as_dict(), "last_cool": self.last_cool.as_dict(),
+                "t_submit": self.t_submit, "t_admit": self.t_admit, "t_done": self.t_done}
+
+
+class cl_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("active", ctypes.c_int), ("queued", ctypes.c_int), ("pooled", ctypes.c_int),
+                ("peak_active", ctypes.c_int), ("bytes_in_use", ctypes.c_uint64),
+                ("peak_bytes", ctypes.c_uint64)]
 
     def as_dict(self):
         return {n: getattr(self, n) for n, _ in self._fields_}
@@ -89,6 +127,12 @@ SIGNATURES = {
     "cl_observables_noalloc": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int), ctypes.c_double,
                                               ctypes.c_double, ctypes.c_double, _P, _P]),
     "cl_cool_last_report": (ctypes.c_int, [_P, ctypes.POINTER(cl_cool_report)]),
+    "cl_set_adaptive_step": (ctypes.c_int, [_P, ctypes.c_double]),
+    "cl_get_langevin_time": (ctypes.c_int, [_P, _dp, _dp, _dp]),
+    "cl_set_blocks": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "cl_get_blocks": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
+    "cl_autotune": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(cl_cool_params), ctypes.c_int,
+                                   ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]),
     "cl_stream_create": (ctypes.c_int, [ctypes.POINTER(_P)]),
     "cl_stream_destroy": (ctypes.c_int, [_P]),
     "cl_capture_step": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(cl_cool_params)]),
@@ -99,6 +143,17 @@ SIGNATURES = {
     "cl_batch_run": (ctypes.c_int, [_P, ctypes.c_int]),
     "cl_batch_synchronize": (ctypes.c_int, [_P]),
     "cl_batch_free": (None, [_P]),
+    "cl_reset_lattice": (ctypes.c_int, [_P, ctypes.POINTER(cl_params)]),
+    "cl_lattice_bytes": (ctypes.c_int, [ctypes.POINTER(cl_params), ctypes.POINTER(ctypes.c_size_t)]),
+    "cl_server_create": (ctypes.c_int, [ctypes.POINTER(cl_server_config), ctypes.POINTER(_P)]),
+    "cl_server_clock": (ctypes.c_double, [_P]),
+    "cl_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(cl_request), ctypes.c_double]),
+    "cl_server_poll": (ctypes.c_int, [_P, ctypes.POINTER(cl_result), ctypes.c_int,
+                                      ctypes.POINTER(ctypes.c_int)]),
+    "cl_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(cl_server_stats)]),
+    "cl_server_run_trace": (ctypes.c_int, [_P, ctypes.c_int, ctypes.POINTER(cl_request), _dp,
+                                           ctypes.POINTER(cl_result)]),
+    "cl_server_free": (None, [_P]),
     "cl_status_str": (ctypes.c_char_p, [ctypes.c_int]),
     "cl_last_error": (ctypes.c_char_p, []),
     "cl_version": (ctypes.c_int, []),
@@ -162,6 +217,103 @@ def cl_cool_last_report(lat):
     rep = cl_cool_report()
     _check(load().cl_cool_last_report(lat, ctypes.byref(rep)), "cl_cool_last_report")
     return rep.as_dict()
+
+
+def cl_set_adaptive_step(lat, k_ref):
+    _check(load().cl_set_adaptive_step(lat, k_ref), "cl_set_adaptive_step")
+
+
+def cl_get_langevin_time(lat):
+    """Returns (t, eps_last, kmax_last)."""
+    t, e, k = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(load().cl_get_langevin_time(lat, ctypes.byref(t), ctypes.byref(e), ctypes.byref(k)),
+           "cl_get_langevin_time")
+    return t.value, e.value, k.value
+
+
+def cl_set_blocks(lat, blocks):
+    b = (ctypes.c_int * CL_NTUNE)(*[int(v) for v in blocks])
+    _check(load().cl_set_blocks(lat, b), "cl_set_blocks")
+
+
+def cl_get_blocks(lat):
+    b = (ctypes.c_int * CL_NTUNE)()
+    _check(load().cl_get_blocks(lat, b), "cl_get_blocks")
+    return list(b)
+
+
+def cl_autotune(lat, eps, cp, reps=3, use_cache=True, want_table=False):
+    """Returns (blocks, table): table[c][f] = mean ms per step of family f at
+    block size TUNE_CANDIDATES[c] (None unless want_table)."""
+    b = (ctypes.c_int * CL_NTUNE)()
+    ms = np.zeros((len(TUNE_CANDIDATES), CL_NTUNE)) if want_table else None
+    _check(load().cl_autotune(lat, eps, ctypes.byref(cp), reps, int(use_cache), b,
+                              ms.ctypes.data_as(_dp) if want_table else None), "cl_autotune")
+    return list(b), ms
+
+
+def cl_reset_lattice(lat, params):
+    _check(load().cl_reset_lattice(lat, ctypes.byref(params)), "cl_reset_lattice")
+
+
+def cl_lattice_bytes(params):
+    b = ctypes.c_size_t()
+    _check(load().cl_lattice_bytes(ctypes.byref(params), ctypes.byref(b)), "cl_lattice_bytes")
+    return b.value
+
+
+def make_request(L, beta, theta, eps, n_steps, seed, start=CL_START_COLD, gauge_sigma=0.0, tag=0):
+    L = tuple(int(v) for v in (L if hasattr(L, "__len__") else (L,) * 4))
+    th = complex(theta)
+    return cl_request((ctypes.c_int * 4)(*L), beta, th.real, th.imag, eps, int(n_steps), seed, start,
+                      gauge_sigma, tag)
+
+
+def make_server_config(hbm_budget_bytes=150e9, max_slots=64, prec=CL_FP32_STORAGE, chunk_steps=8,
+                       use_graphs=True, cool=None, blocks_from_autotune=True):
+    return cl_server_config(hbm_budget_bytes, max_slots, prec, chunk_steps, int(use_graphs),
+                            int(cool is not None), cool if cool is not None else cl_cool_params(),
+                            int(blocks_from_autotune))
+
+
+def cl_server_create(cfg):
+    h = _P()
+    _check(load().cl_server_create(ctypes.byref(cfg), ctypes.byref(h)), "cl_server_create")
+    return h
+
+
+def cl_server_clock(srv):
+    return load().cl_server_clock(srv)
+
+
+def cl_server_submit(srv, req, t_submit=-1.0):
+    _check(load().cl_server_submit(srv, ctypes.byref(req), t_submit), "cl_server_submit")
+
+
+def cl_server_poll(srv, max_out=64):
+    out = (cl_result * max_out)()
+    n = ctypes.c_int()
+    _check(load().cl_server_poll(srv, out, max_out, ctypes.byref(n)), "cl_server_poll")
+    return [out[i].as_dict() for i in range(n.value)]
+
+
+def cl_server_stats_get(srv):
+    st = cl_server_stats()
+    _check(load().cl_server_stats_get(srv, ctypes.byref(st)), "cl_server_stats_get")
+    return st.as_dict()
+
+
+def cl_server_run_trace(srv, reqs, arrivals):
+    n = len(reqs)
+    arr = (cl_request * max(n, 1))(*reqs)
+    t = np.ascontiguousarray(arrivals, dtype=np.float64)
+    out = (cl_result * max(n, 1))()
+    _check(load().cl_server_run_trace(srv, n, arr, t.ctypes.data_as(_dp), out), "cl_server_run_trace")
+    return [out[i].as_dict() for i in range(n)]
+
+
+def cl_server_free(srv):
+    load().cl_server_free(srv)
 
 
 def cl_stream_create():
@@ -339,6 +491,57 @@ def make_cool(eps, alpha=1.0, mode=CL_D0, n_min=0, n_max=0, tol_rel=1e-3, d_floo
     return cl_cool_params(eps, alpha, mode, n_min, n_max, tol_rel, d_floor, d_guard, forced_sweeps)
 
 
+class Server:
+    """Owning wrapper of cl_server (see make_server_config)."""
+
+    def __init__(self, cfg):
+        self.h = None
+        self.h = cl_server_create(cfg)
+
+    def clock(self):
+        return cl_server_clock(self.h)
+
+    def submit(self, req, t_submit=-1.0):
+        cl_server_submit(self.h, req, t_submit)
+
+    def poll(self, max_out=64):
+        return cl_server_poll(self.h, max_out)
+
+    def stats(self):
+        return cl_server_stats_get(self.h)
+
+    def run_trace(self, reqs, arrivals):
+        return cl_server_run_trace(self.h, reqs, arrivals)
+
+    def drain(self, n, sleep=1e-4):
+        """Poll until n results have come back; returns them."""
+        import time
+        out = []
+        while len(out) < n:
+            got = self.poll()
+            out.extend(got)
+            if not got:
+                time.sleep(sleep)
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            cl_server_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Batch:
     """Owning wrapper of cl_batch: one graph launch advances every chain by
     one step.  The Lattice objects must outlive it and have distinct,
@@ -397,6 +600,21 @@ class Lattice:
 
     def last_cool_report(self):
         return cl_cool_last_report(self.h)
+
+    def set_adaptive_step(self, k_ref):
+        cl_set_adaptive_step(self.h, k_ref)
+
+    def langevin_time(self):
+        return cl_get_langevin_time(self.h)
+
+    def autotune(self, eps, cp, reps=3, use_cache=True, want_table=False):
+        return cl_autotune(self.h, eps, cp, reps, use_cache, want_table)
+
+    def blocks(self):
+        return cl_get_blocks(self.h)
+
+    def set_blocks(self, blocks):
+        cl_set_blocks(self.h, blocks)
 
     def capture_step(self, eps, cp=None):
         cl_capture_step(self.h, eps, cp)

@@ -3,19 +3,27 @@
 // link exchange.  All arithmetic runs in the kernels (kernels.cu,
 // k_update_*.cu); this file only allocates, sequences launches and copies.
 #include <climits>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
+#include <array>
+#include <mutex>
+#include <map>
 
 #include "../../include/cl.h"
 #include "launch.h"
+#include "runtime.h"
 
 using namespace clgc;
+using namespace clrt;
 
 namespace {
-
 thread_local std::string g_err;
+}  // namespace
+
+namespace clrt {
 
 const double KAPPA_Q = -1.0 / (256.0 * 9.86960440108935861883);  // q_L = kappa [Tr F F ...]
 
@@ -24,59 +32,15 @@ cl_status fail(cl_status s, const std::string& msg) {
   return s;
 }
 
-#define CK(call)                                                                   \
-  do {                                                                             \
-    cudaError_t e_ = (call);                                                       \
-    if (e_ != cudaSuccess)                                                         \
-      return fail(e_ == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA,      \
-                  std::string(#call) + ": " + cudaGetErrorString(e_));             \
-  } while (0)
-
-}  // namespace
+}  // namespace clrt
 
 namespace clgc {
 // Error text for entry points defined in other translation units.
 void set_last_error(const std::string& msg) { g_err = msg; }
 }  // namespace clgc
 
-struct cl_lattice {
-  cl_params p;
-  GeoH g;
-  int prec;
-  size_t esz;  // bytes of one complex element (16 or 8)
-  cudaStream_t st;
-  void* U;     // links, SoA [4][9][V]
-  void* Un;    // second link buffer (CL update target)
-  void* Ui;    // link inverses [4][9][V]
-  void* Pq;    // plaquettes [6][9][V]
-  void* Dq;    // P - P^{-1} [6][9][V]
-  void* C;     // per-plaquette drift contributions [24][9][V]
-  void* Gq;    // partial sums of transported dual fields [6][9][V]
-  void* F;     // clover field, SoA [6][9][V]
-  void* f;     // cooling gradient [8][V] (FP64 in both forms)
-  void* Om;    // packed Hermitian Omega [9][V]
-  void* Omi;   // and its inverse
-  double* partials;
-  CoolState* cs;
-  ObsOut* obs;
-  double* stage;  // AoS double staging, V*4*18 (allocated on first use)
-  double* qsite;  // per-site q_L (on first use)
-  uint64_t step;       // host mirror of *step_dev
-  uint32_t* step_dev;  // Philox step counter read by the update kernel
-  int64_t launches;
-  // step graphs (cl_capture_step): variant v starts from the link buffer in gU[v]
-  cudaGraphExec_t gexec[2];
-  void* gU[2];
-  int64_t glaunches;  // kernels in one captured step
-  // optional per-phase CUDA-event timing (cl_set_timing)
-  int timing;
-  std::vector<cudaEvent_t>* ev_pool;
-  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>* ev_pending;
-  double phase_ms[CL_NPHASE];
-  int64_t phase_n[CL_NPHASE];
-};
 
-namespace {
+namespace clrt {
 
 size_t real_size(const cl_lattice* l) { return l->prec == 0 ? 8 : 4; }
 
@@ -155,11 +119,23 @@ cl_status do_steps(cl_lattice* l, double eps, int n) {
   const double sre = KAPPA_Q * l->p.theta_im, sim = -KAPPA_Q * l->p.theta_re;
   for (int i = 0; i < n; ++i) {
     CK(do_force(l, th, sre, sim));
-    CK(timed(l, CL_PHASE_UPDATE, [&] {
-      return launch_update_gather(l->prec, 0, l->g, l->U, l->C, l->Un, eps, l->p.seed, l->step_dev,
-                                  l->st);
-    }));
-    CK(timed(l, CL_PHASE_UPDATE, [&] { return launch_step_bump(l->step_dev, l->st); }));
+    const bool adaptive = l->k_ref > 0.0;
+    if (adaptive) {
+      // drift into the (now free) link-inverse buffer with max |K|, then the
+      // step size on the device, then the update from the stored drift
+      CK(timed(l, CL_PHASE_UPDATE, [&] {
+        return launch_update_gather(l->prec, 2, l->g, l->U, l->C, l->Ui, eps, l->p.seed, l->sd, false, l->st);
+      }));
+      CK(timed(l, CL_PHASE_UPDATE, [&] { return launch_step_eps(l->sd, eps, l->k_ref, l->st); }));
+      CK(timed(l, CL_PHASE_UPDATE, [&] {
+        return launch_update_gather(l->prec, 3, l->g, l->U, l->Ui, l->Un, eps, l->p.seed, l->sd, true, l->st);
+      }));
+    } else {
+      CK(timed(l, CL_PHASE_UPDATE, [&] {
+        return launch_update_gather(l->prec, 0, l->g, l->U, l->C, l->Un, eps, l->p.seed, l->sd, false, l->st);
+      }));
+    }
+    CK(timed(l, CL_PHASE_UPDATE, [&] { return launch_step_bump(l->sd, eps, adaptive, l->st); }));
     std::swap(l->U, l->Un);
     l->step++;
   }
@@ -241,7 +217,38 @@ void to_report(const CoolState& c, cl_cool_report* r) {
   r->un_after = c.un_after;
 }
 
-}  // namespace
+}  // namespace clrt
+
+namespace clrt {
+
+// Device bytes of one lattice (the buffers cl_init_lattice allocates).
+size_t lattice_bytes(int V, int prec) {
+  const size_t Vs = (size_t)V, esz = prec == 0 ? 16 : 8, real = prec == 0 ? 8 : 4;
+  return esz * 9 * Vs * (4 + 4 + 4 + 6 + 6 + 24 + 6 + 6) + sizeof(double) * 8 * Vs + real * 9 * Vs * 2 +
+         sizeof(double) * NQ_OBS * (size_t)reduce_blocks(V) + sizeof(CoolState) + sizeof(ObsOut) +
+         sizeof(uint32_t);
+}
+
+// Start field, step counter and cooling state from l->p (cold or Haar start,
+// then the optional random SL(3,C) gauge transformation).
+cudaError_t init_state(cl_lattice* l) {
+  const cl_params* params = &l->p;
+  l->step = 0;
+  cudaError_t e = cudaMemsetAsync(l->cs, 0, sizeof(CoolState), l->st);
+  if (e == cudaSuccess) e = cudaMemsetAsync(l->sd, 0, sizeof(StepDev), l->st);
+  if (e == cudaSuccess)
+    e = params->start == CL_START_HOT ? launch_hot(l->prec, l->g, l->U, params->seed, l->st)
+                                      : launch_cold(l->prec, l->g, l->U, l->st);
+  l->launches++;
+  if (e == cudaSuccess && params->gauge_sigma > 0.0) {
+    e = launch_gauge_omega(l->prec, l->g, l->Om, l->Omi, params->seed, params->gauge_sigma, l->st);
+    if (e == cudaSuccess) e = launch_cool_apply(l->prec, l->g, l->U, l->Om, l->Omi, nullptr, l->st);
+    l->launches += 2;
+  }
+  return e;
+}
+
+}  // namespace clrt
 
 extern "C" {
 
@@ -291,27 +298,48 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
   alloc((void**)&l->partials, sizeof(double) * NQ_OBS * (size_t)reduce_blocks(l->g.V));
   alloc((void**)&l->cs, sizeof(CoolState));
   alloc((void**)&l->obs, sizeof(ObsOut));
-  alloc((void**)&l->step_dev, sizeof(uint32_t));
+  alloc((void**)&l->sd, sizeof(StepDev));
   if (s != CL_OK) {
     cl_free(l);
     return s;
   }
-  cudaError_t e = cudaMemsetAsync(l->cs, 0, sizeof(CoolState), l->st);
-  if (e == cudaSuccess) e = cudaMemsetAsync(l->step_dev, 0, sizeof(uint32_t), l->st);
-  if (e == cudaSuccess)
-    e = params->start == CL_START_HOT ? launch_hot(l->prec, l->g, l->U, params->seed, l->st)
-                                      : launch_cold(l->prec, l->g, l->U, l->st);
-  l->launches++;
-  if (e == cudaSuccess && params->gauge_sigma > 0.0) {
-    e = launch_gauge_omega(l->prec, l->g, l->Om, l->Omi, params->seed, params->gauge_sigma, l->st);
-    if (e == cudaSuccess) e = launch_cool_apply(l->prec, l->g, l->U, l->Om, l->Omi, nullptr, l->st);
-    l->launches += 2;
-  }
+  cudaError_t e = init_state(l);
   if (e != cudaSuccess) {
     cl_free(l);
     return fail(CL_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e));
   }
   *out = l;
+  return CL_OK;
+}
+
+cl_status cl_reset_lattice(cl_lattice* l, const cl_params* params) {
+  if (!l || !params) return fail(CL_ERR_INVALID, "NULL argument");
+  for (int mu = 0; mu < 4; ++mu)
+    if (params->L[mu] != l->p.L[mu]) return fail(CL_ERR_INVALID, "reset needs the same extents");
+  if (params->prec != l->p.prec) return fail(CL_ERR_INVALID, "reset needs the same precision");
+  if (params->start != CL_START_COLD && params->start != CL_START_HOT)
+    return fail(CL_ERR_INVALID, "bad start");
+  CK(cudaStreamSynchronize(l->st));
+  CK(resolve_timing(l));
+  for (int v = 0; v < 2; ++v)
+    if (l->gexec[v]) {
+      cudaGraphExecDestroy(l->gexec[v]);
+      l->gexec[v] = nullptr;
+    }
+  l->p = *params;
+  CK(init_state(l));
+  return CL_OK;
+}
+
+cl_status cl_lattice_bytes(const cl_params* params, size_t* bytes) {
+  if (!params || !bytes) return fail(CL_ERR_INVALID, "NULL argument");
+  long long V = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    if (params->L[mu] < 1) return fail(CL_ERR_INVALID, "lattice extent < 1");
+    V *= params->L[mu];
+    if (V * 6 * 9 > INT_MAX) return fail(CL_ERR_INVALID, "lattice too large");
+  }
+  *bytes = lattice_bytes((int)V, params->prec == CL_FP64 ? 0 : 1);
   return CL_OK;
 }
 
@@ -469,8 +497,27 @@ cl_status cl_set_step(cl_lattice* l, uint64_t step) {
   l->step = step;
   static thread_local uint32_t v;
   v = (uint32_t)step;
-  CK(cudaMemcpyAsync(l->step_dev, &v, sizeof(uint32_t), cudaMemcpyHostToDevice, l->st));
+  static_assert(offsetof(StepDev, step) == 0, "the step word leads StepDev");
+  CK(cudaMemcpyAsync(reinterpret_cast<uint32_t*>(l->sd), &v, sizeof(uint32_t), cudaMemcpyHostToDevice, l->st));
   CK(cudaStreamSynchronize(l->st));
+  return CL_OK;
+}
+
+cl_status cl_set_adaptive_step(cl_lattice* l, double k_ref) {
+  if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  if (!(k_ref >= 0.0)) return fail(CL_ERR_INVALID, "k_ref must be >= 0");
+  l->k_ref = k_ref;
+  return CL_OK;
+}
+
+cl_status cl_get_langevin_time(cl_lattice* l, double* t, double* eps_last, double* kmax_last) {
+  if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
+  StepDev h;
+  CK(cudaMemcpyAsync(&h, l->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, l->st));
+  CK(cudaStreamSynchronize(l->st));
+  if (t) *t = h.t;
+  if (eps_last) *eps_last = h.eps_n;
+  if (kmax_last) *kmax_last = h.kmax;
   return CL_OK;
 }
 
@@ -480,7 +527,7 @@ cl_status cl_drift(cl_lattice* l, double* host_aos) {
   if (s != CL_OK) return s;
   const bool th = theta_nonzero(l);
   CK(do_force(l, th, KAPPA_Q * l->p.theta_im, -KAPPA_Q * l->p.theta_re));
-  CK(launch_update_gather(l->prec, 1, l->g, l->U, l->C, l->Un, 0.0, l->p.seed, l->step_dev, l->st));
+  CK(launch_update_gather(l->prec, 1, l->g, l->U, l->C, l->Un, 0.0, l->p.seed, l->sd, false, l->st));
   CK(launch_soa_to_aos(l->prec, l->g, l->Un, l->stage, 4, l->st));
   l->launches += 2;
   CK(cudaMemcpyAsync(host_aos, l->stage, sizeof(double) * 18 * 4 * (size_t)l->g.V,
@@ -517,7 +564,9 @@ cl_status cl_launch_count(const cl_lattice* l, int64_t* count) {
 }
 
 // ------------------------------------------------------------- graphs
-namespace {
+}  // extern "C"
+
+namespace clrt {
 
 // Enqueue one step of the hot path (CL step, then cooling when cp != NULL).
 cl_status enqueue_step(cl_lattice* l, double eps, const cl_cool_params* cp) {
@@ -533,7 +582,9 @@ cl_status check_step_args(const cl_lattice* l, double eps, const cl_cool_params*
   return cp ? check_cool(cp) : CL_OK;
 }
 
-}  // namespace
+}  // namespace clrt
+
+extern "C" {
 
 cl_status cl_capture_step(cl_lattice* l, double eps, const cl_cool_params* cp) {
   cl_status s = check_step_args(l, eps, cp);
@@ -740,6 +791,161 @@ cl_status cl_batch_synchronize(cl_batch* b) {
   return CL_OK;
 }
 
+// ------------------------------------------------------------- autotuner
+namespace {
+
+const int TUNE_CANDIDATES[] = {32, 64, 128, 256};
+const int N_TUNE_CANDIDATES = 4;
+// the timing phase that holds each tunable family's kernels
+const int TUNE_PHASE[NTUNE] = {CL_PHASE_CLOVER, CL_PHASE_FORCE, CL_PHASE_UPDATE, CL_PHASE_COOL_OMEGA,
+                               CL_PHASE_COOL_APPLY};
+
+struct TuneKey {
+  int device, prec, theta, L[4];
+  bool operator<(const TuneKey& o) const {
+    return std::memcmp(this, &o, sizeof(TuneKey)) < 0;
+  }
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, std::array<int, NTUNE>>* g_tune_cache = nullptr;
+
+TuneKey tune_key(const cl_lattice* l) {
+  TuneKey k;
+  std::memset(&k, 0, sizeof(k));
+  cudaGetDevice(&k.device);
+  k.prec = l->prec;
+  k.theta = theta_nonzero(l) ? 1 : 0;
+  for (int mu = 0; mu < 4; ++mu) k.L[mu] = l->g.L[mu];
+  return k;
+}
+
+bool valid_block(int b) { return b == 0 || (b >= 32 && b <= TUNE_MAX_BLOCK && b % 32 == 0); }
+
+}  // namespace
+
+cl_status cl_set_blocks(cl_lattice* l, const int* blocks) {
+  if (!l || !blocks) return fail(CL_ERR_INVALID, "NULL argument");
+  for (int f = 0; f < NTUNE; ++f)
+    if (!valid_block(blocks[f])) return fail(CL_ERR_INVALID, "block size must be 0 or a multiple of 32 in [32, 256]");
+  for (int f = 0; f < NTUNE; ++f) l->g.blk[f] = blocks[f];
+  return CL_OK;
+}
+
+cl_status cl_get_blocks(cl_lattice* l, int* blocks) {
+  if (!l || !blocks) return fail(CL_ERR_INVALID, "NULL argument");
+  for (int f = 0; f < NTUNE; ++f) blocks[f] = block_of(l->g, f);
+  return CL_OK;
+}
+
+cl_status cl_autotune(cl_lattice* l, double eps, const cl_cool_params* cp, int reps, int use_cache,
+                      int* blocks_out, double* ms_out) {
+  if (!l || !cp || reps < 1) return fail(CL_ERR_INVALID, "bad arguments");
+  if (!(eps >= 0.0)) return fail(CL_ERR_INVALID, "bad eps");
+  cl_status s = check_cool(cp);
+  if (s != CL_OK) return s;
+  const TuneKey key = tune_key(l);
+  if (use_cache && !ms_out) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (g_tune_cache) {
+      auto it = g_tune_cache->find(key);
+      if (it != g_tune_cache->end()) {
+        for (int f = 0; f < NTUNE; ++f) l->g.blk[f] = it->second[f];
+        if (blocks_out) cl_get_blocks(l, blocks_out);
+        return CL_OK;
+      }
+    }
+  }
+  CK(resolve_timing(l));
+  CK(cudaStreamSynchronize(l->st));
+  // snapshot everything a trial step changes; the trials run on the lattice's
+  // own buffers and the snapshot is put back afterwards
+  const size_t link_bytes = l->esz * 4 * 9 * (size_t)l->g.V;
+  void* saved = nullptr;
+  CK(cudaMalloc(&saved, link_bytes));
+  CoolState cs0;
+  StepDev sd0;
+  cudaError_t e = cudaMemcpyAsync(saved, l->U, link_bytes, cudaMemcpyDeviceToDevice, l->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&cs0, l->cs, sizeof(cs0), cudaMemcpyDeviceToHost, l->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&sd0, l->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, l->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(l->st);
+  if (e != cudaSuccess) {
+    cudaFree(saved);
+    return fail(CL_ERR_CUDA, std::string("autotune snapshot: ") + cudaGetErrorString(e));
+  }
+  const uint64_t step0 = l->step;
+  const int64_t launches0 = l->launches;
+  const int timing0 = l->timing;
+  double ms0[CL_NPHASE];
+  int64_t n0[CL_NPHASE];
+  std::memcpy(ms0, l->phase_ms, sizeof(ms0));
+  std::memcpy(n0, l->phase_n, sizeof(n0));
+  int blk0[NTUNE];
+  std::memcpy(blk0, l->g.blk, sizeof(blk0));
+  cl_cool_params tcp = *cp;
+  tcp.forced_sweeps = 2;  // the Omega and apply kernels must run in every trial
+  double table[N_TUNE_CANDIDATES][NTUNE];
+  for (int c = 0; c < N_TUNE_CANDIDATES && s == CL_OK; ++c) {
+    for (int f = 0; f < NTUNE; ++f) l->g.blk[f] = TUNE_CANDIDATES[c];
+    e = cudaMemcpyAsync(l->U, saved, link_bytes, cudaMemcpyDeviceToDevice, l->st);
+    if (e != cudaSuccess) {
+      s = fail(CL_ERR_CUDA, cudaGetErrorString(e));
+      break;
+    }
+    l->timing = 0;
+    s = enqueue_step(l, eps, &tcp);  // warm-up
+    if (s != CL_OK) break;
+    l->timing = 1;
+    for (int i = 0; i < CL_NPHASE; ++i) {
+      l->phase_ms[i] = 0.0;
+      l->phase_n[i] = 0;
+    }
+    for (int r = 0; r < reps && s == CL_OK; ++r) s = enqueue_step(l, eps, &tcp);
+    if (s != CL_OK) break;
+    e = resolve_timing(l);
+    if (e != cudaSuccess) {
+      s = fail(CL_ERR_CUDA, cudaGetErrorString(e));
+      break;
+    }
+    for (int f = 0; f < NTUNE; ++f) table[c][f] = l->phase_ms[TUNE_PHASE[f]] / reps;
+  }
+  l->timing = 0;
+  resolve_timing(l);
+  // restore the lattice
+  e = cudaMemcpyAsync(l->U, saved, link_bytes, cudaMemcpyDeviceToDevice, l->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(l->cs, &cs0, sizeof(cs0), cudaMemcpyHostToDevice, l->st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(l->sd, &sd0, sizeof(StepDev), cudaMemcpyHostToDevice, l->st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(l->st);
+  cudaFree(saved);
+  l->step = step0;
+  l->launches = launches0;
+  l->timing = timing0;
+  std::memcpy(l->phase_ms, ms0, sizeof(ms0));
+  std::memcpy(l->phase_n, n0, sizeof(n0));
+  if (s == CL_OK && e != cudaSuccess) s = fail(CL_ERR_CUDA, std::string("autotune restore: ") + cudaGetErrorString(e));
+  if (s != CL_OK) {
+    std::memcpy(l->g.blk, blk0, sizeof(blk0));
+    return s;
+  }
+  std::array<int, NTUNE> best;
+  for (int f = 0; f < NTUNE; ++f) {
+    int bc = 0;
+    for (int c = 1; c < N_TUNE_CANDIDATES; ++c)
+      if (table[c][f] < table[bc][f]) bc = c;
+    best[f] = TUNE_CANDIDATES[bc];
+    l->g.blk[f] = best[f];
+  }
+  if (ms_out)
+    for (int c = 0; c < N_TUNE_CANDIDATES; ++c)
+      for (int f = 0; f < NTUNE; ++f) ms_out[c * NTUNE + f] = table[c][f];
+  if (blocks_out) cl_get_blocks(l, blocks_out);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    if (!g_tune_cache) g_tune_cache = new std::map<TuneKey, std::array<int, NTUNE>>();
+    (*g_tune_cache)[key] = best;
+  }
+  return CL_OK;
+}
+
 cl_status cl_stream_create(void** out) {
   if (!out) return fail(CL_ERR_INVALID, "NULL argument");
   *out = nullptr;
@@ -786,7 +992,7 @@ cl_status cl_synchronize(cl_lattice* l) {
 void cl_free(cl_lattice* l) {
   if (!l) return;
   void* bufs[] = {l->U, l->Un, l->Ui, l->Pq, l->Dq, l->C, l->Gq, l->F, l->f, l->Om, l->Omi, l->partials, l->cs, l->obs,
-                  l->stage, l->qsite, l->step_dev};
+                  l->stage, l->qsite, l->sd};
   for (int v = 0; v < 2; ++v)
     if (l->gexec[v]) cudaGraphExecDestroy(l->gexec[v]);
   if (l->st) cudaStreamSynchronize(l->st);

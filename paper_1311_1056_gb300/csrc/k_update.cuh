@@ -34,17 +34,19 @@
 #pragma once
 #include "expm.cuh"
 #include "lattice.cuh"
+#include "launch.h"
 #include "philox.cuh"
 #include "su3.cuh"
 
 namespace clgc {
 
-enum { MODE_UPDATE = 0, MODE_DRIFT = 1 };
+enum { MODE_UPDATE = 0, MODE_DRIFT = 1, MODE_DRIFTMAX = 2, MODE_UPDATE_X = 3 };
 
 struct UpdArgs {
   double beta, eps, sqrt_eps;
   uint64_t seed;
-  const uint32_t* step;  // device-resident Philox step counter (graph-replayable)
+  StepDev* sd;    // device-resident step state (graph-replayable)
+  int adaptive;   // 1: the step size is sd->eps_n (set by the drift pass)
 };
 
 // Sign flip on the integer pipe (no floating-point instruction).
@@ -96,7 +98,7 @@ __device__ __forceinline__ void scaled(mat<T>& r, T c, const mat<T>& a) {
 // ---------------------------------------------------------------- inverses
 // Ui = adj(U) = U^{-1} for every link (det U = 1 by the re-projection).
 template <typename T>
-__global__ void __launch_bounds__(128) k_link_inverse(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_link_inverse(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                       typename vec2_of<T>::type* __restrict__ Ui) {
   const int mu = blockIdx.x % 4;
   const int s = (blockIdx.x / 4) * blockDim.x + threadIdx.x;
@@ -111,7 +113,7 @@ __global__ void __launch_bounds__(128) k_link_inverse(Geo g, const typename vec2
 // P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^{-1} U_nu(x)^{-1} and
 // D = P - P^{-1}, six planes per site.
 template <typename T>
-__global__ void __launch_bounds__(128) k_plaq(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                               const typename vec2_of<T>::type* __restrict__ Ui,
                                               typename vec2_of<T>::type* __restrict__ Pq,
                                               typename vec2_of<T>::type* __restrict__ Dq) {
@@ -143,7 +145,7 @@ __global__ void __launch_bounds__(128) k_plaq(Geo g, const typename vec2_of<T>::
 //   L3 = W^{-1} P(x-mu-nu) W with W = U_mu(x-mu-nu) U_nu(x-nu),
 // so F = D(x) + the three carried D's.  Stored times a complex scale.
 template <typename T>
-__global__ void __launch_bounds__(128) k_clover_rot(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_clover_rot(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                     const typename vec2_of<T>::type* __restrict__ Ui,
                                                     const typename vec2_of<T>::type* __restrict__ Dq,
                                                     typename vec2_of<T>::type* __restrict__ F,
@@ -189,7 +191,7 @@ __global__ void __launch_bounds__(128) k_clover_rot(Geo g, const typename vec2_o
 // stages run as two kernels with the partial G^ parked in Gq, so neither
 // spills; in FP32 one kernel runs both.
 template <typename T>
-__global__ void __launch_bounds__(128) k_plaq_force_wilson(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_wilson(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                            const typename vec2_of<T>::type* __restrict__ Ui,
                                                            const typename vec2_of<T>::type* __restrict__ Dq,
                                                            typename vec2_of<T>::type* C, T beta6) {
@@ -325,7 +327,7 @@ __device__ __forceinline__ void force_stage_b(mat<T>& Gh, const Geo& g, int s, c
 
 // Split form (FP64): stage a, G^ parked in Gq, stage b.
 template <typename T>
-__global__ void __launch_bounds__(128) k_plaq_force_a(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_a(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                       const typename vec2_of<T>::type* __restrict__ Ui,
                                                       const typename vec2_of<T>::type* __restrict__ Dq,
                                                       const typename vec2_of<T>::type* __restrict__ F,
@@ -341,7 +343,7 @@ __global__ void __launch_bounds__(128) k_plaq_force_a(Geo g, const typename vec2
   store(Gq, p, s, g.V, Gh);
 }
 template <typename T>
-__global__ void __launch_bounds__(128) k_plaq_force_b(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_b(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                       const typename vec2_of<T>::type* __restrict__ Ui,
                                                       const typename vec2_of<T>::type* __restrict__ Pq,
                                                       const typename vec2_of<T>::type* __restrict__ Dq,
@@ -359,7 +361,7 @@ __global__ void __launch_bounds__(128) k_plaq_force_b(Geo g, const typename vec2
 }
 // Fused form (FP32, which needs no split to stay in registers).
 template <typename T>
-__global__ void __launch_bounds__(128) k_plaq_force_ab(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_ab(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                        const typename vec2_of<T>::type* __restrict__ Ui,
                                                        const typename vec2_of<T>::type* __restrict__ Pq,
                                                        const typename vec2_of<T>::type* __restrict__ Dq,
@@ -412,31 +414,56 @@ __device__ __forceinline__ void exponent(mat<R>& A, const R* g, R eps, R sqrt_ep
 // mu < nu: slot 0 of (x, p) and slot 3 of (x - nu, p); mu > nu: slot 1 of
 // (x, p) and slot 2 of (x - nu, p), p the plane of (mu, nu).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(128) k_update_gather(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                        const typename vec2_of<T>::type* __restrict__ C,
                                                        typename vec2_of<T>::type* __restrict__ out,
                                                        UpdArgs a) {
   const int MU = blockIdx.x % 4;
-  const int s = (blockIdx.x / 4) * blockDim.x + threadIdx.x;
-  if (s >= g.V) return;
+  const int s_raw = (blockIdx.x / 4) * blockDim.x + threadIdx.x;
+  if (MODE != MODE_DRIFTMAX && s_raw >= g.V) return;
+  // the max pass keeps whole warps alive for its shuffle: lanes past the end
+  // redo the last site (same value, so the max is unchanged)
+  const int s = s_raw < g.V ? s_raw : g.V - 1;
   int x[4];
   site_coords(g, s, x);
   mat<T> X, t;
-  set_zero(X);
+  if (MODE == MODE_UPDATE_X) {
+    load(X, C, MU, s, g.V);  // the drift stored by the MODE_DRIFTMAX pass
+  } else {
+    set_zero(X);
 #pragma unroll
-  for (int nu = 0; nu < 4; ++nu) {
-    if (nu == MU) continue;
-    const int p = MU < nu ? plane_index(MU, nu) : plane_index(nu, MU);
-    const int sl_here = MU < nu ? 0 : 1, sl_back = MU < nu ? 3 : 2;
-    load(t, C, 4 * p + sl_here, s, g.V);
+    for (int nu = 0; nu < 4; ++nu) {
+      if (nu == MU) continue;
+      const int p = MU < nu ? plane_index(MU, nu) : plane_index(nu, MU);
+      const int sl_here = MU < nu ? 0 : 1, sl_back = MU < nu ? 3 : 2;
+      load(t, C, 4 * p + sl_here, s, g.V);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) X.e[k] = cadd(X.e[k], t.e[k]);
-    load(t, C, 4 * p + sl_back, hop(g, s, x, nu, -1), g.V);
+      for (int k = 0; k < 9; ++k) X.e[k] = cadd(X.e[k], t.e[k]);
+      load(t, C, 4 * p + sl_back, hop(g, s, x, nu, -1), g.V);
 #pragma unroll
-    for (int k = 0; k < 9; ++k) X.e[k] = cadd(X.e[k], t.e[k]);
+      for (int k = 0; k < 9; ++k) X.e[k] = cadd(X.e[k], t.e[k]);
+    }
   }
   if (MODE == MODE_DRIFT) {
     store(out, MU, s, g.V, X);
+    return;
+  }
+  if (MODE == MODE_DRIFTMAX) {
+    if (s_raw < g.V) store(out, MU, s, g.V, X);
+    // |K|^2 = sum_a |Tr(lambda_a X)|^2 = 2 |X - Tr X / 3|_F^2 (Tr l_a l_b = 2 delta_ab)
+    mat<double> Xd;
+    convert(Xd, X);
+    const double tr_re = (Xd.e[0].re + Xd.e[4].re + Xd.e[8].re) * (1.0 / 3.0);
+    const double tr_im = (Xd.e[0].im + Xd.e[4].im + Xd.e[8].im) * (1.0 / 3.0);
+    Xd.e[0].re -= tr_re; Xd.e[4].re -= tr_re; Xd.e[8].re -= tr_re;
+    Xd.e[0].im -= tr_im; Xd.e[4].im -= tr_im; Xd.e[8].im -= tr_im;
+    unsigned long long k2 = (unsigned long long)__double_as_longlong(2.0 * norm2(Xd));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long v = __shfl_xor_sync(0xffffffffu, k2, o);
+      k2 = v > k2 ? v : k2;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(&a.sd->kmax2_bits, k2);
     return;
   }
   // exponent A = 2 eps (X - Tr X/3) + i sqrt(eps) eta_a lambda_a; exp in FP64.
@@ -444,18 +471,20 @@ __global__ void __launch_bounds__(128) k_update_gather(Geo g, const typename vec
   // (X and the noise carry FP32 information only) and widens it for the exp.
   mat<double> A;
   float rA = -1.f;
-  const uint32_t step = __ldg(a.step);
+  const uint32_t step = a.sd->step;
+  const double eps = a.adaptive ? a.sd->eps_n : a.eps;
+  const double sqrt_eps = a.adaptive ? a.sd->sqrt_eps_n : a.sqrt_eps;
   if (sizeof(T) == 8) {
     double eta[8];
     normals_f64<4>(eta, a.seed, step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
     convert(A, X);
-    exponent<double>(A, eta, a.eps, a.sqrt_eps);
+    exponent<double>(A, eta, eps, sqrt_eps);
   } else {
     float ef[8];
     normals_f32<4>(ef, a.seed, step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
     mat<float> Af;
     convert(Af, X);
-    exponent<float>(Af, ef, (float)a.eps, (float)a.sqrt_eps);
+    exponent<float>(Af, ef, (float)eps, (float)sqrt_eps);
     rA = sqrtf(norm2(Af));
     convert(A, Af);
   }

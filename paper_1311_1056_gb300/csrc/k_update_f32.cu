@@ -8,26 +8,26 @@ namespace {
 typedef vec2_of<float>::type V2;
 // 1-D grid, plane (or direction) fastest: the blocks resident at one time
 // cover every plane of a range of sites, so shared neighbours stay in cache.
-inline dim3 grid(int V, int planes) { return dim3((unsigned)(((V + 127) / 128) * planes)); }
+inline dim3 grid(int V, int planes, int bs) { return dim3((unsigned)(((V + bs - 1) / bs) * planes)); }
 }  // namespace
 
 cudaError_t launch_link_inverse_f32(const GeoH& h, const void* U, void* Ui, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
-  k_link_inverse<float><<<grid(g.V, 4), 128, 0, st>>>(g, (const V2*)U, (V2*)Ui);
+  k_link_inverse<float><<<grid(g.V, 4, block_of(h, TUNE_CLOVER)), block_of(h, TUNE_CLOVER), 0, st>>>(g, (const V2*)U, (V2*)Ui);
   return cudaGetLastError();
 }
 
 cudaError_t launch_plaq_f32(const GeoH& h, const void* U, const void* Ui, void* Pq, void* Dq,
                            cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
-  k_plaq<float><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (V2*)Pq, (V2*)Dq);
+  k_plaq<float><<<grid(g.V, 6, block_of(h, TUNE_CLOVER)), block_of(h, TUNE_CLOVER), 0, st>>>(g, (const V2*)U, (const V2*)Ui, (V2*)Pq, (V2*)Dq);
   return cudaGetLastError();
 }
 
 cudaError_t launch_clover_rot_f32(const GeoH& h, const void* U, const void* Ui, const void* Dq,
                                  void* F, double sre, double sim, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
-  k_clover_rot<float><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+  k_clover_rot<float><<<grid(g.V, 6, block_of(h, TUNE_CLOVER)), block_of(h, TUNE_CLOVER), 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
                                                   (V2*)F, sre, sim);
   return cudaGetLastError();
 }
@@ -38,28 +38,36 @@ cudaError_t launch_plaq_force_f32(bool theta, const GeoH& h, const void* U, cons
   Geo g = make_geo(h.L, h.V);
   const float b6 = (float)(beta / 6.0);
   if (!theta) {
-    k_plaq_force_wilson<float><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+    k_plaq_force_wilson<float><<<grid(g.V, 6, block_of(h, TUNE_FORCE)), block_of(h, TUNE_FORCE), 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
                                                          (V2*)C, b6);
     return cudaGetLastError();
   }
-  k_plaq_force_ab<float><<<grid(g.V, 6), 128, 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
+  k_plaq_force_ab<float><<<grid(g.V, 6, block_of(h, TUNE_FORCE)), block_of(h, TUNE_FORCE), 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
                                                       (const V2*)Dq, (const V2*)F, (V2*)C, b6);
   return cudaGetLastError();
 }
 
 cudaError_t launch_update_gather_f32(int mode, const GeoH& h, const void* U, const void* C, void* out,
-                                    double eps, uint64_t seed, const uint32_t* step, cudaStream_t st) {
+                                    double eps, uint64_t seed, StepDev* sd, bool adaptive, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
   UpdArgs a;
   a.beta = 0.0;
   a.eps = eps;
   a.sqrt_eps = sqrt(eps);
   a.seed = seed;
-  a.step = step;
-  if (mode == MODE_DRIFT)
-    k_update_gather<float, MODE_DRIFT><<<grid(g.V, 4), 128, 0, st>>>(g, (const V2*)U, (const V2*)C, (V2*)out, a);
-  else
-    k_update_gather<float, MODE_UPDATE><<<grid(g.V, 4), 128, 0, st>>>(g, (const V2*)U, (const V2*)C, (V2*)out, a);
+  a.sd = sd;
+  a.adaptive = adaptive ? 1 : 0;
+  const int bs = block_of(h, TUNE_UPDATE);
+  const dim3 gr = grid(g.V, 4, bs);
+  const V2* u = (const V2*)U;
+  const V2* c = (const V2*)C;
+  V2* o = (V2*)out;
+  switch (mode) {
+    case MODE_DRIFT: k_update_gather<float, MODE_DRIFT><<<gr, bs, 0, st>>>(g, u, c, o, a); break;
+    case MODE_DRIFTMAX: k_update_gather<float, MODE_DRIFTMAX><<<gr, bs, 0, st>>>(g, u, c, o, a); break;
+    case MODE_UPDATE_X: k_update_gather<float, MODE_UPDATE_X><<<gr, bs, 0, st>>>(g, u, c, o, a); break;
+    default: k_update_gather<float, MODE_UPDATE><<<gr, bs, 0, st>>>(g, u, c, o, a); break;
+  }
   return cudaGetLastError();
 }
 

@@ -18,10 +18,6 @@ Geo to_geo(const GeoH& h) { return make_geo(h.L, h.V); }
 inline dim3 grid_sites(int V, int planes = 1) {
   return dim3((unsigned)((V + RED_THREADS - 1) / RED_THREADS), (unsigned)planes);
 }
-// 1-D grid with the direction fastest (see k_update_f64.cu).
-inline dim3 grid_sites_1d(int V, int planes) {
-  return dim3((unsigned)(((V + RED_THREADS - 1) / RED_THREADS) * planes));
-}
 
 // Fixed-order block reduction of NQ doubles (slot MAXSLOT takes the max);
 // one record per block into partials.
@@ -355,7 +351,7 @@ __global__ void k_cool_adapt(Geo g, const double* partials, int nb, CoolArgs a, 
 
 // Omega_x = exp(-eps alpha_ad f_ax lambda_a) and its inverse, FP64.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_cool_omega(Geo g, const double* __restrict__ f, T* Om, T* Omi,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_omega(Geo g, const double* __restrict__ f, T* Om, T* Omi,
                                                            double eps, const CoolState* cs) {
   if (cs->done) return;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -372,7 +368,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_omega(Geo g, const double*
 // U_{x,mu} <- Omega_x U_{x,mu} Omega_{x+mu}^{-1}, all links at once (in place:
 // every link is read and written by the same thread).
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_cool_apply(Geo g, typename vec2_of<T>::type* U, const T* __restrict__ Om,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_apply(Geo g, typename vec2_of<T>::type* U, const T* __restrict__ Om,
                                                            const T* __restrict__ Omi,
                                                            const CoolState* cs) {
   if (cs && cs->done) return;
@@ -556,20 +552,24 @@ cudaError_t launch_cool_adapt(const GeoH& h, const double* partials, CoolArgs a,
 cudaError_t launch_cool_omega(int prec, const GeoH& h, const void* f, void* Om, void* Omi, double eps,
                               const CoolState* cs, cudaStream_t st) {
   Geo g = to_geo(h);
+  const int bs = block_of(h, TUNE_OMEGA);
+  const dim3 grid((unsigned)((g.V + bs - 1) / bs));
   if (prec == 0)
-    k_cool_omega<double><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const double*)f, (double*)Om, (double*)Omi, eps, cs);
+    k_cool_omega<double><<<grid, bs, 0, st>>>(g, (const double*)f, (double*)Om, (double*)Omi, eps, cs);
   else
-    k_cool_omega<float><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (const double*)f, (float*)Om, (float*)Omi, eps, cs);
+    k_cool_omega<float><<<grid, bs, 0, st>>>(g, (const double*)f, (float*)Om, (float*)Omi, eps, cs);
   return cudaGetLastError();
 }
 
 cudaError_t launch_cool_apply(int prec, const GeoH& h, void* U, const void* Om, const void* Omi,
                               const CoolState* cs, cudaStream_t st) {
   Geo g = to_geo(h);
+  const int bs = block_of(h, TUNE_APPLY);
+  const dim3 grid((unsigned)(((g.V + bs - 1) / bs) * 4));
   if (prec == 0)
-    k_cool_apply<double><<<grid_sites_1d(g.V, 4), RED_THREADS, 0, st>>>(g, (double2*)U, (const double*)Om, (const double*)Omi, cs);
+    k_cool_apply<double><<<grid, bs, 0, st>>>(g, (double2*)U, (const double*)Om, (const double*)Omi, cs);
   else
-    k_cool_apply<float><<<grid_sites_1d(g.V, 4), RED_THREADS, 0, st>>>(g, (float2*)U, (const float*)Om, (const float*)Omi, cs);
+    k_cool_apply<float><<<grid, bs, 0, st>>>(g, (float2*)U, (const float*)Om, (const float*)Omi, cs);
   return cudaGetLastError();
 }
 

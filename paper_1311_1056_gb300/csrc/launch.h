@@ -6,9 +6,30 @@
 
 namespace clgc {
 
+// Launch families whose block size is tunable (cl_autotune).  Every thread
+// of these kernels owns one site (or one link), so the block size changes
+// neither the arithmetic nor its order; the reductions keep a fixed shape.
+enum { TUNE_CLOVER = 0, TUNE_FORCE = 1, TUNE_UPDATE = 2, TUNE_OMEGA = 3, TUNE_APPLY = 4, NTUNE = 5 };
+const int TUNE_DEFAULT_BLOCK = 128;
+const int TUNE_MAX_BLOCK = 256;  // the launch bound of the tunable kernels
+
 struct GeoH {
   int L[4];
   int V;
+  int blk[NTUNE];  // threads per block per family; 0 = TUNE_DEFAULT_BLOCK
+};
+
+inline int block_of(const GeoH& h, int fam) { return h.blk[fam] > 0 ? h.blk[fam] : TUNE_DEFAULT_BLOCK; }
+
+// Per-lattice step state, resident on the device so that captured graphs
+// replay with fresh noise and the adaptive step size is decided on the GPU.
+struct StepDev {
+  uint32_t step;                 // Philox step counter (the noise key's step word)
+  uint32_t pad;
+  double eps_n, sqrt_eps_n;      // step size of the current step (adaptive mode)
+  double t;                      // Langevin time: sum of the step sizes taken
+  double kmax;                   // K_max of the last adaptive step
+  unsigned long long kmax2_bits; // running max of |K|^2 (non-negative doubles order as integers)
 };
 
 // Packed results of the cooling rule, resident on the device.
@@ -62,11 +83,17 @@ cudaError_t launch_clover_rot(int prec, const GeoH& g, const void* U, const void
 cudaError_t launch_plaq_force(int prec, bool theta, const GeoH& g, const void* U, const void* Ui,
                               const void* Pq, const void* Dq, const void* F, void* Gq, void* C,
                               double beta, cudaStream_t st);
-cudaError_t launch_update_gather(int prec, int mode, const GeoH& g, const void* U, const void* C,
-                                 void* out, double eps, uint64_t seed, const uint32_t* step,
-                                 cudaStream_t st);
+// mode 0: update from the gathered drift (eps, or the device step size when
+// sd_adaptive); 1: write the drift X_S to out; 2: write X_S to out and fold
+// max |K|^2 into sd->kmax2_bits; 3: update reading X_S from C (a mode-2 output).
+cudaError_t launch_update_gather(int prec, int mode, const GeoH& g, const void* U, const void* C, void* out,
+                                 double eps, uint64_t seed, StepDev* sd, bool sd_adaptive, cudaStream_t st);
 // step += 1 on the device (the Philox step counter read by the update).
-cudaError_t launch_step_bump(uint32_t* step, cudaStream_t st);
+// After an update: step += 1 and t += the step size taken (eps, or the
+// device step size when adaptive).
+cudaError_t launch_step_bump(StepDev* sd, double eps, bool adaptive, cudaStream_t st);
+// Adaptive step size from the drift pass: eps_n = eps min(1, k_ref / K_max).
+cudaError_t launch_step_eps(StepDev* sd, double eps, double k_ref, cudaStream_t st);
 // Cooling: gradient f (8 FP64 values per site, [a][V]) + partial sums; the
 // rule; Omega; apply.
 cudaError_t launch_cool_grad(int prec, const GeoH& g, const void* U, void* f, double* partials,

@@ -41,3 +41,33 @@ def test_invalid_arguments_fail_without_device_work():
     assert "extent" in cl.cl_last_error()
     with pytest.raises(cl.CLError):
         cl.cl_step(None, 0.01, 1)
+
+
+def test_struct_layouts_match_the_header(tmp_path):
+    """The ctypes structures of the binding have the sizes and field offsets
+    the C compiler gives the header's structs."""
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_1311_1056_gb300 import cl
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = ["cl_params", "cl_cool_params", "cl_obs", "cl_cool_report", "cl_request",
+               "cl_server_config", "cl_result", "cl_server_stats"]
+    lines = ["#include <stdio.h>", "#include <stddef.h>", '#include "cl.h"', "int main(void) {"]
+    for s in structs:
+        lines.append('printf("%s %%zu\\n", sizeof(%s));' % (s, s))
+        for f, _ in getattr(cl, s)._fields_:
+            lines.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (s, f, s, f))
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c99", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(l.split() for l in subprocess.check_output([str(exe)]).decode().split("\n") if l)
+    for s in structs:
+        T = getattr(cl, s)
+        assert int(got[s]) == ctypes.sizeof(T), s
+        for f, _ in T._fields_:
+            assert int(got["%s.%s" % (s, f)]) == getattr(T, f).offset, (s, f)
