@@ -393,10 +393,21 @@ def reference(args):
 
 
 # ----------------------------------------------------------- batched ensemble
-BATCH = dict(eps=0.005, alpha=1.0, n_min=1, n_max=10, tol_rel=0.01)
+# k_ref: the adaptive Langevin step size (eps_n = eps min(1, k_ref / K_max));
+# typical K_max of these lattices is 17-19, and without the control chains at
+# beta 5.6, theta 2 run away (non-finite links) after ~750 steps.
+BATCH = dict(eps=0.005, alpha=1.0, n_min=1, n_max=10, tol_rel=0.01, k_ref=12.0)
 BATCH_NAME = ("ensemble of independent chains, L^4 with L uniform in {8, 12, 16}, beta ~ U[5.6, 6.2], "
               "theta in {0, 0.5, 1, 1.5, 2}, cold start; each CL step (eps 0.005) followed by adaptive "
-              "cooling (alpha_ad = 1 / D_2, 1..10 sweeps, stop below 1 % relative progress)")
+              "cooling (alpha_ad = 1 / D_2, 1..10 sweeps, stop below 1 % relative progress), adaptive step "
+              "size k_ref 12")
+
+
+def _log(msg):
+    print("[bench %.1fs] %s" % (time.perf_counter() - _T0, msg), file=sys.stderr, flush=True)
+
+
+_T0 = time.perf_counter()
 
 
 def _run_chains(cl, torch, chains, prec, n_steps, batched, tune):
@@ -408,6 +419,8 @@ def _run_chains(cl, torch, chains, prec, n_steps, batched, tune):
                       n_max=BATCH["n_max"], tol_rel=BATCH["tol_rel"])
     lats = [cl.Lattice(c["L"], beta=c["beta"], theta=c["theta"], prec=prec, seed=c["seed"],
                        start=cl.CL_START_COLD, own_stream=True) for c in chains]
+    for lat in lats:
+        lat.set_adaptive_step(BATCH["k_ref"])
     tuned = {}
     if tune:
         for c, lat in zip(chains, lats):
@@ -415,9 +428,11 @@ def _run_chains(cl, torch, chains, prec, n_steps, batched, tune):
             tuned["%d^4 theta%s0" % (c["L"][0], "!=" if c["theta"] else "=")] = blocks
     n0 = sum(l.launches() for l in lats)
     torch.cuda.synchronize()
+    _log("  %d lattices ready" % len(lats))
     if batched:
         b = cl.Batch(lats, BATCH["eps"], [cp] * len(lats))
         torch.cuda.synchronize()
+        _log("  batch graph captured")
         t0 = time.perf_counter()
         b.run(n_steps)
         b.synchronize()
@@ -457,23 +472,25 @@ def batch_mode(args):
     sampler = ClockSampler(0)
     sampler.start()
     arms = {}
-    arms["batched_fp32"] = _run_chains(cl, torch, chains, cl.CL_FP32_STORAGE, n_steps, True, True)
-    arms["batched_fp64"] = _run_chains(cl, torch, chains, cl.CL_FP64, n_steps, True, True)
-    arms["alone_fp32"] = _run_chains(cl, torch, chains, cl.CL_FP32_STORAGE, n_steps, False, False)
-    arms["alone_fp64"] = _run_chains(cl, torch, chains, cl.CL_FP64, n_steps, False, False)
+    for name, prec, batched in (("batched_fp32", cl.CL_FP32_STORAGE, True), ("batched_fp64", cl.CL_FP64, True),
+                                ("alone_fp32", cl.CL_FP32_STORAGE, False), ("alone_fp64", cl.CL_FP64, False)):
+        _log("arm %s" % name)
+        arms[name] = _run_chains(cl, torch, chains, prec, n_steps, batched, batched)
+        _log("arm %s: %.2f s" % (name, arms[name][0]))
     clocks = sampler.stop()
     ref_obs = arms["alone_fp64"][1]
 
     def obs_err(obs):
         out = {}
         for k in ("plaq_re", "plaq_im", "un", "q_re", "q_im"):
-            d = [abs(a[k] - b[k]) for a, b in zip(obs, ref_obs)]
-            out[k] = {"max": float(max(d)), "median": float(np.median(d))}
+            d = [abs(a[k] - b[k]) for a, b in zip(obs, ref_obs) if np.isfinite(a[k]) and np.isfinite(b[k])]
+            out[k] = {"max": float(max(d)) if d else None, "median": float(np.median(d)) if d else None}
         return out
 
     res = {}
     for name, (sec, obs, reps, launches, tuned) in arms.items():
         res[name] = {"value": total / sec, "seconds": round(sec, 4), "gpu_launches": launches,
+                     "nonfinite_chains": sum(1 for o in obs if not np.isfinite(o["un"])),
                      "mean_sweeps_last_step": float(np.mean([r["sweeps"] for r in reps])),
                      "abs_err_vs_alone_fp64": obs_err(obs)}
         if tuned:
@@ -494,7 +511,13 @@ def batch_mode(args):
 # ------------------------------------------------------------------- serving
 SERVE_NAME = ("request trace: Poisson arrivals, L^4 with L = round(exp U[ln 4, ln 24]), beta ~ U[5.6, 6.2], "
               "theta ~ U[0, 2], 100..2000 CL steps (eps 0.005) each followed by adaptive cooling "
-              "(alpha_ad = 1 / D_2, 1..10 sweeps); HBM budget 150 GB")
+              "(alpha_ad = 1 / D_2, 1..10 sweeps), adaptive step size k_ref 12; HBM budget 150 GB")
+
+
+# A request whose unitarity norm climbs past this after a chunk has run away
+# (the norm stays within 1e-3 of 1 on healthy chains and goes to inf within
+# tens of steps once past ~1.01): the server stops it there.
+SERVE_RUNAWAY_UN = 1.1
 
 
 def _serve_once(cl, trace, prec, slots, graphs, tune):
@@ -504,7 +527,8 @@ def _serve_once(cl, trace, prec, slots, graphs, tune):
                             start=cl.CL_START_COLD, tag=r["id"]) for r in trace]
     arrivals = [r["t"] - trace[0]["t"] for r in trace]
     cfg = cl.make_server_config(hbm_budget_bytes=150e9, max_slots=slots, prec=prec, chunk_steps=8,
-                                use_graphs=graphs, cool=cp, blocks_from_autotune=tune)
+                                use_graphs=graphs, cool=cp, blocks_from_autotune=tune, k_ref=BATCH["k_ref"],
+                                runaway_un=SERVE_RUNAWAY_UN)
     with cl.Server(cfg) as srv:
         res = srv.run_trace(reqs, arrivals)
         st = srv.stats()
@@ -525,8 +549,12 @@ def serve_mode(args):
     _serve_once(cl, warm, cl.CL_FP64, 1, False, False)
     sampler = ClockSampler(0)
     sampler.start()
-    arms = {"served_fp32": _serve_once(cl, trace, cl.CL_FP32_STORAGE, args.slots, True, True),
-            "one_at_a_time_fp64": _serve_once(cl, trace, cl.CL_FP64, 1, False, False)}
+    arms = {}
+    _log("serve: served_fp32")
+    arms["served_fp32"] = _serve_once(cl, trace, cl.CL_FP32_STORAGE, args.slots, True, True)
+    _log("serve: one_at_a_time_fp64")
+    arms["one_at_a_time_fp64"] = _serve_once(cl, trace, cl.CL_FP64, 1, False, False)
+    _log("serve: done")
     clocks = sampler.stop()
     ref = arms["one_at_a_time_fp64"][0]
     out = {}
@@ -534,14 +562,20 @@ def serve_mode(args):
         lat = np.array([res[r["id"]]["t_done"] - res[r["id"]]["t_submit"] for r in trace])
         span = max(v["t_done"] for v in res.values()) - min(v["t_submit"] for v in res.values())
         errs = {}
+        both = [i for i in res if res[i]["status"] == cl.CL_OK and ref[i]["status"] == cl.CL_OK]
         for k in ("plaq_re", "un", "q_re"):
-            d = np.array([abs(res[i]["obs"][k] - ref[i]["obs"][k]) for i in res])
-            errs[k] = {"max": float(d.max()), "median": float(np.median(d))}
+            d = np.array([abs(res[i]["obs"][k] - ref[i]["obs"][k]) for i in both])
+            errs[k] = {"max": float(d.max()) if d.size else None,
+                       "median": float(np.median(d)) if d.size else None}
+        sites = {r["id"]: workloads.sites(r) for r in trace}
+        done_work = sum(sites[i] * res[i]["n_steps"] for i in res)  # site-steps actually run
         out[name] = {"p50_s": float(np.percentile(lat, 50)), "p99_s": float(np.percentile(lat, 99)),
-                     "mean_s": float(lat.mean()), "makespan_s": span, "value": work / span,
+                     "mean_s": float(lat.mean()), "makespan_s": span, "value": done_work / span,
                      "requests_per_s": len(trace) / span, "peak_active": st["peak_active"],
                      "peak_bytes": st["peak_bytes"],
-                     "nonfinite": sum(1 for v in res.values() if v["status"] != cl.CL_OK),
+                     "runaway": sum(1 for v in res.values() if v["status"] == cl.CL_ERR_RUNAWAY),
+                     "nonfinite": sum(1 for v in res.values() if v["status"] == cl.CL_ERR_NONFINITE),
+                     "steps_run": int(sum(v["n_steps"] for v in res.values())),
                      "abs_err_vs_one_at_a_time_fp64": errs}
     a, b = out["served_fp32"], out["one_at_a_time_fp64"]
     line = {"metric": "served CL+cooling site-updates/s; p50/p99 latency", "unit": UNIT,

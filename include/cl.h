@@ -224,6 +224,39 @@ cl_status cl_batch_run(cl_batch* batch, int n_steps);
 cl_status cl_batch_synchronize(cl_batch* batch);
 void cl_batch_free(cl_batch* batch);
 
+/* ------------------------------------------------------ SU(2) Polyakov chain
+ * The model of Sec. 3-4 (eq. "eq:s"): S = -(beta/2) Tr(U_1 U_2 ... U_N) with
+ * complex beta and links in SL(2,C); many independent chains of the same
+ * length N advanced together (one CTA per chain, the chain kept in shared
+ * memory for up to 256 steps per launch).  The one-link model it reduces to
+ * has <(1/2) Tr(U_1 ... U_N)> = I_2(beta) / I_1(beta).
+ * Links: host arrays [chain][k][2][2] complex as {re,im} doubles (8 per link).
+ * CL step: U_k <- exp(i sigma_a (eps K_a + sqrt(eps) eta_a)) U_k, K_a = -D_a S,
+ * eta_a = sqrt(2) * normal (Philox key = the chain's seed, counter
+ * (k, step, 3 << 8, j)), then U_k / det(U_k)^(1/2).  Cooling: f_ak =
+ * 2 Tr[sigma_a (U_k U_k^+ - U_{k-1}^+ U_{k-1})], Omega_k = exp(-eps alpha_ad
+ * f_ak sigma_a), U_k <- Omega_k U_k Omega_{k+1}^{-1}, with the stop rule of
+ * cl_cool (D_1 = (1/2)<Tr U U^+>, D_2 = <|f_ak|>).
+ * cl_pchain_create: beta [n_chains][2] (re, im), seeds [n_chains]; start U = 1
+ *   transformed by Omega_k = exp(i w_a sigma_a), w_a = i gauge_sigma g_a
+ *   (Philox stream 4, counter (k, 0, 4 << 8, j)).  1 <= n_links <= 1024,
+ *   1 <= n_chains <= 65535.
+ * cl_pchain_run: n_steps of [CL step (eps), cooling with cp (NULL: none)];
+ *   with obs_every > 0, after every obs_every-th step of this call one record
+ *   per chain is written to obs_out[record][chain][5]: (1/2) Tr(U_1...U_N)
+ *   re, im; unitarity norm (1/N) sum (1/2) Tr U U^+; max |det U - 1|; sweeps.
+ *   Waits for the stream at the end.
+ * Errors: CL_ERR_INVALID, CL_ERR_OOM, CL_ERR_CUDA. */
+typedef struct cl_pchain cl_pchain;
+cl_status cl_pchain_create(int n_chains, int n_links, const double* beta, const uint64_t* seeds,
+                           double gauge_sigma, void* cuda_stream, cl_pchain** out);
+cl_status cl_pchain_run(cl_pchain* chains, int n_steps, double eps, const cl_cool_params* cp,
+                        int obs_every, double* obs_out);
+cl_status cl_pchain_get_links(cl_pchain* chains, double* host);
+cl_status cl_pchain_set_links(cl_pchain* chains, const double* host);
+cl_status cl_pchain_get_step(const cl_pchain* chains, uint64_t* step);
+void cl_pchain_free(cl_pchain* chains);
+
 /* ------------------------------------------------------------------ serving
  * A request server: complex-Langevin trajectories (one chain each) admitted
  * as they arrive and advanced concurrently on one GPU.  Every resident chain
@@ -259,19 +292,23 @@ typedef struct {
   int cool_enabled;         /* 1: each step is followed by cooling with `cool` */
   cl_cool_params cool;      /* its eps is replaced by the request's eps */
   int blocks_from_autotune; /* 1: tune block sizes per lattice shape (cached) */
+  double k_ref;             /* > 0: adaptive step size of every chain (cl_set_adaptive_step) */
+  double runaway_un;        /* > 0 (with cooling): a chain whose unitarity norm after a
+                               chunk's last cooling call exceeds this, or whose links
+                               are non-finite, is stopped there with CL_ERR_RUNAWAY */
 } cl_server_config;
 
 typedef struct {
   int64_t tag;
-  cl_status status;          /* CL_OK or CL_ERR_NONFINITE */
-  int n_steps;
+  cl_status status;          /* CL_OK, CL_ERR_RUNAWAY (stopped early) or CL_ERR_NONFINITE */
+  int n_steps;               /* steps run (fewer than requested after a runaway) */
   cl_obs obs;                /* observables after the last step */
   cl_cool_report last_cool;  /* report of the last step's cooling */
   double t_submit, t_admit, t_done;  /* server clock, seconds */
 } cl_result;
 
 typedef struct {
-  int64_t submitted, admitted, completed;
+  int64_t submitted, admitted, completed, runaways;
   int active, queued, pooled, peak_active;
   uint64_t bytes_in_use, peak_bytes;
 } cl_server_stats;

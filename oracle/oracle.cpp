@@ -144,7 +144,9 @@ Mat inverse(const Mat& a) {
 Mat expm(const Mat& a) {
   int s = 0;
   double nrm = norm1(a);
-  while (nrm > 0.5) {
+  // (s < 1100 only stops the halving of an infinite norm; every finite
+  // double is below 2^1024 and needs fewer halvings)
+  while (nrm > 0.5 && s < 1100) {
     nrm *= 0.5;
     ++s;
   }

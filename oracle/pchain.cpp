@@ -103,7 +103,7 @@ M2 pauli(int a) {
 M2 expm(const M2& a) {
   double n = normF(a);
   int sq = 0;
-  while (n > 0.5) {
+  while (n > 0.5 && sq < 1100) {  // the bound only stops an infinite norm
     n *= 0.5;
     ++sq;
   }

@@ -67,7 +67,8 @@ class cl_server_config(ctypes.Structure):
     _fields_ = [("hbm_budget_bytes", ctypes.c_double), ("max_slots", ctypes.c_int),
                 ("prec", ctypes.c_int), ("chunk_steps", ctypes.c_int), ("use_graphs", ctypes.c_int),
                 ("cool_enabled", ctypes.c_int), ("cool", cl_cool_params),
-                ("blocks_from_autotune", ctypes.c_int)]
+                ("blocks_from_autotune", ctypes.c_int), ("k_ref", ctypes.c_double),
+                ("runaway_un", ctypes.c_double)]
 
 
 class cl_result(ctypes.Structure):
@@ -83,6 +84,7 @@ class cl_result(ctypes.Structure):
 
 class cl_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("admitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("runaways", ctypes.c_int64),
                 ("active", ctypes.c_int), ("queued", ctypes.c_int), ("pooled", ctypes.c_int),
                 ("peak_active", ctypes.c_int), ("bytes_in_use", ctypes.c_uint64),
                 ("peak_bytes", ctypes.c_uint64)]
@@ -133,6 +135,14 @@ SIGNATURES = {
     "cl_get_blocks": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "cl_autotune": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(cl_cool_params), ctypes.c_int,
                                    ctypes.c_int, ctypes.POINTER(ctypes.c_int), _dp]),
+    "cl_pchain_create": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _dp, ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.c_double, _P, ctypes.POINTER(_P)]),
+    "cl_pchain_run": (ctypes.c_int, [_P, ctypes.c_int, ctypes.c_double, ctypes.POINTER(cl_cool_params),
+                                      ctypes.c_int, _dp]),
+    "cl_pchain_get_links": (ctypes.c_int, [_P, _dp]),
+    "cl_pchain_set_links": (ctypes.c_int, [_P, _dp]),
+    "cl_pchain_get_step": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    "cl_pchain_free": (None, [_P]),
     "cl_stream_create": (ctypes.c_int, [ctypes.POINTER(_P)]),
     "cl_stream_destroy": (ctypes.c_int, [_P]),
     "cl_capture_step": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(cl_cool_params)]),
@@ -270,10 +280,10 @@ def make_request(L, beta, theta, eps, n_steps, seed, start=CL_START_COLD, gauge_
 
 
 def make_server_config(hbm_budget_bytes=150e9, max_slots=64, prec=CL_FP32_STORAGE, chunk_steps=8,
-                       use_graphs=True, cool=None, blocks_from_autotune=True):
+                       use_graphs=True, cool=None, blocks_from_autotune=True, k_ref=0.0, runaway_un=0.0):
     return cl_server_config(hbm_budget_bytes, max_slots, prec, chunk_steps, int(use_graphs),
                             int(cool is not None), cool if cool is not None else cl_cool_params(),
-                            int(blocks_from_autotune))
+                            int(blocks_from_autotune), k_ref, runaway_un)
 
 
 def cl_server_create(cfg):
@@ -489,6 +499,67 @@ def make_params(L, beta=6.0, theta=0.0, prec=CL_FP64, seed=1, start=CL_START_COL
 def make_cool(eps, alpha=1.0, mode=CL_D0, n_min=0, n_max=0, tol_rel=1e-3, d_floor=0.0,
               d_guard=1e-12, forced_sweeps=-1):
     return cl_cool_params(eps, alpha, mode, n_min, n_max, tol_rel, d_floor, d_guard, forced_sweeps)
+
+
+class PolyakovChains:
+    """Owning wrapper of cl_pchain: n_chains SU(2) Polyakov chains of n_links
+    links (beta: one complex value or one per chain; seeds: one per chain).
+    Links as complex128 arrays of shape (n_chains, n_links, 2, 2)."""
+
+    def __init__(self, n_chains, n_links, beta, seeds, gauge_sigma=0.0, stream=0):
+        self.n_chains, self.n_links = int(n_chains), int(n_links)
+        b = np.broadcast_to(np.asarray(beta, dtype=np.complex128), (self.n_chains,))
+        bb = np.ascontiguousarray(np.stack([b.real, b.imag], axis=1))
+        sd = np.ascontiguousarray(np.asarray(seeds, dtype=np.uint64))
+        assert sd.shape == (self.n_chains,)
+        self.h = None
+        h = _P()
+        _check(load().cl_pchain_create(self.n_chains, self.n_links, bb.ctypes.data_as(_dp),
+                                       sd.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), gauge_sigma,
+                                       _P(stream or None), ctypes.byref(h)), "cl_pchain_create")
+        self.h = h
+
+    def run(self, n_steps, eps, cp=None, obs_every=0):
+        """Returns records of shape (n_steps // obs_every, n_chains, 5):
+        tr_re, tr_im, un, max_det_dev, sweeps (empty when obs_every = 0)."""
+        nrec = n_steps // obs_every if obs_every > 0 else 0
+        out = np.zeros((max(nrec, 1), self.n_chains, 5))
+        _check(load().cl_pchain_run(self.h, n_steps, eps, ctypes.byref(cp) if cp is not None else None,
+                                    obs_every, out.ctypes.data_as(_dp)), "cl_pchain_run")
+        return out[:nrec]
+
+    def links(self):
+        out = np.zeros((self.n_chains, self.n_links, 2, 2), np.complex128)
+        _check(load().cl_pchain_get_links(self.h, out.ctypes.data_as(_dp)), "cl_pchain_get_links")
+        return out
+
+    def set_links(self, U):
+        U = np.ascontiguousarray(U, dtype=np.complex128)
+        assert U.shape == (self.n_chains, self.n_links, 2, 2)
+        _check(load().cl_pchain_set_links(self.h, U.ctypes.data_as(_dp)), "cl_pchain_set_links")
+
+    @property
+    def step_count(self):
+        v = ctypes.c_uint64()
+        _check(load().cl_pchain_get_step(self.h, ctypes.byref(v)), "cl_pchain_get_step")
+        return v.value
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().cl_pchain_free(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Server:

@@ -42,6 +42,14 @@ __device__ __forceinline__ int taylor_terms(float r) {
   return n;
 }
 
+// Squarings for a norm r > 1: ceil(log2 r), at most 100.  A runaway field
+// can give r = +inf (or a norm beyond float range); the cap keeps the
+// squaring loop bounded, and the result then overflows to inf/NaN, which the
+// observables report as non-finite links.
+__device__ __forceinline__ int scaling_steps(float r) {
+  return (int)ceilf(log2f(fminf(r, 1.0e30f)));
+}
+
 // exp(A) for traceless complex A, FP64.  r_hint >= 0 is the Frobenius norm
 // of A when the caller has it (e.g. from an FP32 copy); < 0 computes it.
 __device__ __forceinline__ void expm_traceless(mat<double>& E, const mat<double>& A, float r_hint = -1.f) {
@@ -58,7 +66,7 @@ __device__ __forceinline__ void expm_traceless(mat<double>& E, const mat<double>
   double sc = 1.0;  // scaling 2^-s
   cx<double> b0 = c0, b1 = c1;  // det and Tr(B^2)/2 of B = A 2^-s
   if (r > 1.0f) {
-    s = (int)ceilf(log2f(r));
+    s = scaling_steps(r);
     sc = ldexp(1.0, -s);
     r = (float)(r * sc);
     const double sc2 = sc * sc;
@@ -150,7 +158,7 @@ __device__ __forceinline__ void expm_hermitian_pair(herm& om, herm& omi, const h
   double sc = 1.0;
   double b1 = c1, b0 = c0;
   if (r > 1.0f) {
-    s = (int)ceilf(log2f(r));
+    s = scaling_steps(r);
     sc = ldexp(1.0, -s);
     r = (float)(r * sc);
     b1 = c1 * sc * sc;

@@ -40,6 +40,9 @@ struct Chain {
   bool final_enqueued = false;
   ObsOut* h_obs = nullptr;     // pinned
   CoolState* h_cs = nullptr;   // pinned
+  CoolState* h_ccs = nullptr;  // pinned [INFLIGHT]: cooling state after each queued chunk
+  int chunk_n[INFLIGHT] = {0, 0};
+  bool runaway = false;        // a chunk ended above the runaway bound: no further chunks
 };
 
 struct Pending {
@@ -56,6 +59,7 @@ void destroy_chain(Chain* c) {
   if (c->final_ev) cudaEventDestroy(c->final_ev);
   if (c->h_obs) cudaFreeHost(c->h_obs);
   if (c->h_cs) cudaFreeHost(c->h_cs);
+  if (c->h_ccs) cudaFreeHost(c->h_ccs);
   if (c->st) cudaStreamDestroy(c->st);
   delete c;
 }
@@ -122,18 +126,24 @@ cl_status enqueue_steps(cl_server* s, Chain* c, int n) {
 
 // Keep INFLIGHT chunks queued; after the last step, the observables and the
 // cooling report are copied to pinned host memory behind final_ev.
+bool watch_runaway(const cl_server* s) { return s->cfg.cool_enabled && s->cfg.runaway_un > 0.0; }
+
 cl_status feed(cl_server* s, Chain* c) {
   while (!c->final_enqueued && c->ev_count < INFLIGHT) {
-    const int k = std::min(s->cfg.chunk_steps, c->req.n_steps - c->enq_steps);
+    const int k = c->runaway ? 0 : std::min(s->cfg.chunk_steps, c->req.n_steps - c->enq_steps);
     if (k > 0) {
       cl_status st = enqueue_steps(s, c, k);
       if (st != CL_OK) return st;
       c->enq_steps += k;
       const int slot = (c->ev_head + c->ev_count) % INFLIGHT;
+      // the cooling state after the chunk: the host checks it for a runaway
+      if (watch_runaway(s))
+        CK(cudaMemcpyAsync(&c->h_ccs[slot], c->lat->cs, sizeof(CoolState), cudaMemcpyDeviceToHost, c->st));
+      c->chunk_n[slot] = k;
       CK(cudaEventRecord(c->ev[slot], c->st));
       c->ev_count++;
     }
-    if (c->enq_steps == c->req.n_steps) {
+    if (c->enq_steps == c->req.n_steps || c->runaway) {
       cl_status st = do_obs(c->lat, c->lat->obs, nullptr);
       if (st != CL_OK) return st;
       CK(cudaMemcpyAsync(c->h_obs, c->lat->obs, sizeof(ObsOut), cudaMemcpyDeviceToHost, c->st));
@@ -157,6 +167,7 @@ cl_status new_chain(cl_server* s, const cl_params& p, Chain** out) {
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->final_ev, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_obs, sizeof(ObsOut));
   if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_cs, sizeof(CoolState));
+  if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_ccs, INFLIGHT * sizeof(CoolState));
   if (st == CL_OK && e != cudaSuccess) st = fail(CL_ERR_CUDA, std::string("server chain: ") + cudaGetErrorString(e));
   if (st == CL_OK) st = cl_init_lattice(&p, (void*)c->st, &c->lat);
   if (st == CL_OK && s->cfg.blocks_from_autotune) {
@@ -218,7 +229,12 @@ cl_status admit(cl_server* s) {
     c->enq_steps = 0;
     c->ev_head = c->ev_count = 0;
     c->final_enqueued = false;
+    c->runaway = false;
     s->queue.pop_front();
+    {
+      cl_status st = cl_set_adaptive_step(c->lat, s->cfg.k_ref);
+      if (st != CL_OK) return st;
+    }
     if (s->cfg.use_graphs) {
       cl_cool_params cp = s->cfg.cool;
       cp.eps = c->req.eps;
@@ -243,6 +259,13 @@ cl_status collect(cl_server* s, int* changes) {
       cudaError_t e = cudaEventQuery(c->ev[c->ev_head]);
       if (e == cudaErrorNotReady) break;
       CK(e);
+      if (watch_runaway(s) && !c->runaway) {
+        const CoolState& cs = c->h_ccs[c->ev_head];
+        if (cs.nonfinite || !(cs.un_after <= s->cfg.runaway_un)) {
+          c->runaway = true;
+          s->stats.runaways++;
+        }
+      }
       c->ev_head = (c->ev_head + 1) % INFLIGHT;
       c->ev_count--;
       (*changes)++;
@@ -264,10 +287,11 @@ cl_status collect(cl_server* s, int* changes) {
     cl_result r;
     std::memset(&r, 0, sizeof(r));
     r.tag = c->req.tag;
-    r.n_steps = c->req.n_steps;
+    r.n_steps = c->enq_steps;
     to_cl_obs(*c->h_obs, &r.obs);
     to_report(*c->h_cs, &r.last_cool);
-    r.status = c->h_obs->nonfinite != 0.0 || c->h_cs->nonfinite ? CL_ERR_NONFINITE : CL_OK;
+    r.status = c->runaway ? CL_ERR_RUNAWAY
+               : (c->h_obs->nonfinite != 0.0 || c->h_cs->nonfinite ? CL_ERR_NONFINITE : CL_OK);
     r.t_submit = c->t_submit;
     r.t_admit = c->t_admit;
     r.t_done = s->now();
@@ -291,6 +315,8 @@ cl_status cl_server_create(const cl_server_config* cfg, cl_server** out) {
   if (cfg->max_slots < 1 || cfg->chunk_steps < 1 || !(cfg->hbm_budget_bytes > 0.0))
     return fail(CL_ERR_INVALID, "bad server configuration");
   if (cfg->prec != CL_FP64 && cfg->prec != CL_FP32_STORAGE) return fail(CL_ERR_INVALID, "bad precision");
+  if (!(cfg->k_ref >= 0.0)) return fail(CL_ERR_INVALID, "k_ref must be >= 0");
+  if (!(cfg->runaway_un >= 0.0)) return fail(CL_ERR_INVALID, "runaway_un must be >= 0");
   if (cfg->cool_enabled) {
     cl_status st = check_cool(&cfg->cool);
     if (st != CL_OK) return st;

@@ -123,3 +123,22 @@ def test_run_trace_returns_every_request():
     assert sorted(r["tag"] for r in res) == list(range(len(reqs)))
     for r in res:
         assert r["t_done"] > r["t_submit"] and r["status"] == cl.CL_OK
+
+
+def test_runaway_requests_stop_early():
+    """A chain whose unitarity norm after a chunk exceeds the bound stops
+    there with CL_ERR_RUNAWAY; its neighbour (theta = 0 from the cold start,
+    which stays in SU(3) to rounding) runs to the end as if alone."""
+    bad = cl.make_request((4, 4, 4, 4), 5.6, 2.0, 0.01, 400, seed=3, start=cl.CL_START_HOT, tag=0)
+    good = cl.make_request((4, 4, 4, 4), 6.0, 0.0, 0.01, 20, seed=4, start=cl.CL_START_COLD, tag=1)
+    cfg = cl.make_server_config(hbm_budget_bytes=1e9, max_slots=4, prec=cl.CL_FP64, chunk_steps=4,
+                                cool=_cool(0.01), runaway_un=1.0 + 1e-9)
+    with cl.Server(cfg) as srv:
+        srv.submit(bad)
+        srv.submit(good)
+        res = {r["tag"]: r for r in srv.drain(2)}
+        st = srv.stats()
+    assert res[0]["status"] == cl.CL_ERR_RUNAWAY and 4 <= res[0]["n_steps"] <= 12
+    assert res[1]["status"] == cl.CL_OK and res[1]["n_steps"] == 20
+    assert res[1]["obs"] == _alone(good, cl.CL_FP64)[0]
+    assert st["runaways"] == 1
