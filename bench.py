@@ -393,14 +393,17 @@ def reference(args):
 
 
 # ----------------------------------------------------------- batched ensemble
-# k_ref: the adaptive Langevin step size (eps_n = eps min(1, k_ref / K_max));
-# typical K_max of these lattices is 17-19, and without the control chains at
-# beta 5.6, theta 2 run away (non-finite links) after ~750 steps.
-BATCH = dict(eps=0.005, alpha=1.0, n_min=1, n_max=10, tol_rel=0.01, k_ref=12.0)
+# Cooling: alpha_ad = alpha / D_2 with alpha = 0.1 (with alpha = 1 the step
+# eps alpha / <|f|> passes the stability bound of the gradient flow once <|f|>
+# drops below ~0.3 and the field explodes), 0..10 sweeps, no sweep within 1e-6
+# of SU(3), stop below 1 % relative progress.  k_ref: the adaptive Langevin
+# step size (eps_n = eps min(1, k_ref / K_max)); typical K_max of these
+# lattices is 17-19, and without it chains at beta 5.6, theta 2 run away.
+BATCH = dict(eps=0.005, alpha=0.1, n_min=0, n_max=10, tol_rel=0.01, d_floor=1e-6, k_ref=12.0)
 BATCH_NAME = ("ensemble of independent chains, L^4 with L uniform in {8, 12, 16}, beta ~ U[5.6, 6.2], "
               "theta in {0, 0.5, 1, 1.5, 2}, cold start; each CL step (eps 0.005) followed by adaptive "
-              "cooling (alpha_ad = 1 / D_2, 1..10 sweeps, stop below 1 % relative progress), adaptive step "
-              "size k_ref 12")
+              "cooling (alpha_ad = 0.1 / D_2, 0..10 sweeps, stop below 1 % relative progress or within "
+              "1e-6 of SU(3)), adaptive step size k_ref 12")
 
 
 def _log(msg):
@@ -416,7 +419,7 @@ def _run_chains(cl, torch, chains, prec, n_steps, batched, tune):
     (each chain on its own stream); otherwise one chain after the other with
     eager calls."""
     cp = cl.make_cool(BATCH["eps"], BATCH["alpha"], cl.CL_D2_MEANABS, n_min=BATCH["n_min"],
-                      n_max=BATCH["n_max"], tol_rel=BATCH["tol_rel"])
+                      n_max=BATCH["n_max"], tol_rel=BATCH["tol_rel"], d_floor=BATCH["d_floor"])
     lats = [cl.Lattice(c["L"], beta=c["beta"], theta=c["theta"], prec=prec, seed=c["seed"],
                        start=cl.CL_START_COLD, own_stream=True) for c in chains]
     for lat in lats:
@@ -511,7 +514,7 @@ def batch_mode(args):
 # ------------------------------------------------------------------- serving
 SERVE_NAME = ("request trace: Poisson arrivals, L^4 with L = round(exp U[ln 4, ln 24]), beta ~ U[5.6, 6.2], "
               "theta ~ U[0, 2], 100..2000 CL steps (eps 0.005) each followed by adaptive cooling "
-              "(alpha_ad = 1 / D_2, 1..10 sweeps), adaptive step size k_ref 12; HBM budget 150 GB")
+              "(alpha_ad = 0.1 / D_2, 0..10 sweeps), adaptive step size k_ref 12; HBM budget 150 GB")
 
 
 # A request whose unitarity norm climbs past this after a chunk has run away
@@ -522,7 +525,7 @@ SERVE_RUNAWAY_UN = 1.1
 
 def _serve_once(cl, trace, prec, slots, graphs, tune):
     cp = cl.make_cool(BATCH["eps"], BATCH["alpha"], cl.CL_D2_MEANABS, n_min=BATCH["n_min"],
-                      n_max=BATCH["n_max"], tol_rel=BATCH["tol_rel"])
+                      n_max=BATCH["n_max"], tol_rel=BATCH["tol_rel"], d_floor=BATCH["d_floor"])
     reqs = [cl.make_request(r["L"], r["beta"], r["theta"], BATCH["eps"], r["steps"], seed=r["seed"],
                             start=cl.CL_START_COLD, tag=r["id"]) for r in trace]
     arrivals = [r["t"] - trace[0]["t"] for r in trace]
@@ -590,6 +593,58 @@ def serve_mode(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------- studies
+def cooling_study_mode(args):
+    """NEXT-2: D_0 / D_1 / D_2 decay of the distance under cooling alone."""
+    from paper_1311_1056_gb300 import build, cl, studies
+
+    build.build()
+    cl.load()
+    out = {"metric": "gauge-cooling decay d(sweeps), D_0 / D_1 / D_2", "chains": {}, "su3_8x4": {}}
+    for n in (1, 10, 100, 1000):
+        for mode, alpha in (("D0", 1.0), ("D1", 1.0), ("D2", 1.0), ("D2", 0.1)):
+            d = studies.chain_cooling(n, mode, alpha=alpha, eps=0.01, sweeps=args.sweeps)
+            out["chains"]["N=%d %s alpha=%g" % (n, mode, alpha)] = studies.summarize(d[:, 0])
+            _log("chain N=%d %s alpha=%g done" % (n, mode, alpha))
+    for mode, alpha in (("D0", 1.0), ("D1", 1.0), ("D2", 1.0), ("D2", 0.1)):
+        d = studies.lattice_cooling((8, 8, 8, 8), mode, alpha=alpha, eps=0.01, sweeps=min(args.sweeps, 1000))
+        out["su3_8x4"]["%s alpha=%g" % (mode, alpha)] = studies.summarize(d)
+        _log("SU(3) %s alpha=%g done" % (mode, alpha))
+    print(json.dumps(out), flush=True)
+
+
+def theta_scan_mode(args):
+    """NEXT-4: plaquette and Q_L against theta_L^2 on 6^4 (Sec. 5)."""
+    import numpy as np
+    from paper_1311_1056_gb300 import build, cl, studies
+
+    build.build()
+    cl.load()
+    t0 = time.perf_counter()
+    res = studies.theta_scan(n_steps=args.scan_steps)
+    sec = time.perf_counter() - t0
+    rows = []
+    for r in res:
+        p, q = r["plaq"], r["q"]
+        keep = slice(len(p) // 4, None)  # drop the first quarter (thermalisation)
+        fin = np.isfinite(p[keep]).all()
+
+        def mean_err(x):
+            x = x[keep]
+            nb = 10
+            b = x[: len(x) // nb * nb].reshape(nb, -1).mean(axis=1)
+            return complex(x.mean()), float(np.abs(b - b.mean()).std() / np.sqrt(nb))
+        pm, pe = mean_err(p)
+        qm, qe = mean_err(q)
+        rows.append({"beta": r["beta"], "theta2": r["theta2"], "finite": bool(fin),
+                     "langevin_time": round(r["langevin_time"], 3),
+                     "plaq": [round(pm.real, 6), round(pm.imag, 6)], "plaq_err": round(pe, 6),
+                     "Q": [round(qm.real, 4), round(qm.imag, 4)], "Q_err": round(qe, 4),
+                     "un_final": float(r["un"][-1])})
+    print(json.dumps({"metric": "theta scan, 6^4 SU(3), CL + adaptive cooling", "steps": args.scan_steps,
+                      "seconds": round(sec, 2), "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -600,9 +655,12 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--mode", choices=["step", "batch", "serve"], default="step",
+    ap.add_argument("--mode", choices=["step", "batch", "serve", "cooling-study", "theta-scan"],
+                    default="step",
                     help="step: the 32^4 single-chain step (default); batch: the chain ensemble; "
-                         "serve: the request trace")
+                         "serve: the request trace; cooling-study, theta-scan: the studies of Sec. 4-5")
+    ap.add_argument("--sweeps", type=int, default=3000)
+    ap.add_argument("--scan-steps", type=int, default=20000)
     ap.add_argument("--requests", type=int, default=100)
     ap.add_argument("--rate", type=float, default=20.0)
     ap.add_argument("--slots", type=int, default=64)
@@ -613,6 +671,10 @@ def main():
         return batch_mode(args)
     if args.mode == "serve":
         return serve_mode(args)
+    if args.mode == "cooling-study":
+        return cooling_study_mode(args)
+    if args.mode == "theta-scan":
+        return theta_scan_mode(args)
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
     if args.impl == "reference":

@@ -1,0 +1,97 @@
+"""Studies of Sec. 3-5 run on the library's kernels.
+
+* cooling_decay: the distance d = UN - 1 of a gauge-transformed unitary
+  configuration under gauge cooling alone, one sweep at a time, for the
+  choices D_0, D_1, D_2 of the adaptive strength alpha_ad = alpha / D
+  (Sec. 4), on SU(2) Polyakov chains of N links (the model of Sec. 3-4) and on
+  an SU(3) lattice.
+* theta_scan: CL with adaptive cooling (alpha_ad = 0.1 / D_2) and the
+  adaptive step size on small SU(3) lattices at several beta and
+  theta_L^2 = 0, +-1, +-4 (Sec. 5), as one batch of chains; returns the
+  series of the plaquette, Q_L and the unitarity norm.
+
+Every number comes from the CUDA kernels through the C-ABI (cl.py).
+"""
+import numpy as np
+
+from . import cl
+
+MODES = {"D0": cl.CL_D0, "D1": cl.CL_D1, "D2": cl.CL_D2_MEANABS}
+
+
+def chain_cooling(n_links, mode, alpha=1.0, eps=0.01, sweeps=2000, sigma=0.1, seed=3, n_chains=1):
+    """d after every sweep (shape (sweeps, n_chains)) for SU(2) chains of
+    n_links links, cooled from U_k = Om_k Om_{k+1}^{-1} (no Langevin update)."""
+    cp = cl.make_cool(eps, alpha, MODES[mode], forced_sweeps=1)
+    with cl.PolyakovChains(n_chains, n_links, 1.0, np.arange(seed, seed + n_chains), gauge_sigma=sigma) as pc:
+        rec = pc.run(sweeps, 0.0, cp, obs_every=1)
+    return rec[:, :, 2] - 1.0
+
+
+def lattice_cooling(L, mode, alpha=1.0, eps=0.01, sweeps=500, sigma=0.1, seed=3, prec=cl.CL_FP64):
+    """d after every sweep for an SU(3) lattice: cold start transformed by a
+    random SL(3,C) gauge transformation (spread sigma), cooled one sweep per call."""
+    cp = cl.make_cool(eps, alpha, MODES[mode], forced_sweeps=1)
+    out = np.zeros(sweeps)
+    with cl.Lattice(L, beta=6.0, prec=prec, seed=seed, start=cl.CL_START_COLD, gauge_sigma=sigma) as lat:
+        for k in range(sweeps):
+            rep = lat.cool(cp)
+            out[k] = rep["un_after"] - 1.0
+    return out
+
+
+def summarize(d, thresholds=(1e-3, 1e-5), marks=(10, 100, 1000)):
+    """Sweeps to reach each threshold (None if never), d at the marks and the
+    log-log slope of d over the last decade of sweeps."""
+    d = np.asarray(d, dtype=np.float64)
+    n = len(d)
+    out = {"first_sweep_below": {}, "d_at": {}}
+    for t in thresholds:
+        idx = np.nonzero(d <= t)[0]
+        out["first_sweep_below"]["%g" % t] = int(idx[0]) + 1 if idx.size else None
+    for m in marks:
+        if m <= n:
+            out["d_at"][str(m)] = float(d[m - 1])
+    lo = max(1, n // 10)
+    x = np.log(np.arange(lo, n) + 1.0)
+    y = np.log(np.maximum(np.abs(d[lo:]), 1e-300))
+    out["loglog_slope_last_decade"] = float(np.polyfit(x, y, 1)[0]) if n - lo > 2 else None
+    out["d_final"] = float(d[-1])
+    return out
+
+
+def theta_scan(L=(6, 6, 6, 6), betas=(5.9, 6.0, 6.1), theta2=(0.0, 1.0, -1.0, 4.0, -4.0), n_steps=4000,
+               eps=0.005, every=20, k_ref=12.0, seed=100, prec=cl.CL_FP64, cool=None):
+    """theta_L = sqrt(theta_L^2): real for theta_L^2 > 0, imaginary for < 0.
+    One batch of len(betas) * len(theta2) chains; every `every` steps the
+    plaquette and Q_L of each chain are recorded.  Returns a list of dicts
+    (beta, theta2, plaquette and Q series)."""
+    cp = cool if cool is not None else cl.make_cool(eps, 0.1, cl.CL_D2_MEANABS, n_min=0, n_max=10,
+                                                    tol_rel=0.01, d_floor=1e-6)
+    specs = [(b, t2) for b in betas for t2 in theta2]
+    lats = []
+    for i, (b, t2) in enumerate(specs):
+        th = np.sqrt(t2) if t2 >= 0 else 1j * np.sqrt(-t2)
+        lat = cl.Lattice(L, beta=b, theta=th, prec=prec, seed=seed + i, start=cl.CL_START_COLD,
+                         own_stream=True)
+        lat.set_adaptive_step(k_ref)
+        lats.append(lat)
+    series = [[] for _ in specs]
+    try:
+        with cl.Batch(lats, eps, [cp] * len(lats)) as b:
+            for _ in range(n_steps // every):
+                b.run(every)
+                b.synchronize()
+                for i, lat in enumerate(lats):
+                    series[i].append(cl.cl_observables(lat.h, check=False))
+        times = [lat.langevin_time()[0] for lat in lats]
+    finally:
+        for lat in lats:
+            lat.close()
+    out = []
+    for (b, t2), ser, t in zip(specs, series, times):
+        out.append({"beta": b, "theta2": t2, "langevin_time": t,
+                    "plaq": np.array([o["plaq_re"] + 1j * o["plaq_im"] for o in ser]),
+                    "q": np.array([o["q_re"] + 1j * o["q_im"] for o in ser]),
+                    "un": np.array([o["un"] for o in ser])})
+    return out

@@ -1,0 +1,91 @@
+"""The studies of Sec. 3-5 on the GPU kernels: gauge cooling of a single
+link converges exponentially (Sec. 3), longer chains converge more slowly
+(Sec. 4, Fig. "Nlink"), the D_2 rule reaches a given distance in fewer sweeps
+than the fixed strength at first (Sec. 4), and in the theta scan the action
+is real for theta_L^2 <= 0 (links stay in SU(3), Im P = 0) but not for real
+theta_L (Sec. 5)."""
+import numpy as np
+import pytest
+import scipy.linalg
+
+import oracle as O
+from paper_1311_1056_gb300 import build, cl, studies
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    cl.load()
+
+
+def test_one_link_cools_exponentially():
+    sig = {a: O.pauli(a) for a in (1, 2, 3)}
+    G = scipy.linalg.expm(0.3 * (0.8 * sig[1] + 0.5j * sig[2] - 0.4 * sig[3]))
+    c = 0.6
+    lam = c + 1j * np.sqrt(1 - c * c)
+    U = G @ np.diag([lam, 1 / lam]) @ np.linalg.inv(G)  # (1/2) Tr U = 0.6: equivalent to SU(2)
+    cp = cl.make_cool(0.01, 1.0, cl.CL_D0, forced_sweeps=1)
+    with cl.PolyakovChains(1, 1, 1.0, [1]) as pc:
+        pc.set_links(U[None, None])
+        d = pc.run(400, 0.0, cp, obs_every=1)[:, 0, 2] - 1.0
+    assert d[0] > 1e-2 and d[-1] < 1e-10
+    # exponential: log d falls linearly (at a constant rate) once d is small,
+    # down to the rounding level
+    idx = np.nonzero((d > 1e-11) & (d < 1e-4))[0]
+    assert len(idx) >= 10 and np.all(np.diff(idx) == 1)
+    rate = -np.diff(np.log(d[idx]))
+    assert rate.std() < 0.05 * rate.mean()
+
+
+def test_longer_chains_cool_more_slowly():
+    reach = {}
+    for n in (10, 100, 1000):
+        d = studies.chain_cooling(n, "D0", alpha=1.0, eps=0.01, sweeps=1500)[:, 0]
+        reach[n] = studies.summarize(d)["first_sweep_below"]["1e-05"]
+        if n == 1000:
+            late = studies.summarize(d)["loglog_slope_last_decade"]
+    assert reach[10] < reach[100] <= reach[1000] + 50
+    assert -2.5 < late < -1.0  # a power law, not the single link's exponential
+
+
+def test_d2_reaches_the_first_decades_sooner():
+    d0 = studies.summarize(studies.chain_cooling(1000, "D0", sweeps=300)[:, 0])
+    d2 = studies.summarize(studies.chain_cooling(1000, "D2", alpha=1.0, sweeps=300)[:, 0])
+    assert d2["first_sweep_below"]["0.001"] < d0["first_sweep_below"]["0.001"]
+
+
+def test_theta_scan_real_and_imaginary_theta():
+    # D_1 cooling with at least one sweep per step keeps real-action chains at SU(3) to
+    # rounding (the unitary directions are unstable under CL and rounding seeds them)
+    cp = cl.make_cool(0.005, 1.0, cl.CL_D1, n_min=1, n_max=10, tol_rel=0.01)
+    res = studies.theta_scan(betas=(6.0,), theta2=(0.0, 1.0, -1.0), n_steps=400, every=20, cool=cp)
+    by = {r["theta2"]: r for r in res}
+    for t2 in (0.0, -1.0):  # real action: the links stay in SU(3)
+        assert np.abs(by[t2]["plaq"].imag).max() < 1e-12
+        assert np.abs(by[t2]["q"].imag).max() < 1e-10
+        assert np.abs(by[t2]["un"] - 1.0).max() < 1e-12
+    assert np.abs(by[1.0]["plaq"].imag).max() > 1e-6  # complex action
+    assert np.abs(by[1.0]["q"].imag).max() > 1e-4
+    for r in res:
+        assert np.isfinite(r["plaq"]).all() and r["langevin_time"] > 0
+
+
+def test_theta_dependence_of_q_at_small_theta():
+    """<q_L> = i theta_L chi_L + O(theta^3) (Sec. 5): on 6^4 at beta = 6.1 over
+    Langevin time ~60, Im Q grows with real theta, Re Q falls with theta =
+    i phi, and both slopes are the same chi within the errors."""
+    res = studies.theta_scan(betas=(6.1,), theta2=(1.0, 4.0, -1.0, -4.0), n_steps=16000, every=20)
+    q = {}
+    for r in res:
+        x = r["q"][len(r["q"]) // 4:]
+        nb = 8
+        b = x[: len(x) // nb * nb].reshape(nb, -1).mean(axis=1)
+        q[r["theta2"]] = (x.mean(), np.abs(b - b.mean()).std() / np.sqrt(nb))
+        assert np.isfinite(x).all()
+    (q1, e1), (q2, e2) = q[1.0], q[4.0]
+    (p1, f1), (p2, f2) = q[-1.0], q[-4.0]
+    assert q1.imag > 3 * e1 and q2.imag > q1.imag
+    assert p1.real < -3 * f1 and p2.real < p1.real
+    assert abs(q1.imag + p1.real) < 4 * np.hypot(e1, f1)  # the same chi for real and imaginary theta
