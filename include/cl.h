@@ -220,6 +220,15 @@ cl_status cl_replay(cl_lattice* lat, int n_steps);
 typedef struct cl_batch cl_batch;
 cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
                           const cl_cool_params* cps, int with_cooling, cl_batch** out);
+/* Add a lattice (with its eps and, for a cooling batch, its cooling
+ * parameters) to / remove one from the batch; the batch graph is captured
+ * again (waits for the batch's pending work).  A removed lattice is the
+ * caller's again and may be stepped on its own.  An empty batch runs nothing.
+ * Errors: CL_ERR_INVALID (already a member / not a member, shared stream,
+ * default stream, bad eps or cp), CL_ERR_CUDA. */
+cl_status cl_batch_add(cl_batch* batch, cl_lattice* lat, double eps, const cl_cool_params* cp);
+cl_status cl_batch_remove(cl_batch* batch, cl_lattice* lat);
+cl_status cl_batch_size(const cl_batch* batch, int* n);
 cl_status cl_batch_run(cl_batch* batch, int n_steps);
 cl_status cl_batch_synchronize(cl_batch* batch);
 void cl_batch_free(cl_batch* batch);

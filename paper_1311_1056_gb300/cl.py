@@ -151,6 +151,9 @@ SIGNATURES = {
                                        ctypes.POINTER(cl_cool_params), ctypes.c_int,
                                        ctypes.POINTER(_P)]),
     "cl_batch_run": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cl_batch_add": (ctypes.c_int, [_P, _P, ctypes.c_double, ctypes.POINTER(cl_cool_params)]),
+    "cl_batch_remove": (ctypes.c_int, [_P, _P]),
+    "cl_batch_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "cl_batch_synchronize": (ctypes.c_int, [_P]),
     "cl_batch_free": (None, [_P]),
     "cl_reset_lattice": (ctypes.c_int, [_P, ctypes.POINTER(cl_params)]),
@@ -358,6 +361,20 @@ def cl_batch_create(lats, eps, cps=None):
 
 def cl_batch_run(batch, n_steps):
     _check(load().cl_batch_run(batch, n_steps), "cl_batch_run")
+
+
+def cl_batch_add(batch, lat, eps, cp=None):
+    _check(load().cl_batch_add(batch, lat, eps, ctypes.byref(cp) if cp is not None else None), "cl_batch_add")
+
+
+def cl_batch_remove(batch, lat):
+    _check(load().cl_batch_remove(batch, lat), "cl_batch_remove")
+
+
+def cl_batch_size(batch):
+    n = ctypes.c_int()
+    _check(load().cl_batch_size(batch, ctypes.byref(n)), "cl_batch_size")
+    return n.value
 
 
 def cl_batch_synchronize(batch):
@@ -625,6 +642,17 @@ class Batch:
 
     def run(self, n_steps=1):
         cl_batch_run(self.h, n_steps)
+
+    def add(self, lat, eps, cp=None):
+        cl_batch_add(self.h, lat.h, eps, cp)
+        self.lats.append(lat)
+
+    def remove(self, lat):
+        cl_batch_remove(self.h, lat.h)
+        self.lats.remove(lat)
+
+    def __len__(self):
+        return cl_batch_size(self.h)
 
     def synchronize(self):
         cl_batch_synchronize(self.h)

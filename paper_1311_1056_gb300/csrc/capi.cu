@@ -652,6 +652,9 @@ cl_status cl_replay(cl_lattice* l, int n_steps) {
 
 struct cl_batch {
   std::vector<cl_lattice*> lats;
+  std::vector<double> eps;
+  std::vector<cl_cool_params> cps;
+  int with_cooling;
   cudaStream_t origin;
   cudaEvent_t fork, done;
   std::vector<cudaEvent_t> joins, ready;
@@ -659,72 +662,70 @@ struct cl_batch {
   std::vector<void*> startU[2];  // per lattice, the link buffer each variant starts from
 };
 
-void cl_batch_free(cl_batch* b) {
-  if (!b) return;
-  if (b->origin) cudaStreamSynchronize(b->origin);
+namespace {
+
+void drop_graphs(cl_batch* b) {
   for (int v = 0; v < 2; ++v)
-    if (b->exec[v]) cudaGraphExecDestroy(b->exec[v]);
+    if (b->exec[v]) {
+      cudaGraphExecDestroy(b->exec[v]);
+      b->exec[v] = nullptr;
+    }
   for (cudaEvent_t e : b->joins)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : b->ready)
     if (e) cudaEventDestroy(e);
-  if (b->fork) cudaEventDestroy(b->fork);
-  if (b->done) cudaEventDestroy(b->done);
-  if (b->origin) cudaStreamDestroy(b->origin);
-  delete b;
+  b->joins.clear();
+  b->ready.clear();
 }
 
-cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
-                          const cl_cool_params* cps, int with_cooling, cl_batch** out) {
-  if (!out || n < 1 || !lats || !eps) return fail(CL_ERR_INVALID, "bad batch arguments");
-  *out = nullptr;
-  for (int i = 0; i < n; ++i) {
-    cl_status s = check_step_args(lats[i], eps[i], with_cooling ? &cps[i] : nullptr);
-    if (s != CL_OK) return s;
-    for (int j = 0; j < i; ++j)
-      if (lats[j] == lats[i] || lats[j]->st == lats[i]->st)
-        return fail(CL_ERR_INVALID, "batch lattices need distinct lattices on distinct streams");
-  }
-  cl_batch* b = new cl_batch();
-  b->lats.assign(lats, lats + n);
-  b->origin = nullptr;
-  b->fork = nullptr;
-  b->done = nullptr;
-  b->exec[0] = b->exec[1] = nullptr;
-  cl_status s = CL_OK;
-  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
-  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+cl_status check_batch_member(const cl_batch* b, const cl_lattice* l, double eps, const cl_cool_params* cp) {
+  cl_status s = check_step_args(l, eps, cp);
+  if (s != CL_OK) return s;
+  for (const cl_lattice* m : b->lats)
+    if (m == l || m->st == l->st)
+      return fail(CL_ERR_INVALID, "batch lattices need distinct lattices on distinct streams");
+  return CL_OK;
+}
+
+// (Re)capture the batch graph: one step of every member, forked from the
+// origin stream to each member's stream and joined back; two variants (the
+// members' link buffers before and after one swap).
+cl_status capture_batch(cl_batch* b) {
+  drop_graphs(b);
+  const int n = (int)b->lats.size();
+  if (n == 0) return CL_OK;
+  cudaError_t e = cudaSuccess;
   b->joins.assign(n, nullptr);
   b->ready.assign(n, nullptr);
   for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->joins[i], cudaEventDisableTiming);
   for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&b->ready[i], cudaEventDisableTiming);
+  // the members' pending work must finish before the capture
+  for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamSynchronize(b->lats[i]->st);
+  if (e != cudaSuccess) return fail(CL_ERR_CUDA, std::string("batch setup: ") + cudaGetErrorString(e));
   std::vector<void*> U0(n), Un0(n);
-  for (int i = 0; i < n; ++i) {
-    U0[i] = lats[i]->U;
-    Un0[i] = lats[i]->Un;
-  }
-  // the lattices' pending work must finish before the first replay
-  for (int i = 0; i < n && e == cudaSuccess; ++i) e = cudaStreamSynchronize(lats[i]->st);
-  if (e != cudaSuccess) s = fail(CL_ERR_CUDA, std::string("batch setup: ") + cudaGetErrorString(e));
   std::vector<int> timing(n);
   for (int i = 0; i < n; ++i) {
-    timing[i] = lats[i]->timing;
-    lats[i]->timing = 0;
+    U0[i] = b->lats[i]->U;
+    Un0[i] = b->lats[i]->Un;
+    timing[i] = b->lats[i]->timing;
+    b->lats[i]->timing = 0;
   }
+  cl_status s = CL_OK;
   for (int v = 0; v < 2 && s == CL_OK; ++v) {
     std::vector<uint64_t> step0(n);
     std::vector<int64_t> n0(n);
-    b->startU[v].resize(n);
+    b->startU[v].assign(n, nullptr);
     e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) e = cudaEventRecord(b->fork, b->origin);
+    for (int i = 0; i < n; ++i) {
+      step0[i] = b->lats[i]->step;
+      n0[i] = b->lats[i]->launches;
+    }
     for (int i = 0; i < n && e == cudaSuccess && s == CL_OK; ++i) {
-      cl_lattice* l = lats[i];
+      cl_lattice* l = b->lats[i];
       b->startU[v][i] = l->U;
-      step0[i] = l->step;
-      n0[i] = l->launches;
       e = cudaStreamWaitEvent(l->st, b->fork, 0);
-      if (e == cudaSuccess) s = enqueue_step(l, eps[i], with_cooling ? &cps[i] : nullptr);
+      if (e == cudaSuccess) s = enqueue_step(l, b->eps[i], b->with_cooling ? &b->cps[i] : nullptr);
       l->glaunches = l->launches - n0[i];
       if (e == cudaSuccess && s == CL_OK) e = cudaEventRecord(b->joins[i], l->st);
       if (e == cudaSuccess && s == CL_OK) e = cudaStreamWaitEvent(b->origin, b->joins[i], 0);
@@ -732,10 +733,8 @@ cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
     cudaGraph_t gr = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(b->origin, &gr);
     for (int i = 0; i < n; ++i) {
-      if (i < (int)step0.size()) {
-        lats[i]->step = step0[i];
-        lats[i]->launches = n0[i];
-      }
+      b->lats[i]->step = step0[i];
+      b->lats[i]->launches = n0[i];
     }
     if (s == CL_OK && (e != cudaSuccess || e2 != cudaSuccess))
       s = fail(CL_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : e2));
@@ -745,11 +744,56 @@ cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
     }
     if (gr) cudaGraphDestroy(gr);
   }
+  // each variant swapped the buffers once: after two they are back in place
   for (int i = 0; i < n; ++i) {
-    lats[i]->timing = timing[i];
-    lats[i]->U = U0[i];
-    lats[i]->Un = Un0[i];
+    b->lats[i]->timing = timing[i];
+    b->lats[i]->U = U0[i];
+    b->lats[i]->Un = Un0[i];
   }
+  if (s != CL_OK) drop_graphs(b);
+  return s;
+}
+
+}  // namespace
+
+void cl_batch_free(cl_batch* b) {
+  if (!b) return;
+  if (b->origin) cudaStreamSynchronize(b->origin);
+  drop_graphs(b);
+  if (b->fork) cudaEventDestroy(b->fork);
+  if (b->done) cudaEventDestroy(b->done);
+  if (b->origin) cudaStreamDestroy(b->origin);
+  delete b;
+}
+
+cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
+                          const cl_cool_params* cps, int with_cooling, cl_batch** out) {
+  if (!out || n < 1 || !lats || !eps || (with_cooling && !cps)) return fail(CL_ERR_INVALID, "bad batch arguments");
+  *out = nullptr;
+  cl_batch* b = new cl_batch();
+  b->with_cooling = with_cooling ? 1 : 0;
+  b->origin = nullptr;
+  b->fork = nullptr;
+  b->done = nullptr;
+  b->exec[0] = b->exec[1] = nullptr;
+  for (int i = 0; i < n; ++i) {
+    cl_status s = check_batch_member(b, lats[i], eps[i], with_cooling ? &cps[i] : nullptr);
+    if (s != CL_OK) {
+      delete b;
+      return s;
+    }
+    b->lats.push_back(lats[i]);
+    b->eps.push_back(eps[i]);
+    cl_cool_params cp;
+    std::memset(&cp, 0, sizeof(cp));
+    if (with_cooling) cp = cps[i];
+    b->cps.push_back(cp);
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
+  cl_status s = e == cudaSuccess ? capture_batch(b)
+                                 : fail(CL_ERR_CUDA, std::string("batch setup: ") + cudaGetErrorString(e));
   if (s != CL_OK) {
     cl_batch_free(b);
     return s;
@@ -758,10 +802,51 @@ cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
   return CL_OK;
 }
 
+cl_status cl_batch_add(cl_batch* b, cl_lattice* lat, double eps, const cl_cool_params* cp) {
+  if (!b) return fail(CL_ERR_INVALID, "NULL batch");
+  if (b->with_cooling && !cp) return fail(CL_ERR_INVALID, "this batch cools: cp is needed");
+  cl_status s = check_batch_member(b, lat, eps, b->with_cooling ? cp : nullptr);
+  if (s != CL_OK) return s;
+  CK(cudaStreamSynchronize(b->origin));
+  b->lats.push_back(lat);
+  b->eps.push_back(eps);
+  cl_cool_params c;
+  std::memset(&c, 0, sizeof(c));
+  if (b->with_cooling) c = *cp;
+  b->cps.push_back(c);
+  s = capture_batch(b);
+  if (s != CL_OK) {
+    b->lats.pop_back();
+    b->eps.pop_back();
+    b->cps.pop_back();
+    cl_status s2 = capture_batch(b);
+    (void)s2;
+  }
+  return s;
+}
+
+cl_status cl_batch_remove(cl_batch* b, cl_lattice* lat) {
+  if (!b || !lat) return fail(CL_ERR_INVALID, "NULL argument");
+  size_t i = 0;
+  while (i < b->lats.size() && b->lats[i] != lat) ++i;
+  if (i == b->lats.size()) return fail(CL_ERR_INVALID, "lattice is not in the batch");
+  CK(cudaStreamSynchronize(b->origin));
+  b->lats.erase(b->lats.begin() + i);
+  b->eps.erase(b->eps.begin() + i);
+  b->cps.erase(b->cps.begin() + i);
+  return capture_batch(b);
+}
+
+cl_status cl_batch_size(const cl_batch* b, int* n) {
+  if (!b || !n) return fail(CL_ERR_INVALID, "NULL argument");
+  *n = (int)b->lats.size();
+  return CL_OK;
+}
+
 cl_status cl_batch_run(cl_batch* b, int n_steps) {
   if (!b || n_steps < 0) return fail(CL_ERR_INVALID, "bad arguments");
   const int n = (int)b->lats.size();
-  if (n_steps == 0) return CL_OK;
+  if (n_steps == 0 || n == 0) return CL_OK;
   // order against work already queued on the lattices' own streams
   for (int i = 0; i < n; ++i) {
     CK(cudaEventRecord(b->ready[i], b->lats[i]->st));

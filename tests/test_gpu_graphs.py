@@ -161,3 +161,36 @@ def test_graph_argument_errors():
             cl.cl_batch_create([lat.h, lat.h], 0.01)  # the same lattice twice
         with pytest.raises(cl.CLError):
             lat.capture_step(-1.0)
+
+
+def test_batch_membership_changes():
+    """Chains join and leave a batch between runs; each ends where it would
+    alone after the same number of steps."""
+    chains = _chains()[:3]
+    cp = cl.make_cool(**ADAPT)
+    lats = [_lat(**c) for c in chains]
+    refs = [_lat(**c) for c in chains]
+    try:
+        with cl.Batch(lats[:2], 0.01, [cp, cp]) as b:
+            b.run(2)
+            b.add(lats[2], 0.01, cp)
+            assert len(b) == 3
+            b.run(3)
+            b.remove(lats[0])
+            b.run(2)
+            with pytest.raises(cl.CLError):
+                b.remove(lats[0])  # no longer a member
+            with pytest.raises(cl.CLError):
+                b.add(lats[1], 0.01, cp)  # already a member
+        lats[0].step(0.01, 1)  # stepped on its own after leaving
+        lats[0].cool(cp)
+        for ref, n in zip(refs, (6, 7, 5)):
+            for _ in range(n):
+                ref.step(0.01, 1)
+                ref.cool(cp)
+        for lat, ref in zip(lats, refs):
+            assert lat.step_count == ref.step_count
+            assert np.array_equal(lat.links(), ref.links())
+    finally:
+        for lat in lats + refs:
+            lat.close()
