@@ -186,6 +186,21 @@ cl_status cl_get_blocks(cl_lattice* lat, int* blocks);
 cl_status cl_autotune(cl_lattice* lat, double eps, const cl_cool_params* cp, int reps, int use_cache,
                       int* blocks_out, double* ms_out);
 
+/* Checkpoint / resume.  The whole state of a chain in one host buffer of
+ * cl_state_size bytes: a header (extents, precision, parameters, Philox step
+ * word and Langevin time, last adaptive step size, cooling-rule state,
+ * adaptive-step reference, tuned block sizes) followed by the links as FP64
+ * AoS (layout of cl_get_links; exact for the FP32-storage form too).  The
+ * noise is counter-based, so a lattice loaded from a checkpoint continues bit
+ * for bit as the saved one would have.  cl_load_state needs a lattice of the
+ * same extents and precision; it takes the saved parameters (beta, theta,
+ * seed, ...) over and drops captured step graphs.  Both wait for the
+ * lattice's stream.  Errors: CL_ERR_INVALID (NULL, short buffer, not a
+ * checkpoint, other extents or precision), CL_ERR_CUDA. */
+cl_status cl_state_size(const cl_lattice* lat, size_t* bytes);
+cl_status cl_save_state(cl_lattice* lat, void* host, size_t bytes);
+cl_status cl_load_state(cl_lattice* lat, const void* host, size_t bytes);
+
 /* A non-blocking CUDA stream owned by the caller (for cl_init_lattice when
  * the caller has none of its own); destroy it after the lattices that use it
  * (cl_stream_destroy waits for its work first).  Errors: CL_ERR_INVALID,

@@ -143,6 +143,9 @@ SIGNATURES = {
     "cl_pchain_set_links": (ctypes.c_int, [_P, _dp]),
     "cl_pchain_get_step": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     "cl_pchain_free": (None, [_P]),
+    "cl_state_size": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_size_t)]),
+    "cl_save_state": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_size_t]),
+    "cl_load_state": (ctypes.c_int, [_P, ctypes.c_void_p, ctypes.c_size_t]),
     "cl_stream_create": (ctypes.c_int, [ctypes.POINTER(_P)]),
     "cl_stream_destroy": (ctypes.c_int, [_P]),
     "cl_capture_step": (ctypes.c_int, [_P, ctypes.c_double, ctypes.POINTER(cl_cool_params)]),
@@ -327,6 +330,24 @@ def cl_server_run_trace(srv, reqs, arrivals):
 
 def cl_server_free(srv):
     load().cl_server_free(srv)
+
+
+def cl_state_size(lat):
+    n = ctypes.c_size_t()
+    _check(load().cl_state_size(lat, ctypes.byref(n)), "cl_state_size")
+    return n.value
+
+
+def cl_save_state(lat):
+    """The chain's checkpoint as bytes."""
+    buf = np.zeros(cl_state_size(lat), np.uint8)
+    _check(load().cl_save_state(lat, buf.ctypes.data, buf.size), "cl_save_state")
+    return buf.tobytes()
+
+
+def cl_load_state(lat, data):
+    buf = np.frombuffer(data, np.uint8).copy()
+    _check(load().cl_load_state(lat, buf.ctypes.data, buf.size), "cl_load_state")
 
 
 def cl_stream_create():
@@ -705,6 +726,12 @@ class Lattice:
 
     def langevin_time(self):
         return cl_get_langevin_time(self.h)
+
+    def save_state(self):
+        return cl_save_state(self.h)
+
+    def load_state(self, data):
+        cl_load_state(self.h, data)
 
     def autotune(self, eps, cp, reps=3, use_cache=True, want_table=False):
         return cl_autotune(self.h, eps, cp, reps, use_cache, want_table)

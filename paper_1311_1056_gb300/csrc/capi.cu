@@ -12,6 +12,8 @@
 #include <mutex>
 #include <map>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/cl.h"
 #include "launch.h"
 #include "runtime.h"
@@ -57,9 +59,20 @@ cudaEvent_t take_event(cl_lattice* l) {
 
 // Launch through f(); with timing on, bracket it by two events on the
 // lattice's stream and remember them under `phase`.
+const char* const PHASE_NAMES[CL_NPHASE] = {"clover", "update", "cool_grad", "cool_rule",
+                                            "cool_omega", "cool_apply", "obs", "force"};
+
+// NVTX range around the enqueue of one phase (a profiler shows the phases by
+// name; without one attached the calls cost a few nanoseconds).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+};
+
 template <typename Fn>
 cudaError_t timed(cl_lattice* l, int phase, Fn f, int kernels = 1) {
   l->launches += kernels;
+  NvtxRange r(PHASE_NAMES[phase]);
   if (!l->timing) return f();
   cudaEvent_t a = take_event(l), b = take_event(l);
   if (!a || !b) return cudaErrorMemoryAllocation;
@@ -1031,6 +1044,85 @@ cl_status cl_autotune(cl_lattice* l, double eps, const cl_cool_params* cp, int r
     if (!g_tune_cache) g_tune_cache = new std::map<TuneKey, std::array<int, NTUNE>>();
     (*g_tune_cache)[key] = best;
   }
+  return CL_OK;
+}
+
+// ------------------------------------------------------------- checkpoints
+namespace {
+
+const uint32_t CKPT_MAGIC = 0x4b434c43u;  // "CLCK"
+const uint32_t CKPT_VERSION = 1;
+
+struct CkptHeader {
+  uint32_t magic, version;
+  int32_t L[4];
+  int32_t prec;
+  int32_t blk[NTUNE];
+  uint64_t step;
+  double k_ref;
+  cl_params params;
+  StepDev sd;
+  CoolState cs;
+  uint64_t link_doubles;  // V * 4 * 18
+};
+
+size_t ckpt_bytes(const cl_lattice* l) { return sizeof(CkptHeader) + sizeof(double) * 72 * (size_t)l->g.V; }
+
+}  // namespace
+
+cl_status cl_state_size(const cl_lattice* l, size_t* bytes) {
+  if (!l || !bytes) return fail(CL_ERR_INVALID, "NULL argument");
+  *bytes = ckpt_bytes(l);
+  return CL_OK;
+}
+
+cl_status cl_save_state(cl_lattice* l, void* host, size_t bytes) {
+  if (!l || !host) return fail(CL_ERR_INVALID, "NULL argument");
+  if (bytes < ckpt_bytes(l)) return fail(CL_ERR_INVALID, "buffer smaller than cl_state_size");
+  CkptHeader h;
+  std::memset(&h, 0, sizeof(h));
+  h.magic = CKPT_MAGIC;
+  h.version = CKPT_VERSION;
+  for (int mu = 0; mu < 4; ++mu) h.L[mu] = l->g.L[mu];
+  h.prec = l->prec;
+  for (int f = 0; f < NTUNE; ++f) h.blk[f] = l->g.blk[f];
+  h.step = l->step;
+  h.k_ref = l->k_ref;
+  h.params = l->p;
+  h.link_doubles = 72ull * (uint64_t)l->g.V;
+  CK(cudaMemcpyAsync(&h.sd, l->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, l->st));
+  CK(cudaMemcpyAsync(&h.cs, l->cs, sizeof(CoolState), cudaMemcpyDeviceToHost, l->st));
+  CK(cudaStreamSynchronize(l->st));
+  std::memcpy(host, &h, sizeof(h));
+  return cl_get_links(l, (double*)((char*)host + sizeof(CkptHeader)));
+}
+
+cl_status cl_load_state(cl_lattice* l, const void* host, size_t bytes) {
+  if (!l || !host) return fail(CL_ERR_INVALID, "NULL argument");
+  if (bytes < sizeof(CkptHeader)) return fail(CL_ERR_INVALID, "buffer too small for a checkpoint");
+  CkptHeader h;
+  std::memcpy(&h, host, sizeof(h));
+  if (h.magic != CKPT_MAGIC || h.version != CKPT_VERSION) return fail(CL_ERR_INVALID, "not a checkpoint");
+  for (int mu = 0; mu < 4; ++mu)
+    if (h.L[mu] != l->g.L[mu]) return fail(CL_ERR_INVALID, "checkpoint of other extents");
+  if (h.prec != l->prec) return fail(CL_ERR_INVALID, "checkpoint of the other precision");
+  if (h.link_doubles != 72ull * (uint64_t)l->g.V || bytes < ckpt_bytes(l))
+    return fail(CL_ERR_INVALID, "truncated checkpoint");
+  CK(cudaStreamSynchronize(l->st));
+  for (int v = 0; v < 2; ++v)
+    if (l->gexec[v]) {  // the captured steps carry the old parameters
+      cudaGraphExecDestroy(l->gexec[v]);
+      l->gexec[v] = nullptr;
+    }
+  l->p = h.params;
+  l->k_ref = h.k_ref;
+  for (int f = 0; f < NTUNE; ++f) l->g.blk[f] = h.blk[f];
+  l->step = h.step;
+  cl_status s = cl_set_links(l, (const double*)((const char*)host + sizeof(CkptHeader)));
+  if (s != CL_OK) return s;
+  CK(cudaMemcpyAsync(l->sd, &h.sd, sizeof(StepDev), cudaMemcpyHostToDevice, l->st));
+  CK(cudaMemcpyAsync(l->cs, &h.cs, sizeof(CoolState), cudaMemcpyHostToDevice, l->st));
+  CK(cudaStreamSynchronize(l->st));
   return CL_OK;
 }
 
