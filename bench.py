@@ -666,6 +666,18 @@ def theta_scan_mode(args):
                       "seconds": round(sec, 2), "rows": rows}), flush=True)
 
 
+def precision_mode(args):
+    """The FP32-storage form against the FP64 form, every observable."""
+    from paper_1311_1056_gb300 import build, cl, studies
+
+    build.build()
+    cl.load()
+    L = tuple(args.L) if args.L else WORKLOAD["L"]
+    tab = studies.precision_table(L=L, checkpoints=(1, 10, 100))
+    print(json.dumps({"metric": "FP32-storage error vs FP64 on identical noise", "workload": WORKLOAD_NAME,
+                      "lattice": list(L), "table": {str(k): v for k, v in tab.items()}}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -676,7 +688,7 @@ def main():
     ap.add_argument("--no-fp32", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--mode", choices=["step", "batch", "serve", "cooling-study", "theta-scan"],
+    ap.add_argument("--mode", choices=["step", "batch", "serve", "cooling-study", "theta-scan", "precision"],
                     default="step",
                     help="step: the 32^4 single-chain step (default); batch: the chain ensemble; "
                          "serve: the request trace; cooling-study, theta-scan: the studies of Sec. 4-5")
@@ -696,6 +708,8 @@ def main():
         return cooling_study_mode(args)
     if args.mode == "theta-scan":
         return theta_scan_mode(args)
+    if args.mode == "precision":
+        return precision_mode(args)
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
     if args.impl == "reference":

@@ -57,17 +57,22 @@ __device__ __forceinline__ void normals_f64(double* g, uint64_t seed, uint32_t s
   }
 }
 
-// The same numbers to float precision, with no FP64 instruction: the uniforms
-// keep the top 24 bits of the first word of each pair, u = (k + 1/2) 2^-24,
-// which agrees with the 52-bit uniform to float rounding.  Used by the
-// FP32-storage form, whose links carry FP32 precision anyway.
+// The same numbers to float precision, with no FP64 instruction.  The radius
+// uniform is the 52-bit one, (k_hi 2^26 + k_lo + 1/2) 2^-52, summed in float:
+// it keeps float's relative precision down to the smallest u1, where the
+// logarithm is steep (a 24-bit grid u = (k + 1/2) 2^-24 would be off by a
+// relative 2^-24 / u1 there, ~1 % for the rare u1 ~ 1e-5 of the tail).  The
+// angle uniform needs absolute precision only: u2 = (k + 1/2) 2^-24 from the
+// top 24 bits of its first word.  Used by the FP32-storage form, whose links
+// carry FP32 precision anyway.
 template <int NP>
 __device__ __forceinline__ void normals_f32(float* g, uint64_t seed, uint32_t step, uint32_t site,
                                             uint32_t slot, uint32_t stream) {
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
     uint4 w = philox_words(seed, step, site, slot, stream, (uint32_t)j);
-    float u1 = ((float)(w.x >> 8) + 0.5f) * 5.9604644775390625e-8f;
+    float u1 = fmaf((float)(w.x >> 6), 1.490116119384765625e-8f,            // 2^-26
+                    ((float)(w.y >> 6) + 0.5f) * 2.220446049250313080847e-16f);  // 2^-52
     float u2 = ((float)(w.z >> 8) + 0.5f) * 5.9604644775390625e-8f;
     float rad = sqrtf(-2.0f * logf(u1));
     float s, c;

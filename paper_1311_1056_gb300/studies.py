@@ -5,6 +5,9 @@
   choices D_0, D_1, D_2 of the adaptive strength alpha_ad = alpha / D
   (Sec. 4), on SU(2) Polyakov chains of N links (the model of Sec. 3-4) and on
   an SU(3) lattice.
+* precision_table: the FP32-storage form against the FP64 form on identical
+  noise (same start, seed and step counter): max |U32 - U64| over the links
+  and the error of every observable after a number of steps.
 * theta_scan: CL with adaptive cooling (alpha_ad = 0.1 / D_2) and the
   adaptive step size on small SU(3) lattices at several beta and
   theta_L^2 = 0, +-1, +-4 (Sec. 5), as one batch of chains; returns the
@@ -94,4 +97,34 @@ def theta_scan(L=(6, 6, 6, 6), betas=(5.9, 6.0, 6.1), theta2=(0.0, 1.0, -1.0, 4.
                     "plaq": np.array([o["plaq_re"] + 1j * o["plaq_im"] for o in ser]),
                     "q": np.array([o["q_re"] + 1j * o["q_im"] for o in ser]),
                     "un": np.array([o["un"] for o in ser])})
+    return out
+
+
+OBS_KEYS = ("plaq_re", "plaq_im", "un", "q_re", "q_im", "sw_re", "sw_im", "s_re", "s_im", "max_det_dev")
+
+
+def precision_table(L=(32, 32, 32, 32), beta=6.2, theta=1.0, eps=0.005, sweeps=10, checkpoints=(1, 10, 100),
+                    seed=1):
+    """FP32-storage vs FP64 on the same workload as the throughput bench
+    (Haar start, fixed count of D_1 sweeps).  Returns {n_steps: {"links":
+    max abs difference, observable: (fp64 value, abs difference, relative
+    difference)}}."""
+    cp = cl.make_cool(eps, 1.0, cl.CL_D1, forced_sweeps=sweeps)
+    out = {}
+    with cl.Lattice(L, beta=beta, theta=theta, prec=cl.CL_FP64, seed=seed, start=cl.CL_START_HOT) as a, \
+            cl.Lattice(L, beta=beta, theta=theta, prec=cl.CL_FP32_STORAGE, seed=seed,
+                       start=cl.CL_START_HOT) as b:
+        done = 0
+        for n in sorted(checkpoints):
+            for lat in (a, b):
+                for _ in range(n - done):
+                    lat.step(eps, 1)
+                    lat.cool(cp, want_report=False)
+            done = n
+            oa, ob = a.observables(), b.observables()
+            row = {"links": float(np.abs(a.links() - b.links()).max())}
+            for k in OBS_KEYS:
+                d = abs(ob[k] - oa[k])
+                row[k] = (oa[k], d, d / abs(oa[k]) if oa[k] != 0 else None)
+            out[n] = row
     return out
