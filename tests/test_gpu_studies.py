@@ -50,6 +50,15 @@ def test_longer_chains_cool_more_slowly():
     assert -2.5 < late < -1.0  # a power law, not the single link's exponential
 
 
+def test_long_chain_decay_is_a_power_law_near_three_halves():
+    """Sec. 4: on a long chain the distance decays asymptotically like
+    t^(-3/2) under the fixed-strength cooling (N = 1000, sweeps 500-5000)."""
+    d = studies.chain_cooling(1000, "D0", alpha=1.0, eps=0.01, sweeps=5000)[:, 0]
+    x = np.log(np.arange(500, 5000) + 1.0)
+    slope = np.polyfit(x, np.log(d[500:5000]), 1)[0]
+    assert -1.75 < slope < -1.25, slope
+
+
 def test_d2_reaches_the_first_decades_sooner():
     d0 = studies.summarize(studies.chain_cooling(1000, "D0", sweeps=300)[:, 0])
     d2 = studies.summarize(studies.chain_cooling(1000, "D2", alpha=1.0, sweeps=300)[:, 0])
