@@ -144,6 +144,27 @@ struct PcArgs {
   double* obs;            // [record][chain][5]
 };
 
+// An array of n 2x2 complex matrices in shared memory, component-major
+// (entry q of matrix k at p[q n + k]): consecutive threads touch consecutive
+// doubles, so a warp's access is free of bank conflicts.
+struct SM2 {
+  double* p;
+  int n;
+  __device__ __forceinline__ M2 get(int k) const {
+    M2 r;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r.e[q] = C{p[(2 * q) * n + k], p[(2 * q + 1) * n + k]};
+    return r;
+  }
+  __device__ __forceinline__ void set(int k, const M2& m) const {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      p[(2 * q) * n + k] = m.e[q].re;
+      p[(2 * q + 1) * n + k] = m.e[q].im;
+    }
+  }
+};
+
 // Fixed-order sum of three values and max of one over the block; every
 // thread gets the totals.  red holds 32 * 4 doubles.
 __device__ __forceinline__ void block_reduce4(double v[4], double* red) {
@@ -173,22 +194,23 @@ __device__ __forceinline__ void block_reduce4(double v[4], double* red) {
 }
 
 // As[k] = U_0 ... U_k, Bs[k] = U_k ... U_{n-1}.
-__device__ __forceinline__ void scan_products(const M2* Us, M2* As, M2* Bs, int n) {
+__device__ __forceinline__ void scan_products(const SM2& Us, const SM2& As, const SM2& Bs, int n) {
   const int k = threadIdx.x;
   const bool act = k < n;
   if (act) {
-    As[k] = Us[k];
-    Bs[k] = Us[k];
+    const M2 u = Us.get(k);
+    As.set(k, u);
+    Bs.set(k, u);
   }
   __syncthreads();
   for (int off = 1; off < n; off <<= 1) {
     const bool da = act && k >= off, db = act && k + off < n;
     M2 pa, pb;
-    if (da) pa = As[k - off];
-    if (db) pb = Bs[k + off];
+    if (da) pa = As.get(k - off);
+    if (db) pb = Bs.get(k + off);
     __syncthreads();
-    if (da) As[k] = m2mul(pa, As[k]);
-    if (db) Bs[k] = m2mul(Bs[k], pb);
+    if (da) As.set(k, m2mul(pa, As.get(k)));
+    if (db) Bs.set(k, m2mul(Bs.get(k), pb));
     __syncthreads();
   }
 }
@@ -200,16 +222,17 @@ __global__ void __launch_bounds__(MAXT, 1) k_pchain(PcArgs a) {
   extern __shared__ double smem[];
   const int n = a.n, c = blockIdx.x, k = threadIdx.x;
   const bool act = k < n;
-  M2* Us = (M2*)smem;
-  M2* As = Us + n;
-  M2* Bs = As + n;
-  double* red = (double*)(Bs + n);
+  const SM2 Us{smem, n}, As{smem + 8 * n, n}, Bs{smem + 16 * n, n};
+  double* red = smem + 24 * n;
   double2* Ug = a.U + (size_t)c * n * 4;
-  if (act)
+  if (act) {
+    M2 u;
     for (int q = 0; q < 4; ++q) {
       const double2 v = Ug[4 * k + q];
-      Us[k].e[q] = C{v.x, v.y};
+      u.e[q] = C{v.x, v.y};
     }
+    Us.set(k, u);
+  }
   __syncthreads();
   const C beta = C{a.beta[2 * c], a.beta[2 * c + 1]};
   const uint64_t seed = a.seed[c];
@@ -219,7 +242,7 @@ __global__ void __launch_bounds__(MAXT, 1) k_pchain(PcArgs a) {
     scan_products(Us, As, Bs, n);
     // (each thread reads only its own link of Us, so it writes it in place)
     if (act) {
-      const M2 P = k == 0 ? Bs[0] : m2mul(Bs[k], As[k - 1]);
+      const M2 P = k == 0 ? Bs.get(0) : m2mul(Bs.get(k), As.get(k - 1));
       double g[4];
       normals_f64<2>(g, seed, a.step0 + (uint32_t)s, (uint32_t)k, 0u, STREAM_PC_CL);
       const C htr = cscale(cadd(P.e[0], P.e[3]), 0.5);
@@ -236,11 +259,11 @@ __global__ void __launch_bounds__(MAXT, 1) k_pchain(PcArgs a) {
       A.e[1].im += sq * g[0];
       A.e[2].re -= sq * g[1];
       A.e[2].im += sq * g[0];
-      M2 W = m2mul(exp_traceless(A), Us[k]);
+      M2 W = m2mul(exp_traceless(A), Us.get(k));
       const C z = cinv(csqrt_p(m2det(W)));
 #pragma unroll
       for (int q = 0; q < 4; ++q) W.e[q] = cmul(W.e[q], z);
-      Us[k] = W;
+      Us.set(k, W);
     }
     __syncthreads();
     // ---- gauge cooling (the adaptive rule of the SU(3) path, per chain)
@@ -249,8 +272,8 @@ __global__ void __launch_bounds__(MAXT, 1) k_pchain(PcArgs a) {
     for (int it = 0;; ++it) {
       double v[4] = {0.0, 0.0, 0.0, 0.0}, f[3] = {0.0, 0.0, 0.0};
       if (act) {
-        const M2& u = Us[k];
-        const M2& w = Us[k == 0 ? n - 1 : k - 1];
+        const M2 u = Us.get(k);
+        const M2 w = Us.get(k == 0 ? n - 1 : k - 1);
         // G = u u^+ - w^+ w (Hermitian)
         C G00 = C{0.0, 0.0}, G01 = C{0.0, 0.0}, G10 = C{0.0, 0.0}, G11 = C{0.0, 0.0};
         G00 = cfma(u.e[0], cconj(u.e[0]), cfma(u.e[1], cconj(u.e[1]), G00));
@@ -294,10 +317,13 @@ __global__ void __launch_bounds__(MAXT, 1) k_pchain(PcArgs a) {
       if (act) {
         const double ea = -a.ca.eps * alpha_ad;  // the cooling eps, not the Langevin one
         const double h[3] = {ea * f[0], ea * f[1], ea * f[2]};
-        exp_herm_pair(h, As[k], Bs[k]);
+        M2 om, omi;
+        exp_herm_pair(h, om, omi);
+        As.set(k, om);
+        Bs.set(k, omi);
       }
       __syncthreads();
-      if (act) Us[k] = m2mul(m2mul(As[k], Us[k]), Bs[k + 1 == n ? 0 : k + 1]);
+      if (act) Us.set(k, m2mul(m2mul(As.get(k), Us.get(k)), Bs.get(k + 1 == n ? 0 : k + 1)));
       __syncthreads();
       ++sweeps;
       un_prev = un;
@@ -308,14 +334,15 @@ __global__ void __launch_bounds__(MAXT, 1) k_pchain(PcArgs a) {
       scan_products(Us, As, Bs, n);
       double v[4] = {0.0, 0.0, 0.0, 0.0};
       if (act) {
-        const C d = m2det(Us[k]);
+        const C d = m2det(Us.get(k));
         v[3] = hypot(d.re - 1.0, d.im);
       }
       block_reduce4(v, red);
       if (k == 0) {
         double* o = a.obs + ((size_t)(done / a.obs_every - 1) * a.n_chains + c) * 5;
-        o[0] = 0.5 * (As[n - 1].e[0].re + As[n - 1].e[3].re);
-        o[1] = 0.5 * (As[n - 1].e[0].im + As[n - 1].e[3].im);
+        const M2 tot = As.get(n - 1);
+        o[0] = 0.5 * (tot.e[0].re + tot.e[3].re);
+        o[1] = 0.5 * (tot.e[0].im + tot.e[3].im);
         o[2] = un;
         o[3] = v[3];
         o[4] = (double)sweeps;
@@ -323,8 +350,10 @@ __global__ void __launch_bounds__(MAXT, 1) k_pchain(PcArgs a) {
       __syncthreads();
     }
   }
-  if (act)
-    for (int q = 0; q < 4; ++q) Ug[4 * k + q] = make_double2(Us[k].e[q].re, Us[k].e[q].im);
+  if (act) {
+    const M2 u = Us.get(k);
+    for (int q = 0; q < 4; ++q) Ug[4 * k + q] = make_double2(u.e[q].re, u.e[q].im);
+  }
 }
 
 }  // namespace
@@ -352,7 +381,7 @@ __global__ void k_pchain_start(int n, int n_chains, double2* U, const uint64_t* 
   for (int q = 0; q < 4; ++q) o[q] = make_double2(u.e[q].re, u.e[q].im);
 }
 
-size_t pchain_smem(int n) { return (size_t)3 * n * sizeof(M2) + 4 * 32 * sizeof(double); }
+size_t pchain_smem(int n) { return (size_t)24 * n * sizeof(double) + 4 * 32 * sizeof(double); }
 
 }  // namespace
 }  // namespace clgc
