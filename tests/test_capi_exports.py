@@ -71,3 +71,16 @@ def test_struct_layouts_match_the_header(tmp_path):
         assert int(got[s]) == ctypes.sizeof(T), s
         for f, _ in T._fields_:
             assert int(got["%s.%s" % (s, f)]) == getattr(T, f).offset, (s, f)
+
+
+def test_oversized_lattice_is_rejected_before_any_device_work():
+    """The largest lattice accepted has V * 54 <= 2^31 - 1 sites (79^4 =
+    38.9 M); 80^4 is refused with CL_ERR_INVALID before any CUDA call."""
+    from paper_1311_1056_gb300 import cl
+    with pytest.raises(cl.CLError) as e:
+        cl.cl_init_lattice(cl.make_params((80, 80, 80, 80)))
+    assert e.value.status == cl.CL_ERR_INVALID and "too large" in cl.cl_last_error()
+    p = cl.make_params((80, 80, 80, 80))
+    with pytest.raises(cl.CLError):
+        cl.cl_lattice_bytes(p)
+    assert cl.cl_lattice_bytes(cl.make_params((79, 79, 79, 79), prec=cl.CL_FP32_STORAGE)) > 150e9
