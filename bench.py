@@ -94,7 +94,8 @@ def measured_peaks():
 
 # The sources of the kernels the bench launches (their launch shapes included);
 # the host runtime, the server and the chain kernel do not change them.
-KERNEL_SOURCES = ("expm.cuh", "k_update.cuh", "k_update_f32.cu", "k_update_f64.cu", "kernels.cu", "launch.h",
+KERNEL_SOURCES = ("df64.cuh", "expm.cuh", "k_update.cuh", "k_update_df64.cu", "k_update_f32.cu", "k_update_f64.cu",
+                  "kernels.cu", "launch.h",
                   "lattice.cuh", "philox.cuh", "su3.cuh")
 
 
@@ -219,7 +220,7 @@ def dist_setup():
 
 def run_form(cl, torch, prec_name, args, rank, stream):
     w = WORKLOAD
-    prec = cl.CL_FP64 if prec_name == "fp64" else cl.CL_FP32_STORAGE
+    prec = {"fp64": cl.CL_FP64, "fp32": cl.CL_FP32_STORAGE, "df64": cl.CL_DF64}[prec_name]
     L = tuple(args.L) if args.L else w["L"]
     V = L[0] * L[1] * L[2] * L[3]
     lat = cl.Lattice(L, beta=w["beta"], theta=w["theta"], prec=prec, seed=w["seed"] + rank,
@@ -292,7 +293,9 @@ def e2e_measure(cl, torch, lat, V, one_step, steps):
 
 def roofline_of(prec_name, V, phases, sm_max_mhz, theta_on=True):
     """Roofline of the kernel that dominates the step (a single-kernel phase)."""
-    fm, pipe = flop_model(prec_name, theta_on)
+    # DF64 runs the FP64 form's algorithm with double-float link algebra: its
+    # work is counted in FP64-equivalent flops against the FP64 peak
+    fm, pipe = flop_model("fp64" if prec_name == "df64" else prec_name, theta_on)
     single = {k: v for k, v in phases.items() if k in ("force", "update", "cool_grad", "cool_omega",
                                                        "cool_apply")}
     dom = max(single, key=lambda k: single[k][0])
@@ -306,7 +309,12 @@ def roofline_of(prec_name, V, phases, sm_max_mhz, theta_on=True):
         peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
         src = "152 SMs x 128 FP32 FMA/clk x %d MHz" % sm_max_mhz
     ach = flops / (per * 1e-3) / 1e12
-    return {"kernel": dom, "bound": "alu", "pipe": pipe[dom], "achieved": round(ach, 4),
+    if prec_name == "df64":
+        src = ("FP64-equivalent flops (double-float on the FP32 pipe) against the FP64 peak, "
+               "152 SMs x 2 FP64 FMA/clk x %d MHz" % sm_max_mhz)
+        peak = fp64_peak_tflops(sm_max_mhz)
+    return {"kernel": dom, "bound": "alu", "pipe": "fp32 (double-float)" if prec_name == "df64" else pipe[dom],
+            "achieved": round(ach, 4),
             "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
             "traffic": dram_traffic(dom, prec_name), "flops_per_launch": flops,
             "avg_launch_ms": round(per, 4), "launches": n, "peak_source": src}
@@ -372,6 +380,18 @@ def native(args):
             "hbm_frac": round(ALG_BYTES["fp32"] * V32 / (ms32 * 1e-3) / 1e9 / peaks["hbm_gbs"], 5)
             if peaks.get("hbm_gbs") else None,
             "observables_after": {k: obs32[k] for k in ("plaq_re", "un", "q_re", "q_im")}}}
+    if not args.no_df64:
+        latd, Vd, msd, ld, phd, obsd, _ = run_form(cl, torch, "df64", args, rank, stream)
+        latd.close()
+        msd = rank_max(msd, "cuda")
+        result.setdefault("forms", {})["df64"] = {
+            "value": job_value(Vd, msd, ws), "ms_per_step": msd, "gpu_launches": ld,
+            "dtype": "df64 links (hi + lo floats) and link algebra on the FP32 pipe; f64 exp/noise/"
+                     "reprojection/reductions",
+            "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phd.items()},
+            "roofline": roofline_of("df64", Vd, phd, sm_max),
+            "observables_after": {k: obsd[k] for k in ("plaq_re", "un", "q_re", "q_im")},
+            "abs_diff_vs_fp64_after": {k: abs(obsd[k] - obs[k]) for k in ("plaq_re", "un", "q_re", "q_im")}}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         result["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
     if ws > 1:
@@ -686,6 +706,7 @@ def main():
     ap.add_argument("--impl", choices=["native", "reference"], default="native")
     ap.add_argument("--L", type=int, nargs=4, default=None, help="override the lattice (testing)")
     ap.add_argument("--no-fp32", action="store_true")
+    ap.add_argument("--no-df64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--mode", choices=["step", "batch", "serve", "cooling-study", "theta-scan", "precision"],

@@ -31,7 +31,13 @@
  *  - Precision (cl_precision): CL_FP64 keeps links and all arithmetic in
  *    FP64.  CL_FP32_STORAGE stores and multiplies links in FP32 and keeps in
  *    FP64 the matrix exponentials of the Langevin and cooling updates, the
- *    det U = 1 re-projection and every global reduction.
+ *    det U = 1 re-projection and every global reduction.  CL_DF64 stores
+ *    links as double-float pairs (hi + lo floats, ~48 significant bits) and
+ *    does the link algebra (products, inverses, plaquettes, clover, drift,
+ *    cooling transformations) in double-float arithmetic on the FP32 pipe,
+ *    with the exponentials, the noise, the re-projection and the reductions
+ *    in FP64 as in CL_FP64; its results agree with CL_FP64 to ~1e-14 per
+ *    step.
  *  - Noise: Philox4x32-10 keyed by (seed, step, site, mu), so results do not
  *    depend on launch shape, and a run resumed from cl_get_links /
  *    cl_get_step reproduces the uninterrupted one.
@@ -56,7 +62,7 @@ typedef enum {
   CL_ERR_TIMEOUT = 6    /* a bounded device wait gave up */
 } cl_status;
 
-typedef enum { CL_FP64 = 0, CL_FP32_STORAGE = 1 } cl_precision;
+typedef enum { CL_FP64 = 0, CL_FP32_STORAGE = 1, CL_DF64 = 2 } cl_precision;
 typedef enum { CL_START_COLD = 0, CL_START_HOT = 1 } cl_start;
 
 /* Choice of D in alpha_ad = alpha / D (Sec. 4): D_0 = 1; D_1 = (1/3)<Tr U U^+>
@@ -189,8 +195,9 @@ cl_status cl_autotune(cl_lattice* lat, double eps, const cl_cool_params* cp, int
 /* Checkpoint / resume.  The whole state of a chain in one host buffer of
  * cl_state_size bytes: a header (extents, precision, parameters, Philox step
  * word and Langevin time, last adaptive step size, cooling-rule state,
- * adaptive-step reference, tuned block sizes) followed by the links as FP64
- * AoS (layout of cl_get_links; exact for the FP32-storage form too).  The
+ * adaptive-step reference, tuned block sizes) followed by the link field in
+ * its device storage form (copied verbatim, so the restore is exact in every
+ * precision; FP64 and DF64 16 B, FP32 storage 8 B per complex entry).  The
  * noise is counter-based, so a lattice loaded from a checkpoint continues bit
  * for bit as the saved one would have.  cl_load_state needs a lattice of the
  * same extents and precision; it takes the saved parameters (beta, theta,

@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libcl.so")
-SOURCES = ["capi.cu", "kernels.cu", "k_update_f64.cu", "k_update_f32.cu", "noalloc.cu", "server.cu", "pchain.cu"]
+SOURCES = ["capi.cu", "kernels.cu", "k_update_f64.cu", "k_update_f32.cu", "k_update_df64.cu", "noalloc.cu", "server.cu", "pchain.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include")]
 

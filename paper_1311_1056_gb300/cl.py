@@ -18,7 +18,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libcl.so")
 
 CL_OK, CL_ERR_INVALID, CL_ERR_OOM, CL_ERR_CUDA, CL_ERR_NONFINITE, CL_ERR_RUNAWAY, CL_ERR_TIMEOUT = range(7)
-CL_FP64, CL_FP32_STORAGE = 0, 1
+CL_FP64, CL_FP32_STORAGE, CL_DF64 = 0, 1, 2
 CL_START_COLD, CL_START_HOT = 0, 1
 CL_D0, CL_D1, CL_D2_MEANABS, CL_D2_RMS = 0, 1, 2, 3
 CL_TUNE_CLOVER, CL_TUNE_FORCE, CL_TUNE_UPDATE, CL_TUNE_OMEGA, CL_TUNE_APPLY = range(5)

@@ -44,7 +44,8 @@ void set_last_error(const std::string& msg) { g_err = msg; }
 
 namespace clrt {
 
-size_t real_size(const cl_lattice* l) { return l->prec == 0 ? 8 : 4; }
+// Internal precision codes equal cl_precision: 0 FP64, 1 FP32 storage, 2 DF64.
+size_t real_size(const cl_lattice* l) { return l->prec == 1 ? 4 : 8; }
 
 cudaEvent_t take_event(cl_lattice* l) {
   if (!l->ev_pool->empty()) {
@@ -122,7 +123,7 @@ cudaError_t do_force(cl_lattice* l, bool th, double sre, double sim) {
     e = timed(l, CL_PHASE_FORCE, [&] {
       return launch_plaq_force(l->prec, th, l->g, l->U, l->Ui, l->Pq, l->Dq, l->F, l->Gq, l->C, l->p.beta,
                                l->st);
-    }, (th && l->prec == 0) ? 2 : 1);
+    }, (th && l->prec != 1) ? 2 : 1);  // FP64 and DF64 split the theta force in two kernels
   return e;
 }
 
@@ -239,7 +240,7 @@ namespace clrt {
 
 // Device bytes of one lattice (the buffers cl_init_lattice allocates).
 size_t lattice_bytes(int V, int prec) {
-  const size_t Vs = (size_t)V, esz = prec == 0 ? 16 : 8, real = prec == 0 ? 8 : 4;
+  const size_t Vs = (size_t)V, esz = prec == 1 ? 8 : 16, real = prec == 1 ? 4 : 8;
   return esz * 9 * Vs * (4 + 4 + 4 + 6 + 6 + 24 + 6 + 6) + sizeof(double) * 8 * Vs + real * 9 * Vs * 2 +
          sizeof(double) * NQ_OBS * (size_t)reduce_blocks(V) + sizeof(CoolState) + sizeof(ObsOut) +
          sizeof(uint32_t);
@@ -277,7 +278,7 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
     V *= params->L[mu];
     if (V * 6 * 9 > INT_MAX) return fail(CL_ERR_INVALID, "lattice too large");
   }
-  if (params->prec != CL_FP64 && params->prec != CL_FP32_STORAGE)
+  if (params->prec != CL_FP64 && params->prec != CL_FP32_STORAGE && params->prec != CL_DF64)
     return fail(CL_ERR_INVALID, "bad precision");
   if (params->start != CL_START_COLD && params->start != CL_START_HOT)
     return fail(CL_ERR_INVALID, "bad start");
@@ -286,8 +287,8 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
   l->p = *params;
   for (int mu = 0; mu < 4; ++mu) l->g.L[mu] = params->L[mu];
   l->g.V = (int)V;
-  l->prec = params->prec == CL_FP64 ? 0 : 1;
-  l->esz = l->prec == 0 ? 16 : 8;
+  l->prec = (int)params->prec;
+  l->esz = l->prec == 1 ? 8 : 16;
   l->st = (cudaStream_t)cuda_stream;
   l->ev_pool = new std::vector<cudaEvent_t>();
   l->ev_pending = new std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>>();
@@ -355,7 +356,9 @@ cl_status cl_lattice_bytes(const cl_params* params, size_t* bytes) {
     V *= params->L[mu];
     if (V * 6 * 9 > INT_MAX) return fail(CL_ERR_INVALID, "lattice too large");
   }
-  *bytes = lattice_bytes((int)V, params->prec == CL_FP64 ? 0 : 1);
+  if (params->prec != CL_FP64 && params->prec != CL_FP32_STORAGE && params->prec != CL_DF64)
+    return fail(CL_ERR_INVALID, "bad precision");
+  *bytes = lattice_bytes((int)V, (int)params->prec);
   return CL_OK;
 }
 
@@ -1051,7 +1054,7 @@ cl_status cl_autotune(cl_lattice* l, double eps, const cl_cool_params* cp, int r
 namespace {
 
 const uint32_t CKPT_MAGIC = 0x4b434c43u;  // "CLCK"
-const uint32_t CKPT_VERSION = 1;
+const uint32_t CKPT_VERSION = 2;
 
 struct CkptHeader {
   uint32_t magic, version;
@@ -1063,10 +1066,11 @@ struct CkptHeader {
   cl_params params;
   StepDev sd;
   CoolState cs;
-  uint64_t link_doubles;  // V * 4 * 18
+  uint64_t link_bytes;  // the link field in its device storage (SoA), copied verbatim
 };
 
-size_t ckpt_bytes(const cl_lattice* l) { return sizeof(CkptHeader) + sizeof(double) * 72 * (size_t)l->g.V; }
+size_t link_field_bytes(const cl_lattice* l) { return l->esz * 36 * (size_t)l->g.V; }
+size_t ckpt_bytes(const cl_lattice* l) { return sizeof(CkptHeader) + link_field_bytes(l); }
 
 }  // namespace
 
@@ -1089,12 +1093,13 @@ cl_status cl_save_state(cl_lattice* l, void* host, size_t bytes) {
   h.step = l->step;
   h.k_ref = l->k_ref;
   h.params = l->p;
-  h.link_doubles = 72ull * (uint64_t)l->g.V;
+  h.link_bytes = link_field_bytes(l);
   CK(cudaMemcpyAsync(&h.sd, l->sd, sizeof(StepDev), cudaMemcpyDeviceToHost, l->st));
   CK(cudaMemcpyAsync(&h.cs, l->cs, sizeof(CoolState), cudaMemcpyDeviceToHost, l->st));
+  CK(cudaMemcpyAsync((char*)host + sizeof(CkptHeader), l->U, h.link_bytes, cudaMemcpyDeviceToHost, l->st));
   CK(cudaStreamSynchronize(l->st));
   std::memcpy(host, &h, sizeof(h));
-  return cl_get_links(l, (double*)((char*)host + sizeof(CkptHeader)));
+  return CL_OK;
 }
 
 cl_status cl_load_state(cl_lattice* l, const void* host, size_t bytes) {
@@ -1106,7 +1111,7 @@ cl_status cl_load_state(cl_lattice* l, const void* host, size_t bytes) {
   for (int mu = 0; mu < 4; ++mu)
     if (h.L[mu] != l->g.L[mu]) return fail(CL_ERR_INVALID, "checkpoint of other extents");
   if (h.prec != l->prec) return fail(CL_ERR_INVALID, "checkpoint of the other precision");
-  if (h.link_doubles != 72ull * (uint64_t)l->g.V || bytes < ckpt_bytes(l))
+  if (h.link_bytes != link_field_bytes(l) || bytes < ckpt_bytes(l))
     return fail(CL_ERR_INVALID, "truncated checkpoint");
   CK(cudaStreamSynchronize(l->st));
   for (int v = 0; v < 2; ++v)
@@ -1118,8 +1123,8 @@ cl_status cl_load_state(cl_lattice* l, const void* host, size_t bytes) {
   l->k_ref = h.k_ref;
   for (int f = 0; f < NTUNE; ++f) l->g.blk[f] = h.blk[f];
   l->step = h.step;
-  cl_status s = cl_set_links(l, (const double*)((const char*)host + sizeof(CkptHeader)));
-  if (s != CL_OK) return s;
+  CK(cudaMemcpyAsync(l->U, (const char*)host + sizeof(CkptHeader), h.link_bytes, cudaMemcpyHostToDevice,
+                     l->st));
   CK(cudaMemcpyAsync(l->sd, &h.sd, sizeof(StepDev), cudaMemcpyHostToDevice, l->st));
   CK(cudaMemcpyAsync(l->cs, &h.cs, sizeof(CoolState), cudaMemcpyHostToDevice, l->st));
   CK(cudaStreamSynchronize(l->st));

@@ -56,6 +56,9 @@ __device__ __forceinline__ double flip(double x, unsigned long long m) {
 __device__ __forceinline__ float flip(float x, unsigned long long m) {
   return __int_as_float(__float_as_int(x) ^ (int)(m >> 32));
 }
+__device__ __forceinline__ df64 flip(df64 x, unsigned long long m) {
+  return df64(flip(x.hi, m), flip(x.lo, m));
+}
 template <typename T>
 __device__ __forceinline__ void load_signed(mat<T>& G, const typename vec2_of<T>::type* F, int p,
                                             int s, int V, unsigned long long m) {
@@ -73,10 +76,7 @@ __device__ __forceinline__ void load_rw(mat<T>& a, const typename vec2_of<T>::ty
                                         int site, int V) {
   const typename vec2_of<T>::type* p = f + (size_t)plane * 9 * V + site;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    typename vec2_of<T>::type v = p[(size_t)k * V];
-    a.e[k] = cx<T>{v.x, v.y};
-  }
+  for (int k = 0; k < 9; ++k) a.e[k] = unpack(p[(size_t)k * V]);
 }
 
 // c += [a, b] = a b - b a

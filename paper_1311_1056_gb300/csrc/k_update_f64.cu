@@ -85,30 +85,45 @@ cudaError_t launch_plaq_force_f32(bool, const GeoH&, const void*, const void*, c
                                   const void*, const void*, void*, void*, double, cudaStream_t);
 cudaError_t launch_update_gather_f32(int, const GeoH&, const void*, const void*, void*, double,
                                      uint64_t, StepDev*, bool, cudaStream_t);
+cudaError_t launch_link_inverse_df64(const GeoH&, const void*, void*, cudaStream_t);
+cudaError_t launch_plaq_df64(const GeoH&, const void*, const void*, void*, void*, cudaStream_t);
+cudaError_t launch_clover_rot_df64(const GeoH&, const void*, const void*, const void*, void*, double,
+                                  double, cudaStream_t);
+cudaError_t launch_plaq_force_df64(bool, const GeoH&, const void*, const void*, const void*,
+                                  const void*, const void*, void*, void*, double, cudaStream_t);
+cudaError_t launch_update_gather_df64(int, const GeoH&, const void*, const void*, void*, double,
+                                     uint64_t, StepDev*, bool, cudaStream_t);
 
 cudaError_t launch_link_inverse(int prec, const GeoH& h, const void* U, void* Ui, cudaStream_t st) {
-  return prec == 0 ? launch_link_inverse_f64(h, U, Ui, st) : launch_link_inverse_f32(h, U, Ui, st);
+  if (prec == 0) return launch_link_inverse_f64(h, U, Ui, st);
+  if (prec == 1) return launch_link_inverse_f32(h, U, Ui, st);
+  return launch_link_inverse_df64(h, U, Ui, st);
 }
 cudaError_t launch_plaq(int prec, const GeoH& h, const void* U, const void* Ui, void* Pq, void* Dq,
                         cudaStream_t st) {
-  return prec == 0 ? launch_plaq_f64(h, U, Ui, Pq, Dq, st) : launch_plaq_f32(h, U, Ui, Pq, Dq, st);
+  if (prec == 0) return launch_plaq_f64(h, U, Ui, Pq, Dq, st);
+  if (prec == 1) return launch_plaq_f32(h, U, Ui, Pq, Dq, st);
+  return launch_plaq_df64(h, U, Ui, Pq, Dq, st);
 }
 cudaError_t launch_clover_rot(int prec, const GeoH& h, const void* U, const void* Ui, const void* Dq,
                               void* F, double sre, double sim, cudaStream_t st) {
-  return prec == 0 ? launch_clover_rot_f64(h, U, Ui, Dq, F, sre, sim, st)
-                   : launch_clover_rot_f32(h, U, Ui, Dq, F, sre, sim, st);
+  if (prec == 0) return launch_clover_rot_f64(h, U, Ui, Dq, F, sre, sim, st);
+  if (prec == 1) return launch_clover_rot_f32(h, U, Ui, Dq, F, sre, sim, st);
+  return launch_clover_rot_df64(h, U, Ui, Dq, F, sre, sim, st);
 }
 cudaError_t launch_plaq_force(int prec, bool theta, const GeoH& h, const void* U, const void* Ui,
                               const void* Pq, const void* Dq, const void* F, void* Gq, void* C,
                               double beta, cudaStream_t st) {
-  return prec == 0 ? launch_plaq_force_f64(theta, h, U, Ui, Pq, Dq, F, Gq, C, beta, st)
-                   : launch_plaq_force_f32(theta, h, U, Ui, Pq, Dq, F, Gq, C, beta, st);
+  if (prec == 0) return launch_plaq_force_f64(theta, h, U, Ui, Pq, Dq, F, Gq, C, beta, st);
+  if (prec == 1) return launch_plaq_force_f32(theta, h, U, Ui, Pq, Dq, F, Gq, C, beta, st);
+  return launch_plaq_force_df64(theta, h, U, Ui, Pq, Dq, F, Gq, C, beta, st);
 }
 cudaError_t launch_update_gather(int prec, int mode, const GeoH& h, const void* U, const void* C,
                                  void* out, double eps, uint64_t seed, StepDev* sd, bool adaptive,
                                  cudaStream_t st) {
-  return prec == 0 ? launch_update_gather_f64(mode, h, U, C, out, eps, seed, sd, adaptive, st)
-                   : launch_update_gather_f32(mode, h, U, C, out, eps, seed, sd, adaptive, st);
+  if (prec == 0) return launch_update_gather_f64(mode, h, U, C, out, eps, seed, sd, adaptive, st);
+  if (prec == 1) return launch_update_gather_f32(mode, h, U, C, out, eps, seed, sd, adaptive, st);
+  return launch_update_gather_df64(mode, h, U, C, out, eps, seed, sd, adaptive, st);
 }
 }  // namespace clgc
 

@@ -132,6 +132,14 @@ __global__ void k_hot(Geo g, typename vec2_of<T>::type* U, uint64_t seed) {
   store(U, mu, s, g.V, t);
 }
 
+// Read-only load of one real of a packed field.
+__device__ __forceinline__ double ldg_real(const double* p) { return __ldg(p); }
+__device__ __forceinline__ float ldg_real(const float* p) { return __ldg(p); }
+__device__ __forceinline__ df64 ldg_real(const df64* p) {
+  const float2 v = __ldg(reinterpret_cast<const float2*>(p));
+  return df64(v.x, v.y);
+}
+
 // Packed Hermitian field: planes d0, d1, d2, re01, im01, re02, im02, re12, im12.
 template <typename T>
 __device__ __forceinline__ void store_herm(T* P, int s, int V, const herm& h) {
@@ -147,10 +155,10 @@ __device__ __forceinline__ void store_herm(T* P, int s, int V, const herm& h) {
 }
 template <typename T>
 __device__ __forceinline__ void load_herm_mat(mat<T>& m, const T* __restrict__ P, int s, int V) {
-  T d0 = __ldg(P + s), d1 = __ldg(P + (size_t)V + s), d2 = __ldg(P + 2 * (size_t)V + s);
-  T a = __ldg(P + 3 * (size_t)V + s), b = __ldg(P + 4 * (size_t)V + s);
-  T c = __ldg(P + 5 * (size_t)V + s), d = __ldg(P + 6 * (size_t)V + s);
-  T e = __ldg(P + 7 * (size_t)V + s), f = __ldg(P + 8 * (size_t)V + s);
+  T d0 = ldg_real(P + s), d1 = ldg_real(P + (size_t)V + s), d2 = ldg_real(P + 2 * (size_t)V + s);
+  T a = ldg_real(P + 3 * (size_t)V + s), b = ldg_real(P + 4 * (size_t)V + s);
+  T c = ldg_real(P + 5 * (size_t)V + s), d = ldg_real(P + 6 * (size_t)V + s);
+  T e = ldg_real(P + 7 * (size_t)V + s), f = ldg_real(P + 8 * (size_t)V + s);
   m.e[0] = cx<T>{d0, T(0)};
   m.e[4] = cx<T>{d1, T(0)};
   m.e[8] = cx<T>{d2, T(0)};
@@ -199,10 +207,7 @@ __global__ void k_aos_to_soa(Geo g, const double* __restrict__ aos, typename vec
   int s = (int)(idx / (9 * nplanes));
   int r = (int)(idx - (size_t)s * 9 * nplanes);
   int p = r / 9, k = r - 9 * p;
-  typename vec2_of<T>::type v;
-  v.x = (T)aos[2 * idx];
-  v.y = (T)aos[2 * idx + 1];
-  U[((size_t)p * 9 + k) * g.V + s] = v;
+  U[((size_t)p * 9 + k) * g.V + s] = pack(cx<T>{(T)aos[2 * idx], (T)aos[2 * idx + 1]});
 }
 template <typename T>
 __global__ void k_soa_to_aos(Geo g, const typename vec2_of<T>::type* __restrict__ U,
@@ -213,9 +218,9 @@ __global__ void k_soa_to_aos(Geo g, const typename vec2_of<T>::type* __restrict_
   int s = (int)(idx / (9 * nplanes));
   int r = (int)(idx - (size_t)s * 9 * nplanes);
   int p = r / 9, k = r - 9 * p;
-  typename vec2_of<T>::type v = U[((size_t)p * 9 + k) * g.V + s];
-  aos[2 * idx] = (double)v.x;
-  aos[2 * idx + 1] = (double)v.y;
+  const cx<T> c = unpack(U[((size_t)p * 9 + k) * g.V + s]);
+  aos[2 * idx] = (double)c.re;
+  aos[2 * idx + 1] = (double)c.im;
 }
 
 // --------------------------------------------------------------- cooling
@@ -231,8 +236,8 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
     int x[4];
     site_coords(g, s, x);
-    T g00 = 0, g11 = 0, g22 = 0;
-    cx<T> g01 = {0, 0}, g02 = {0, 0}, g12 = {0, 0};
+    T g00 = T(0), g11 = T(0), g22 = T(0);
+    cx<T> g01 = {T(0), T(0)}, g02 = {T(0), T(0)}, g12 = {T(0), T(0)};
 #pragma unroll
     for (int mu = 0; mu < 4; ++mu) {
       mat<T> u;
@@ -269,14 +274,15 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename
     }
     const T r3 = (T)0.57735026918962576451;
     T fa[8];
-    fa[0] = 4 * g01.re;
-    fa[1] = -4 * g01.im;
-    fa[2] = 2 * (g00 - g11);
-    fa[3] = 4 * g02.re;
-    fa[4] = -4 * g02.im;
-    fa[5] = 4 * g12.re;
-    fa[6] = -4 * g12.im;
-    fa[7] = 2 * r3 * (g00 + g11 - 2 * g22);
+    const T two = T(2), four = T(4);
+    fa[0] = four * g01.re;
+    fa[1] = -(four * g01.im);
+    fa[2] = two * (g00 - g11);
+    fa[3] = four * g02.re;
+    fa[4] = -(four * g02.im);
+    fa[5] = four * g12.re;
+    fa[6] = -(four * g12.im);
+    fa[7] = two * r3 * (g00 + g11 - two * g22);
     bool ok = isfinite(un);
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
@@ -483,6 +489,15 @@ __global__ void k_obs_final(Geo g, const double* partials, int nb, double beta, 
 
 // Reduction kernels loop over sites with at most RED_MAX_BLOCKS blocks, so
 // the one-block rule reads few records; the split depends on V only.
+// Launch with the link type of precision prec (0 FP64, 1 FP32 storage, 2 DF64).
+template <typename Fn>
+cudaError_t by_prec(int prec, Fn fn) {
+  if (prec == 0) fn(double());
+  else if (prec == 1) fn(float());
+  else fn(df64());
+  return cudaGetLastError();
+}
+
 int reduce_blocks(int V) {
   int b = (V + RED_THREADS - 1) / RED_THREADS;
   return b < RED_MAX_BLOCKS ? b : RED_MAX_BLOCKS;
@@ -490,26 +505,27 @@ int reduce_blocks(int V) {
 
 cudaError_t launch_cold(int prec, const GeoH& h, void* U, cudaStream_t st) {
   Geo g = to_geo(h);
-  if (prec == 0) k_cold<double><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (double2*)U);
-  else k_cold<float><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (float2*)U);
-  return cudaGetLastError();
+  return by_prec(prec, [&](auto t) {
+    using T = decltype(t);
+    k_cold<T><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (typename vec2_of<T>::type*)U);
+  });
 }
 
 cudaError_t launch_hot(int prec, const GeoH& h, void* U, uint64_t seed, cudaStream_t st) {
   Geo g = to_geo(h);
-  if (prec == 0) k_hot<double><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (double2*)U, seed);
-  else k_hot<float><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (float2*)U, seed);
-  return cudaGetLastError();
+  return by_prec(prec, [&](auto t) {
+    using T = decltype(t);
+    k_hot<T><<<grid_sites(g.V, 4), RED_THREADS, 0, st>>>(g, (typename vec2_of<T>::type*)U, seed);
+  });
 }
 
 cudaError_t launch_gauge_omega(int prec, const GeoH& h, void* Om, void* Omi, uint64_t seed,
                                double sigma, cudaStream_t st) {
   Geo g = to_geo(h);
-  if (prec == 0)
-    k_gauge_omega<double><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (double*)Om, (double*)Omi, seed, sigma);
-  else
-    k_gauge_omega<float><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (float*)Om, (float*)Omi, seed, sigma);
-  return cudaGetLastError();
+  return by_prec(prec, [&](auto t) {
+    using T = decltype(t);
+    k_gauge_omega<T><<<grid_sites(g.V), RED_THREADS, 0, st>>>(g, (T*)Om, (T*)Omi, seed, sigma);
+  });
 }
 
 cudaError_t launch_aos_to_soa(int prec, const GeoH& h, const double* aos, void* U, int nplanes,
@@ -517,9 +533,10 @@ cudaError_t launch_aos_to_soa(int prec, const GeoH& h, const double* aos, void* 
   Geo g = to_geo(h);
   size_t n = (size_t)g.V * nplanes * 9;
   unsigned blocks = (unsigned)((n + 255) / 256);
-  if (prec == 0) k_aos_to_soa<double><<<blocks, 256, 0, st>>>(g, aos, (double2*)U, nplanes);
-  else k_aos_to_soa<float><<<blocks, 256, 0, st>>>(g, aos, (float2*)U, nplanes);
-  return cudaGetLastError();
+  return by_prec(prec, [&](auto t) {
+    using T = decltype(t);
+    k_aos_to_soa<T><<<blocks, 256, 0, st>>>(g, aos, (typename vec2_of<T>::type*)U, nplanes);
+  });
 }
 
 cudaError_t launch_soa_to_aos(int prec, const GeoH& h, const void* U, double* aos, int nplanes,
@@ -527,19 +544,20 @@ cudaError_t launch_soa_to_aos(int prec, const GeoH& h, const void* U, double* ao
   Geo g = to_geo(h);
   size_t n = (size_t)g.V * nplanes * 9;
   unsigned blocks = (unsigned)((n + 255) / 256);
-  if (prec == 0) k_soa_to_aos<double><<<blocks, 256, 0, st>>>(g, (const double2*)U, aos, nplanes);
-  else k_soa_to_aos<float><<<blocks, 256, 0, st>>>(g, (const float2*)U, aos, nplanes);
-  return cudaGetLastError();
+  return by_prec(prec, [&](auto t) {
+    using T = decltype(t);
+    k_soa_to_aos<T><<<blocks, 256, 0, st>>>(g, (const typename vec2_of<T>::type*)U, aos, nplanes);
+  });
 }
 
 cudaError_t launch_cool_grad(int prec, const GeoH& h, const void* U, void* f, double* partials,
                              const CoolState* cs, cudaStream_t st) {
   Geo g = to_geo(h);
-  if (prec == 0)
-    k_cool_grad<double><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const double2*)U, (double*)f, partials, cs);
-  else
-    k_cool_grad<float><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const float2*)U, (double*)f, partials, cs);
-  return cudaGetLastError();
+  return by_prec(prec, [&](auto t) {
+    using T = decltype(t);
+    k_cool_grad<T><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const typename vec2_of<T>::type*)U, (double*)f,
+                                                              partials, cs);
+  });
 }
 
 cudaError_t launch_cool_adapt(const GeoH& h, const double* partials, CoolArgs a, CoolState* cs,
@@ -554,11 +572,10 @@ cudaError_t launch_cool_omega(int prec, const GeoH& h, const void* f, void* Om, 
   Geo g = to_geo(h);
   const int bs = block_of(h, TUNE_OMEGA);
   const dim3 grid((unsigned)((g.V + bs - 1) / bs));
-  if (prec == 0)
-    k_cool_omega<double><<<grid, bs, 0, st>>>(g, (const double*)f, (double*)Om, (double*)Omi, eps, cs);
-  else
-    k_cool_omega<float><<<grid, bs, 0, st>>>(g, (const double*)f, (float*)Om, (float*)Omi, eps, cs);
-  return cudaGetLastError();
+  return by_prec(prec, [&](auto t) {
+    using T = decltype(t);
+    k_cool_omega<T><<<grid, bs, 0, st>>>(g, (const double*)f, (T*)Om, (T*)Omi, eps, cs);
+  });
 }
 
 cudaError_t launch_cool_apply(int prec, const GeoH& h, void* U, const void* Om, const void* Omi,
@@ -566,21 +583,21 @@ cudaError_t launch_cool_apply(int prec, const GeoH& h, void* U, const void* Om, 
   Geo g = to_geo(h);
   const int bs = block_of(h, TUNE_APPLY);
   const dim3 grid((unsigned)(((g.V + bs - 1) / bs) * 4));
-  if (prec == 0)
-    k_cool_apply<double><<<grid, bs, 0, st>>>(g, (double2*)U, (const double*)Om, (const double*)Omi, cs);
-  else
-    k_cool_apply<float><<<grid, bs, 0, st>>>(g, (float2*)U, (const float*)Om, (const float*)Omi, cs);
-  return cudaGetLastError();
+  return by_prec(prec, [&](auto t) {
+    using T = decltype(t);
+    k_cool_apply<T><<<grid, bs, 0, st>>>(g, (typename vec2_of<T>::type*)U, (const T*)Om, (const T*)Omi, cs);
+  });
 }
 
 cudaError_t launch_obs(int prec, const GeoH& h, const void* U, const void* F, int with_q,
                        double* partials, double* q_site, cudaStream_t st) {
   Geo g = to_geo(h);
-  if (prec == 0)
-    k_obs<double><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const double2*)U, (const double2*)F, with_q, partials, q_site);
-  else
-    k_obs<float><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const float2*)U, (const float2*)F, with_q, partials, q_site);
-  return cudaGetLastError();
+  return by_prec(prec, [&](auto t) {
+    using T = decltype(t);
+    k_obs<T><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const typename vec2_of<T>::type*)U,
+                                                        (const typename vec2_of<T>::type*)F, with_q, partials,
+                                                        q_site);
+  });
 }
 
 cudaError_t launch_obs_final(const GeoH& h, const double* partials, double beta, double th_re,

@@ -64,14 +64,14 @@ void destroy_chain(Chain* c) {
   delete c;
 }
 
-cl_params params_of(const cl_request& r, int prec) {
+cl_params params_of(const cl_request& r, cl_precision prec) {
   cl_params p;
   std::memset(&p, 0, sizeof(p));
   for (int mu = 0; mu < 4; ++mu) p.L[mu] = r.L[mu];
   p.beta = r.beta;
   p.theta_re = r.theta_re;
   p.theta_im = r.theta_im;
-  p.prec = prec == 0 ? CL_FP64 : CL_FP32_STORAGE;
+  p.prec = prec;
   p.seed = r.seed;
   p.start = r.start;
   p.gauge_sigma = r.gauge_sigma;
@@ -103,7 +103,7 @@ cl_status check_request(const cl_server* s, const cl_request* r) {
     if (r->L[mu] < 1) return fail(CL_ERR_INVALID, "lattice extent < 1");
   if (r->n_steps < 0 || !(r->eps >= 0.0)) return fail(CL_ERR_INVALID, "bad n_steps or eps");
   if (r->start != CL_START_COLD && r->start != CL_START_HOT) return fail(CL_ERR_INVALID, "bad start");
-  cl_params p = params_of(*r, s->cfg.prec == CL_FP64 ? 0 : 1);
+  cl_params p = params_of(*r, s->cfg.prec);
   size_t b = 0;
   cl_status st = cl_lattice_bytes(&p, &b);
   if (st != CL_OK) return st;
@@ -159,7 +159,7 @@ cl_status new_chain(cl_server* s, const cl_params& p, Chain** out) {
   *out = nullptr;
   Chain* c = new Chain();
   for (int mu = 0; mu < 4; ++mu) c->L[mu] = p.L[mu];
-  c->prec = p.prec == CL_FP64 ? 0 : 1;
+  c->prec = (int)p.prec;
   cl_status st = cl_lattice_bytes(&p, &c->bytes);
   cudaError_t e = cudaSuccess;
   if (st == CL_OK) e = cudaStreamCreateWithFlags(&c->st, cudaStreamNonBlocking);
@@ -188,8 +188,8 @@ cl_status new_chain(cl_server* s, const cl_params& p, Chain** out) {
 cl_status admit(cl_server* s) {
   while (!s->queue.empty() && (int)s->active.size() < s->cfg.max_slots) {
     const Pending& pd = s->queue.front();
-    const int prec = s->cfg.prec == CL_FP64 ? 0 : 1;
-    cl_params p = params_of(pd.req, prec);
+    const int prec = (int)s->cfg.prec;
+    cl_params p = params_of(pd.req, s->cfg.prec);
     Chain* c = nullptr;
     for (size_t i = 0; i < s->pool.size(); ++i) {
       Chain* q = s->pool[i];
@@ -314,7 +314,8 @@ cl_status cl_server_create(const cl_server_config* cfg, cl_server** out) {
   *out = nullptr;
   if (cfg->max_slots < 1 || cfg->chunk_steps < 1 || !(cfg->hbm_budget_bytes > 0.0))
     return fail(CL_ERR_INVALID, "bad server configuration");
-  if (cfg->prec != CL_FP64 && cfg->prec != CL_FP32_STORAGE) return fail(CL_ERR_INVALID, "bad precision");
+  if (cfg->prec != CL_FP64 && cfg->prec != CL_FP32_STORAGE && cfg->prec != CL_DF64)
+    return fail(CL_ERR_INVALID, "bad precision");
   if (!(cfg->k_ref >= 0.0)) return fail(CL_ERR_INVALID, "k_ref must be >= 0");
   if (!(cfg->runaway_un >= 0.0)) return fail(CL_ERR_INVALID, "runaway_un must be >= 0");
   if (cfg->cool_enabled) {

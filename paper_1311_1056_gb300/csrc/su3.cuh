@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df64.cuh"
+
 namespace clgc {
 
 template <typename T>
@@ -27,6 +29,15 @@ struct mat {
 template <typename T> struct vec2_of;
 template <> struct vec2_of<double> { typedef double2 type; };
 template <> struct vec2_of<float> { typedef float2 type; };
+template <> struct vec2_of<df64> { typedef float4 type; };  // (re.hi, re.lo, im.hi, im.lo)
+
+// One complex entry to / from its storage vector.
+__device__ __forceinline__ cx<double> unpack(double2 v) { return cx<double>{v.x, v.y}; }
+__device__ __forceinline__ cx<float> unpack(float2 v) { return cx<float>{v.x, v.y}; }
+__device__ __forceinline__ cx<df64> unpack(float4 v) { return cx<df64>{df64(v.x, v.y), df64(v.z, v.w)}; }
+__device__ __forceinline__ double2 pack(cx<double> c) { return make_double2(c.re, c.im); }
+__device__ __forceinline__ float2 pack(cx<float> c) { return make_float2(c.re, c.im); }
+__device__ __forceinline__ float4 pack(cx<df64> c) { return df_pack(c.re, c.im); }
 
 template <typename T>
 __device__ __forceinline__ cx<T> cmul(cx<T> a, cx<T> b) {
@@ -144,6 +155,49 @@ __device__ __forceinline__ void mul_herm_right(mat<T>& c, const mat<T>& u, const
     }
 }
 
+// Double-float products as out-of-line functions.  Inlined, one double-float
+// 3x3 product is ~1,400 instructions and the force kernels no longer fit the
+// instruction cache (the warps then wait on instruction fetch); called, every
+// product site shares one body and the operands travel through the (L1-
+// resident) stack.  The FP64 and FP32 forms keep their inlined products.
+static __device__ __noinline__ void mul_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b);
+static __device__ __noinline__ void mul_acc_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b, int sign);
+template <>
+__device__ __forceinline__ void mul<df64>(mat<df64>& c, const mat<df64>& a, const mat<df64>& b) {
+  mul_df(c, a, b);
+}
+template <>
+__device__ __forceinline__ void mul_acc<+1, df64>(mat<df64>& c, const mat<df64>& a, const mat<df64>& b) {
+  mul_acc_df(c, a, b, +1);
+}
+template <>
+__device__ __forceinline__ void mul_acc<-1, df64>(mat<df64>& c, const mat<df64>& a, const mat<df64>& b) {
+  mul_acc_df(c, a, b, -1);
+}
+static __device__ __noinline__ void mul_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<df64> s = cmul(a.e[3 * i], b.e[j]);
+      s = cfma(a.e[3 * i + 1], b.e[3 + j], s);
+      s = cfma(a.e[3 * i + 2], b.e[6 + j], s);
+      c.e[3 * i + j] = s;
+    }
+}
+static __device__ __noinline__ void mul_acc_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b, int sign) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      cx<df64> s = c.e[3 * i + j];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        s = sign > 0 ? cfma(a.e[3 * i + k], b.e[3 * k + j], s) : cfms(a.e[3 * i + k], b.e[3 * k + j], s);
+      c.e[3 * i + j] = s;
+    }
+}
+
 // Adjugate: adj(a) a = det(a) 1; for det a = 1 it is the inverse.
 template <typename T>
 __device__ __forceinline__ void adj(mat<T>& r, const mat<T>& a) {
@@ -206,22 +260,14 @@ __device__ __forceinline__ void load(mat<T>& a, const typename vec2_of<T>::type*
                                      int plane, int site, int V) {
   const typename vec2_of<T>::type* p = f + (size_t)plane * 9 * V + site;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    typename vec2_of<T>::type v = __ldg(p + (size_t)k * V);
-    a.e[k] = cx<T>{v.x, v.y};
-  }
+  for (int k = 0; k < 9; ++k) a.e[k] = unpack(__ldg(p + (size_t)k * V));
 }
 template <typename T>
 __device__ __forceinline__ void store(typename vec2_of<T>::type* __restrict__ f, int plane,
                                       int site, int V, const mat<T>& a) {
   typename vec2_of<T>::type* p = f + (size_t)plane * 9 * V + site;
 #pragma unroll
-  for (int k = 0; k < 9; ++k) {
-    typename vec2_of<T>::type v;
-    v.x = a.e[k].re;
-    v.y = a.e[k].im;
-    p[(size_t)k * V] = v;
-  }
+  for (int k = 0; k < 9; ++k) p[(size_t)k * V] = pack(a.e[k]);
 }
 
 }  // namespace clgc
