@@ -175,9 +175,9 @@ __device__ __forceinline__ void mul_acc<-1, df64>(mat<df64>& c, const mat<df64>&
   mul_acc_df(c, a, b, -1);
 }
 static __device__ __noinline__ void mul_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i)  // rolled: one entry's code in the instruction cache
+#pragma unroll 1
     for (int j = 0; j < 3; ++j) {
       cx<df64> s = cmul(a.e[3 * i], b.e[j]);
       s = cfma(a.e[3 * i + 1], b.e[3 + j], s);
@@ -186,9 +186,9 @@ static __device__ __noinline__ void mul_df(mat<df64>& c, const mat<df64>& a, con
     }
 }
 static __device__ __noinline__ void mul_acc_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b, int sign) {
-#pragma unroll
+#pragma unroll 1
   for (int i = 0; i < 3; ++i)
-#pragma unroll
+#pragma unroll 1
     for (int j = 0; j < 3; ++j) {
       cx<df64> s = c.e[3 * i + j];
 #pragma unroll
