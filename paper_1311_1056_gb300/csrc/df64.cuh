@@ -66,6 +66,10 @@ __device__ __forceinline__ df64 fma(df64 a, df64 b, df64 c) {
   return df_fast_two_sum(s.hi, s.lo + (e + c.lo));
 }
 
+__device__ __forceinline__ df64& operator+=(df64& a, df64 b) { return a = a + b; }
+__device__ __forceinline__ df64& operator-=(df64& a, df64 b) { return a = a - b; }
+__device__ __forceinline__ df64& operator*=(df64& a, df64 b) { return a = a * b; }
+
 __device__ __forceinline__ bool isfinite(df64 x) { return ::isfinite(x.hi) && ::isfinite(x.lo); }
 
 // Storage of a complex df64 number: (re.hi, re.lo, im.hi, im.lo).

@@ -50,15 +50,20 @@ __device__ __forceinline__ int scaling_steps(float r) {
   return (int)ceilf(log2f(fminf(r, 1.0e30f)));
 }
 
-// exp(A) for traceless complex A, FP64.  r_hint >= 0 is the Frobenius norm
-// of A when the caller has it (e.g. from an FP32 copy); < 0 computes it.
-__device__ __forceinline__ void expm_traceless(mat<double>& E, const mat<double>& A, float r_hint = -1.f) {
-  mat<double> A2;
+// exp(A) for traceless complex A.  The matrix work (A^2, the final
+// a + b A + c A^2) is done in the link type T (FP64, or double-float in the
+// DF64 form); the scalar Cayley-Hamilton recurrences always run in FP64.
+// r_hint >= 0 is the Frobenius norm of A when the caller has it (e.g. from an
+// FP32 copy); < 0 computes it.
+template <typename T>
+__device__ __forceinline__ void expm_traceless(mat<T>& E, const mat<T>& A, float r_hint = -1.f) {
+  mat<T> A2;
   mul(A2, A, A);
-  cx<double> c1 = trace(A2);
+  const cx<T> t1 = trace(A2), t0 = trace_mul(A2, A);
+  cx<double> c1 = {(double)t1.re, (double)t1.im};
   c1.re *= 0.5;
   c1.im *= 0.5;
-  cx<double> c0 = trace_mul(A2, A);
+  cx<double> c0 = {(double)t0.re, (double)t0.im};
   c0.re *= (1.0 / 3.0);
   c0.im *= (1.0 / 3.0);
   float r = r_hint >= 0.f ? r_hint : sqrtf((float)norm2(A));
@@ -103,14 +108,12 @@ __device__ __forceinline__ void expm_traceless(mat<double>& E, const mat<double>
     c.re *= sc * sc;
     c.im *= sc * sc;
   }
+  const cx<T> aT = {(T)a.re, (T)a.im}, bT = {(T)b.re, (T)b.im}, cT = {(T)c.re, (T)c.im};
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    cx<double> v = cmul(b, A.e[k]);
-    v = cfma(c, A2.e[k], v);
-    if (k % 4 == 0) {
-      v.re += a.re;
-      v.im += a.im;
-    }
+    cx<T> v = cmul(bT, A.e[k]);
+    v = cfma(cT, A2.e[k], v);
+    if (k % 4 == 0) v = cadd(v, aT);
     E.e[k] = v;
   }
 }

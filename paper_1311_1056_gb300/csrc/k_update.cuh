@@ -32,6 +32,8 @@
 //     = 2 eps (X_S - Tr X_S / 3) + i sqrt(eps) eta_a lambda_a,  <eta_a eta_b> = 2 delta_ab,
 //   U' = exp(A) U  (exp in FP64),  U' <- U' det(U')^{-1/3}  (FP64 factor).
 #pragma once
+#include <type_traits>
+
 #include "expm.cuh"
 #include "lattice.cuh"
 #include "launch.h"
@@ -469,11 +471,33 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const t
   // exponent A = 2 eps (X - Tr X/3) + i sqrt(eps) eta_a lambda_a; exp in FP64.
   // The FP64 form builds A in FP64; the FP32-storage form builds it in FP32
   // (X and the noise carry FP32 information only) and widens it for the exp.
-  mat<double> A;
-  float rA = -1.f;
   const uint32_t step = a.sd->step;
   const double eps = a.adaptive ? a.sd->eps_n : a.eps;
   const double sqrt_eps = a.adaptive ? a.sd->sqrt_eps_n : a.sqrt_eps;
+  if constexpr (std::is_same<T, df64>::value) {
+    // DF64: the exponent, its matrix powers and the update in double-float;
+    // the FP64 noise, the exponential's scalar recurrences and the
+    // determinant's cube root in FP64
+    double eta[8];
+    normals_f64<4>(eta, a.seed, step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
+    df64 etad[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) etad[j] = df64(eta[j]);
+    exponent<df64>(X, etad, df64(eps), df64(sqrt_eps));
+    mat<df64> E, Ul, Un;
+    expm_traceless(E, X);
+    load(Ul, U, MU, s, g.V);
+    mul(Un, E, Ul);
+    const cx<df64> d = det(Un);
+    const cx<double> z = det_inv_cuberoot(cx<double>{(double)d.re, (double)d.im});
+    const cx<df64> zt = {df64(z.re), df64(z.im)};
+#pragma unroll
+    for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], zt);
+    store(out, MU, s, g.V, Un);
+    return;
+  }
+  mat<double> A;
+  float rA = -1.f;
   if (sizeof(T) == 8) {
     double eta[8];
     normals_f64<4>(eta, a.seed, step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
