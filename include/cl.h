@@ -401,6 +401,18 @@ cl_status cl_drift(cl_lattice* lat, double* host_aos);
 /* Cooling gradient f_ax = 2 Tr[lambda_a sum_mu (U U^+ - U^+_{x-mu} U_{x-mu})]
  * (Sec. 2, eq. "eq:24"), host doubles, layout [a][site] (8*V).  Synchronises. */
 cl_status cl_cool_gradient(cl_lattice* lat, double* host_f);
+
+/* The standard normal numbers of the CL noise as the kernels of form prec
+ * draw them (Philox4x32-10 stream 0, Box-Muller): for each of the nsites
+ * sites site0 .. site0 + nsites - 1 and direction mu, the 8 numbers of link
+ * (site, mu) at step `step` (eta_a = sqrt(2) times them, a = 1..8; Sec. 2
+ * noise normalisation), host doubles [site][8].  FP64 draws them in FP64,
+ * DF64 in double-float, FP32 storage in float.  A diagnostic: it uses the
+ * current device and the legacy default stream, allocates and frees its own
+ * device buffer, and synchronises.  Errors: CL_ERR_INVALID (NULL out, bad
+ * precision, nsites < 0, site0 < 0, mu outside 0..3), CL_ERR_OOM, CL_ERR_CUDA. */
+cl_status cl_noise_sample(cl_precision prec, uint64_t seed, uint32_t step, int mu, int site0, int nsites,
+                          double* host_out);
 /* Topological charge density q_L(x) (Sec. 5), host doubles [site]{re,im} (2*V). */
 cl_status cl_qdensity(cl_lattice* lat, double* host_q);
 

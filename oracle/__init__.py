@@ -46,6 +46,7 @@ def lib():
         sig = {
             "or_philox4x32_10": (None, [u32p, u32p, u32p]),
             "or_normals": (None, [u64, u32, u32, u32, u32, cint, dp]),
+            "or_normals_sites": (None, [u64, u32, u32, cint, u32, u32, cint, dp]),
             "or_gellmann": (None, [cint, dp]),
             "or_expm": (None, [dp, dp]),
             "or_inverse": (None, [dp, dp]),
@@ -132,6 +133,12 @@ def philox(ctr, key):
 def normals(seed, step, site, slot, stream, n_pairs):
     out = np.zeros(2 * n_pairs)
     lib().or_normals(seed, step, site, slot, stream, n_pairs, _dp(out))
+    return out
+
+
+def normals_sites(seed, step, site0, nsites, slot, stream, n_pairs):
+    out = np.zeros((nsites, 2 * n_pairs))
+    lib().or_normals_sites(seed, step, site0, nsites, slot, stream, n_pairs, _dp(out))
     return out
 
 

@@ -675,6 +675,12 @@ void or_normals(uint64_t seed, uint32_t step, uint32_t site, uint32_t slot, uint
   normals(seed, step, site, slot, stream, n_pairs, out);
 }
 
+void or_normals_sites(uint64_t seed, uint32_t step, uint32_t site0, int nsites, uint32_t slot,
+                      uint32_t stream, int n_pairs, double* out) {
+  for (int i = 0; i < nsites; ++i)
+    normals(seed, step, site0 + (uint32_t)i, slot, stream, n_pairs, out + (size_t)i * 2 * n_pairs);
+}
+
 void or_gellmann(int a, double* out18) { store(gellmann(a), out18); }
 void or_expm(const double* a18, double* out18) { store(expm(load(a18)), out18); }
 void or_inverse(const double* a18, double* out18) { store(inverse(load(a18)), out18); }

@@ -32,6 +32,9 @@ void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out
  * counter giving one Box-Muller pair. */
 void or_normals(uint64_t seed, uint32_t step, uint32_t site, uint32_t slot,
                 uint32_t stream, int n_pairs, double* out);
+/* The same for the sites site0 .. site0 + nsites - 1: out[(i * 2 * n_pairs) + k]. */
+void or_normals_sites(uint64_t seed, uint32_t step, uint32_t site0, int nsites, uint32_t slot,
+                      uint32_t stream, int n_pairs, double* out);
 
 /* 3x3 primitives (used by the pins that check the oracle's own building blocks). */
 void or_gellmann(int a /* 1..8 */, double* out18);

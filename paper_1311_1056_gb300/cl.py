@@ -121,6 +121,8 @@ SIGNATURES = {
     "cl_drift": (ctypes.c_int, [_P, _dp]),
     "cl_cool_gradient": (ctypes.c_int, [_P, _dp]),
     "cl_qdensity": (ctypes.c_int, [_P, _dp]),
+    "cl_noise_sample": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, _dp]),
     "cl_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "cl_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "cl_get_timing": (ctypes.c_int, [_P, _dp, ctypes.POINTER(ctypes.c_int64)]),
@@ -463,6 +465,15 @@ def cl_cool_gradient(lat, V):
     out = np.empty((8, V))
     _check(load().cl_cool_gradient(lat, out.ctypes.data_as(_dp)), "cl_cool_gradient")
     return out.T.copy()  # (V, 8), like the oracle
+
+
+def noise_sample(prec, seed, step, mu, site0, nsites):
+    """The 8 standard normals of links (site0 .. site0 + nsites - 1, mu) at
+    `step`, as the kernels of form `prec` draw them: array (nsites, 8)."""
+    out = np.empty((max(nsites, 0), 8))
+    _check(load().cl_noise_sample(prec, seed, step, mu, site0, nsites, out.ctypes.data_as(_dp)),
+           "cl_noise_sample")
+    return out
 
 
 def cl_qdensity(lat, V):

@@ -320,7 +320,8 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
     cl_free(l);
     return s;
   }
-  cudaError_t e = init_state(l);
+  cudaError_t e = l->prec == 2 ? prepare_df64_kernels() : cudaSuccess;
+  if (e == cudaSuccess) e = init_state(l);
   if (e != cudaSuccess) {
     cl_free(l);
     return fail(CL_ERR_CUDA, std::string("init: ") + cudaGetErrorString(e));
@@ -562,6 +563,32 @@ cl_status cl_cool_gradient(cl_lattice* l, double* host_f) {
   const size_t n = 8 * (size_t)l->g.V;
   CK(cudaMemcpyAsync(host_f, l->f, sizeof(double) * n, cudaMemcpyDeviceToHost, l->st));
   CK(cudaStreamSynchronize(l->st));
+  if (l->prec == 2) {  // DF64 keeps f as (hi, lo) float pairs: widen in place
+    for (size_t i = 0; i < n; ++i) {
+      float hl[2];
+      std::memcpy(hl, host_f + i, sizeof(hl));
+      host_f[i] = (double)hl[0] + (double)hl[1];
+    }
+  }
+  return CL_OK;
+}
+
+cl_status cl_noise_sample(cl_precision prec, uint64_t seed, uint32_t step, int mu, int site0, int nsites,
+                          double* host_out) {
+  if (!host_out) return fail(CL_ERR_INVALID, "NULL argument");
+  if (prec != CL_FP64 && prec != CL_FP32_STORAGE && prec != CL_DF64) return fail(CL_ERR_INVALID, "bad precision");
+  if (nsites < 0 || site0 < 0 || mu < 0 || mu > 3 || (long long)site0 + nsites > INT_MAX)
+    return fail(CL_ERR_INVALID, "bad site range or direction");
+  if (nsites == 0) return CL_OK;
+  double* d = nullptr;
+  const size_t bytes = sizeof(double) * 8 * (size_t)nsites;
+  cudaError_t e = cudaMalloc(&d, bytes);
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA, cudaGetErrorString(e));
+  e = launch_noise_sample((int)prec, site0, nsites, seed, step, mu, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(host_out, d, bytes, cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(CL_ERR_CUDA, cudaGetErrorString(e));
   return CL_OK;
 }
 

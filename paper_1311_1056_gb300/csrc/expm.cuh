@@ -30,6 +30,20 @@ __constant__ double c_invfact[28] = {
     1.0 / 620448401733239439360000.0, 1.0 / 15511210043330985984000000.0,
     1.0 / 403291461126605635584000000.0, 1.0 / 10888869450418352160768000000.0};
 
+// The same table split into double-float constants.
+__constant__ df64 c_invfact_df[28] = {
+    df_const(1.0), df_const(1.0), df_const(0.5), df_const(1.0 / 6), df_const(1.0 / 24),
+    df_const(1.0 / 120), df_const(1.0 / 720), df_const(1.0 / 5040), df_const(1.0 / 40320),
+    df_const(1.0 / 362880), df_const(1.0 / 3628800), df_const(1.0 / 39916800),
+    df_const(1.0 / 479001600), df_const(1.0 / 6227020800.0), df_const(1.0 / 87178291200.0),
+    df_const(1.0 / 1307674368000.0), df_const(1.0 / 20922789888000.0),
+    df_const(1.0 / 355687428096000.0), df_const(1.0 / 6402373705728000.0),
+    df_const(1.0 / 121645100408832000.0), df_const(1.0 / 2432902008176640000.0),
+    df_const(1.0 / 51090942171709440000.0), df_const(1.0 / 1124000727777607680000.0),
+    df_const(1.0 / 25852016738884976640000.0), df_const(1.0 / 620448401733239439360000.0),
+    df_const(1.0 / 15511210043330985984000000.0), df_const(1.0 / 403291461126605635584000000.0),
+    df_const(1.0 / 10888869450418352160768000000.0)};
+
 // Number of Taylor terms for ||B||_F <= r <= 1 (float arithmetic: an estimate
 // on the cheap pipe; the bound has a factor > 2 of slack at the cut).
 __device__ __forceinline__ int taylor_terms(float r) {
@@ -51,8 +65,8 @@ __device__ __forceinline__ int scaling_steps(float r) {
 }
 
 // exp(A) for traceless complex A.  The matrix work (A^2, the final
-// a + b A + c A^2) is done in the link type T (FP64, or double-float in the
-// DF64 form); the scalar Cayley-Hamilton recurrences always run in FP64.
+// a + b A + c A^2) is done in the link type T (FP64 or FP32); the scalar
+// Cayley-Hamilton recurrences run in FP64.
 // r_hint >= 0 is the Frobenius norm of A when the caller has it (e.g. from an
 // FP32 copy); < 0 computes it.
 template <typename T>
@@ -114,6 +128,63 @@ __device__ __forceinline__ void expm_traceless(mat<T>& E, const mat<T>& A, float
     cx<T> v = cmul(bT, A.e[k]);
     v = cfma(cT, A2.e[k], v);
     if (k % 4 == 0) v = cadd(v, aT);
+    E.e[k] = v;
+  }
+}
+
+// The same exponential entirely in double-float (the DF64 form): the scalar
+// recurrences too, with the coefficients of c_invfact_df.
+__device__ __forceinline__ void expm_traceless_df(mat<df64>& E, const mat<df64>& A) {
+  mat<df64> A2;
+  mul(A2, A, A);
+  const cx<df64> t1 = trace(A2), t0 = trace_mul(A2, A);
+  const df64 third = df_const(1.0 / 3.0);
+  const cx<df64> c1 = {df_ldexp(t1.re, -1), df_ldexp(t1.im, -1)};
+  const cx<df64> c0 = {t0.re * third, t0.im * third};
+  float r = sqrtf((float)norm2(A));
+  int s = 0;
+  cx<df64> b0 = c0, b1 = c1;  // det and Tr(B^2)/2 of B = A 2^-s
+  if (r > 1.0f) {
+    s = scaling_steps(r);
+    r = ldexpf(r, -s);
+    b0 = cx<df64>{df_ldexp(c0.re, -3 * s), df_ldexp(c0.im, -3 * s)};
+    b1 = cx<df64>{df_ldexp(c1.re, -2 * s), df_ldexp(c1.im, -2 * s)};
+  }
+  const int N = taylor_terms(r);
+  const df64 zero(0.0f, 0.0f);
+  cx<df64> a = {c_invfact_df[N], zero}, b = {zero, zero}, c = {zero, zero};
+  for (int k = N - 1; k >= 0; --k) {
+    const cx<df64> na = cfma(c, b0, cx<df64>{c_invfact_df[k], zero});
+    const cx<df64> nb = cfma(c, b1, a);
+    c = b;
+    b = nb;
+    a = na;
+  }
+  for (int i = 0; i < s; ++i) {  // (a + bB + cB^2)^2 with B^3 = b1 B + b0
+    const cx<df64> bc = cmul(b, c), cc = cmul(c, c);
+    const cx<df64> bc2 = {df_ldexp(bc.re, 1), df_ldexp(bc.im, 1)};
+    const cx<df64> a2 = {df_ldexp(a.re, 1), df_ldexp(a.im, 1)};
+    cx<df64> na = cmul(a, a);
+    na = cfma(bc2, b0, na);
+    cx<df64> nb = cmul(a2, b);
+    nb = cfma(bc2, b1, nb);
+    nb = cfma(cc, b0, nb);
+    cx<df64> nc = cmul(b, b);
+    nc = cfma(a2, c, nc);
+    nc = cfma(cc, b1, nc);
+    a = na;
+    b = nb;
+    c = nc;
+  }
+  if (s > 0) {  // back to powers of A
+    b = cx<df64>{df_ldexp(b.re, -s), df_ldexp(b.im, -s)};
+    c = cx<df64>{df_ldexp(c.re, -2 * s), df_ldexp(c.im, -2 * s)};
+  }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    cx<df64> v = cmul(b, A.e[k]);
+    v = cfma(c, A2.e[k], v);
+    if (k % 4 == 0) v = cadd(v, a);
     E.e[k] = v;
   }
 }
@@ -233,6 +304,121 @@ __device__ __forceinline__ cx<double> det_inv_cuberoot(cx<double> d) {
   double sn, cs;
   sincos(ang, &sn, &cs);
   return cx<double>{mag * cs, mag * sn};
+}
+
+// Double-float Hermitian 3x3 and its exponential pair (the DF64 form's
+// cooling transformation), the same steps as above in double-float.
+struct herm_df {
+  df64 d0, d1, d2;
+  cx<df64> o01, o02, o12;
+};
+
+__device__ __forceinline__ df64 df_abs2(cx<df64> z) { return fma(z.re, z.re, z.im * z.im); }
+
+__device__ __forceinline__ void herm_square_df(herm_df& q, const herm_df& h) {
+  const df64 n01 = df_abs2(h.o01), n02 = df_abs2(h.o02), n12 = df_abs2(h.o12);
+  q.d0 = fma(h.d0, h.d0, n01 + n02);
+  q.d1 = fma(h.d1, h.d1, n01 + n12);
+  q.d2 = fma(h.d2, h.d2, n02 + n12);
+  const df64 s01 = h.d0 + h.d1, s02 = h.d0 + h.d2, s12 = h.d1 + h.d2;
+  // (H^2)_01 = (d0 + d1) o01 + o02 conj(o12)
+  q.o01.re = fma(s01, h.o01.re, fma(h.o02.re, h.o12.re, h.o02.im * h.o12.im));
+  q.o01.im = fma(s01, h.o01.im, fma(h.o02.im, h.o12.re, -(h.o02.re * h.o12.im)));
+  // (H^2)_02 = (d0 + d2) o02 + o01 o12
+  q.o02.re = fma(s02, h.o02.re, fma(h.o01.re, h.o12.re, -(h.o01.im * h.o12.im)));
+  q.o02.im = fma(s02, h.o02.im, fma(h.o01.re, h.o12.im, h.o01.im * h.o12.re));
+  // (H^2)_12 = (d1 + d2) o12 + conj(o01) o02
+  q.o12.re = fma(s12, h.o12.re, fma(h.o01.re, h.o02.re, h.o01.im * h.o02.im));
+  q.o12.im = fma(s12, h.o12.im, fma(h.o01.re, h.o02.im, -(h.o01.im * h.o02.re)));
+}
+
+// c 1 + b H + c2 H^2 for real coefficients
+__device__ __forceinline__ void herm_combine_df(herm_df& o, df64 a, df64 b, df64 c, const herm_df& h,
+                                                const herm_df& h2) {
+  o.d0 = fma(c, h2.d0, fma(b, h.d0, a));
+  o.d1 = fma(c, h2.d1, fma(b, h.d1, a));
+  o.d2 = fma(c, h2.d2, fma(b, h.d2, a));
+  o.o01 = cx<df64>{fma(c, h2.o01.re, b * h.o01.re), fma(c, h2.o01.im, b * h.o01.im)};
+  o.o02 = cx<df64>{fma(c, h2.o02.re, b * h.o02.re), fma(c, h2.o02.im, b * h.o02.im)};
+  o.o12 = cx<df64>{fma(c, h2.o12.re, b * h.o12.re), fma(c, h2.o12.im, b * h.o12.im)};
+}
+
+// Omega = exp(H) and Omega^{-1} = exp(-H) for traceless Hermitian H.
+__device__ __forceinline__ void expm_hermitian_pair_df(herm_df& om, herm_df& omi, const herm_df& h) {
+  herm_df h2;
+  herm_square_df(h2, h);
+  const df64 c1 = df_ldexp(h2.d0 + h2.d1 + h2.d2, -1);
+  // det H = d0 d1 d2 + 2 Re(o01 o12 conj(o02)) - d0|o12|^2 - d1|o02|^2 - d2|o01|^2
+  const df64 t_re = fma(h.o01.re, h.o12.re, -(h.o01.im * h.o12.im));
+  const df64 t_im = fma(h.o01.re, h.o12.im, h.o01.im * h.o12.re);
+  df64 c0 = h.d0 * h.d1 * h.d2;
+  c0 = c0 + df_ldexp(fma(t_re, h.o02.re, t_im * h.o02.im), 1);
+  c0 = fma(-h.d0, df_abs2(h.o12), c0);
+  c0 = fma(-h.d1, df_abs2(h.o02), c0);
+  c0 = fma(-h.d2, df_abs2(h.o01), c0);
+  float r = sqrtf(2.0f * c1.hi);
+  int s = 0;
+  df64 b1 = c1, b0 = c0;
+  if (r > 1.0f) {
+    s = scaling_steps(r);
+    r = ldexpf(r, -s);
+    b1 = df_ldexp(c1, -2 * s);
+    b0 = df_ldexp(c0, -3 * s);
+  }
+  const int N = taylor_terms(r);
+  // exp(B) = a + bB + cB^2 and exp(-B) = ap - bp B + cp B^2 (det(-B) = -det B)
+  const df64 zero(0.0f, 0.0f);
+  df64 a = c_invfact_df[N], b = zero, c = zero;
+  df64 ap = a, bp = zero, cp = zero;
+  for (int k = N - 1; k >= 0; --k) {
+    const df64 na = fma(c, b0, c_invfact_df[k]);
+    const df64 nb = fma(c, b1, a);
+    c = b;
+    b = nb;
+    a = na;
+    const df64 nap = fma(-cp, b0, c_invfact_df[k]);
+    const df64 nbp = fma(cp, b1, ap);
+    cp = bp;
+    bp = nbp;
+    ap = nap;
+  }
+  for (int i = 0; i < s; ++i) {
+    df64 bc2 = df_ldexp(b * c, 1), cc = c * c, a2 = df_ldexp(a, 1);
+    df64 na = fma(bc2, b0, a * a);
+    df64 nb = fma(cc, b0, fma(bc2, b1, a2 * b));
+    df64 nc = fma(cc, b1, fma(a2, c, b * b));
+    a = na; b = nb; c = nc;
+    bc2 = df_ldexp(bp * cp, 1), cc = cp * cp, a2 = df_ldexp(ap, 1);
+    na = fma(-bc2, b0, ap * ap);
+    nb = fma(-cc, b0, fma(bc2, b1, a2 * bp));
+    nc = fma(cc, b1, fma(a2, cp, bp * bp));
+    ap = na; bp = nb; cp = nc;
+  }
+  if (s > 0) {
+    b = df_ldexp(b, -s);
+    c = df_ldexp(c, -2 * s);
+    bp = df_ldexp(bp, -s);
+    cp = df_ldexp(cp, -2 * s);
+  }
+  herm_combine_df(om, a, b, c, h, h2);
+  herm_combine_df(omi, ap, -bp, cp, h, h2);  // exp(-H) = ap - bp H + cp H^2
+}
+
+// det(U)^(-1/3) in double-float: the binomial series near det = 1 (the
+// normal case), else the FP64 branch above.
+__device__ __forceinline__ cx<df64> det_inv_cuberoot_df(cx<df64> d) {
+  const cx<df64> e = {d.re - df64(1.0f, 0.0f), d.im};
+  if (e.re.hi * e.re.hi + e.im.hi * e.im.hi < 1e-8f) {
+    const df64 zero(0.0f, 0.0f);
+    cx<df64> p = {df_const(35.0 / 243.0), zero};
+    p = cfma(p, e, cx<df64>{df_const(-14.0 / 81.0), zero});
+    p = cfma(p, e, cx<df64>{df_const(2.0 / 9.0), zero});
+    p = cfma(p, e, cx<df64>{df_const(-1.0 / 3.0), zero});
+    p = cfma(p, e, cx<df64>{df64(1.0f, 0.0f), zero});
+    return p;
+  }
+  const cx<double> z = det_inv_cuberoot(cx<double>{(double)d.re, (double)d.im});
+  return cx<df64>{df64(z.re), df64(z.im)};
 }
 
 }  // namespace clgc

@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq(Geo g, const typename v
   if (s >= g.V) return;
   int x[4];
   site_coords(g, s, x);
-  mat<T> a, b, A, B, P;
+  Work<T, 5> ws(0);
+  mat<T>&a = ws[0], &b = ws[1], &A = ws[2], &B = ws[3], &P = ws[4];
   load(a, U, mu, s, g.V);
   load(b, U, nu, hop(g, s, x, mu, 1), g.V);
   mul(A, a, b);
@@ -159,7 +160,8 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_clover_rot(Geo g, const type
   site_coords(g, s, x);
   const int xmm = hop(g, s, x, mu, -1), xmn = hop(g, s, x, nu, -1);
   const int xmm_mn = hop2(g, s, x, mu, -1, nu, -1);
-  mat<T> acc, w, d, t;
+  Work<T, 4> ws(0);
+  mat<T>&acc = ws[0], &w = ws[1], &d = ws[2], &t = ws[3];
   load(acc, Dq, p, s, g.V);
   // L2 = U_mu(x-mu)^{-1} D(x-mu) U_mu(x-mu)
   load(w, Ui, mu, xmm, g.V);
@@ -200,7 +202,8 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_wilson(Geo g, con
   const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p);
   const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
-  mat<T> D, M, t, a;
+  Work<T, 4> ws(0);
+  mat<T>&D = ws[0], &M = ws[1], &t = ws[2], &a = ws[3];
   load(D, Dq, p, s, g.V);
   scaled(M, -beta6, D);
   store(C, 4 * p + 0, s, g.V, M);
@@ -229,7 +232,8 @@ __device__ __forceinline__ void force_stage_a(mat<T>& Gh, const Geo& g, int s, c
   const int mu = plane_mu(p), nu = plane_nu(p), pc = 5 - p;
   const unsigned long long m = (p == 1 || p == 4) ? 0x8000000000000000ull : 0ull;
   const int c1 = hop(g, s, x, mu, 1);
-  mat<T> D, M, t, q;
+  Work<T, 4> ws(1);  // slot 0 holds Gh
+  mat<T>&D = ws[0], &M = ws[1], &t = ws[2], &q = ws[3];
   load(D, Dq, p, s, g.V);
   // corner c0: slot 0 partial = [D, G0] - (beta/6) D
   load_signed(Gh, F, pc, s, g.V, m);
@@ -271,7 +275,8 @@ __device__ __forceinline__ void force_stage_b(mat<T>& Gh, const Geo& g, int s, c
   const int mu = plane_mu(p), nu = plane_nu(p), pc = 5 - p;
   const unsigned long long m = (p == 1 || p == 4) ? 0x8000000000000000ull : 0ull;
   const int c3 = hop(g, s, x, nu, 1);
-  mat<T> D, M, t, q;
+  Work<T, 4> ws(1);  // slot 0 holds Gh
+  mat<T>&D = ws[0], &M = ws[1], &t = ws[2], &q = ws[3];
   // corner c3: G3r = u G3 u^{-1}; slot 3 partial = [D, G3r] + (beta/6) D
   load_signed(q, F, pc, c3, g.V, m);
   load(M, U, nu, s, g.V);
@@ -340,7 +345,8 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_a(Geo g, const ty
   if (s >= g.V) return;
   int x[4];
   site_coords(g, s, x);
-  mat<T> Gh;
+  Work<T, 1> wg(0);
+  mat<T>& Gh = wg[0];
   force_stage_a(Gh, g, s, x, p, U, Ui, Dq, F, C, beta6);
   store(Gq, p, s, g.V, Gh);
 }
@@ -357,7 +363,8 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_b(Geo g, const ty
   if (s >= g.V) return;
   int x[4];
   site_coords(g, s, x);
-  mat<T> Gh;
+  Work<T, 1> wg(0);
+  mat<T>& Gh = wg[0];
   load(Gh, Gq, p, s, g.V);
   force_stage_b(Gh, g, s, x, p, U, Ui, Pq, Dq, F, C, beta6);
 }
@@ -374,7 +381,8 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_ab(Geo g, const t
   if (s >= g.V) return;
   int x[4];
   site_coords(g, s, x);
-  mat<T> Gh;
+  Work<T, 1> wg(0);
+  mat<T>& Gh = wg[0];
   force_stage_a(Gh, g, s, x, p, U, Ui, Dq, F, C, beta6);
   force_stage_b(Gh, g, s, x, p, U, Ui, Pq, Dq, F, C, beta6);
 }
@@ -475,24 +483,19 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const t
   const double eps = a.adaptive ? a.sd->eps_n : a.eps;
   const double sqrt_eps = a.adaptive ? a.sd->sqrt_eps_n : a.sqrt_eps;
   if constexpr (std::is_same<T, df64>::value) {
-    // DF64: the exponent, its matrix powers and the update in double-float;
-    // the FP64 noise, the exponential's scalar recurrences and the
-    // determinant's cube root in FP64
-    double eta[8];
-    normals_f64<4>(eta, a.seed, step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
-    df64 etad[8];
-#pragma unroll
-    for (int j = 0; j < 8; ++j) etad[j] = df64(eta[j]);
-    exponent<df64>(X, etad, df64(eps), df64(sqrt_eps));
+    // DF64: the noise, the exponent, the exponential (its scalar recurrences
+    // too), the update and the re-projection in double-float; no FP64
+    // instruction on the common path
+    df64 eta[8];
+    normals_df64<4>(eta, a.seed, step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
+    exponent<df64>(X, eta, df64(eps), df64(sqrt_eps));
     mat<df64> E, Ul, Un;
-    expm_traceless(E, X);
+    expm_traceless_df(E, X);
     load(Ul, U, MU, s, g.V);
     mul(Un, E, Ul);
-    const cx<df64> d = det(Un);
-    const cx<double> z = det_inv_cuberoot(cx<double>{(double)d.re, (double)d.im});
-    const cx<df64> zt = {df64(z.re), df64(z.im)};
+    const cx<df64> z = det_inv_cuberoot_df(det(Un));
 #pragma unroll
-    for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], zt);
+    for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], z);
     store(out, MU, s, g.V, Un);
     return;
   }

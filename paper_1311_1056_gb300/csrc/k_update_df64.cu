@@ -16,7 +16,29 @@ inline df64 df_host(double d) {
 // 1-D grid, plane (or direction) fastest: the blocks resident at one time
 // cover every plane of a range of sites, so shared neighbours stay in cache.
 inline dim3 grid(int V, int planes, int bs) { return dim3((unsigned)(((V + bs - 1) / bs) * planes)); }
+// dynamic shared memory of a kernel with nslot workspace matrices per thread
+inline size_t ws_bytes(int nslot, int bs) { return (size_t)nslot * sizeof(mat<df64>) * (size_t)bs; }
+const int NSLOT_PLAQ = 5, NSLOT_CLOVER = 4, NSLOT_WILSON = 4, NSLOT_FORCE = 5;
+
+template <typename K>
+cudaError_t allow_ws(K kernel, int nslot) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)ws_bytes(nslot, TUNE_MAX_BLOCK));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             (int)cudaSharedmemCarveoutMaxShared);
+  return e;
+}
 }  // namespace
+
+cudaError_t prepare_df64_kernels() {
+  cudaError_t e = allow_ws(k_plaq<df64>, NSLOT_PLAQ);
+  if (e == cudaSuccess) e = allow_ws(k_clover_rot<df64>, NSLOT_CLOVER);
+  if (e == cudaSuccess) e = allow_ws(k_plaq_force_wilson<df64>, NSLOT_WILSON);
+  if (e == cudaSuccess) e = allow_ws(k_plaq_force_a<df64>, NSLOT_FORCE);
+  if (e == cudaSuccess) e = allow_ws(k_plaq_force_b<df64>, NSLOT_FORCE);
+  return e;
+}
 
 cudaError_t launch_link_inverse_df64(const GeoH& h, const void* U, void* Ui, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
@@ -27,14 +49,16 @@ cudaError_t launch_link_inverse_df64(const GeoH& h, const void* U, void* Ui, cud
 cudaError_t launch_plaq_df64(const GeoH& h, const void* U, const void* Ui, void* Pq, void* Dq,
                            cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
-  k_plaq<df64><<<grid(g.V, 6, block_of(h, TUNE_CLOVER)), block_of(h, TUNE_CLOVER), 0, st>>>(g, (const V2*)U, (const V2*)Ui, (V2*)Pq, (V2*)Dq);
+  const int bs = block_of(h, TUNE_CLOVER);
+  k_plaq<df64><<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_PLAQ, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (V2*)Pq, (V2*)Dq);
   return cudaGetLastError();
 }
 
 cudaError_t launch_clover_rot_df64(const GeoH& h, const void* U, const void* Ui, const void* Dq,
                                  void* F, double sre, double sim, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
-  k_clover_rot<df64><<<grid(g.V, 6, block_of(h, TUNE_CLOVER)), block_of(h, TUNE_CLOVER), 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+  const int bs = block_of(h, TUNE_CLOVER);
+  k_clover_rot<df64><<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_CLOVER, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
                                                   (V2*)F, sre, sim);
   return cudaGetLastError();
 }
@@ -44,14 +68,15 @@ cudaError_t launch_plaq_force_df64(bool theta, const GeoH& h, const void* U, con
                                  double beta, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
   const df64 b6 = df_host(beta / 6.0);
+  const int bs = block_of(h, TUNE_FORCE);
   if (!theta) {
-    k_plaq_force_wilson<df64><<<grid(g.V, 6, block_of(h, TUNE_FORCE)), block_of(h, TUNE_FORCE), 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+    k_plaq_force_wilson<df64><<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_WILSON, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
                                                          (V2*)C, b6);
     return cudaGetLastError();
   }
-  k_plaq_force_a<df64><<<grid(g.V, 6, block_of(h, TUNE_FORCE)), block_of(h, TUNE_FORCE), 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+  k_plaq_force_a<df64><<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_FORCE, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
                                                   (const V2*)F, (V2*)Gq, (V2*)C, b6);
-  k_plaq_force_b<df64><<<grid(g.V, 6, block_of(h, TUNE_FORCE)), block_of(h, TUNE_FORCE), 0, st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
+  k_plaq_force_b<df64><<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_FORCE, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
                                                   (const V2*)Dq, (const V2*)F, (const V2*)Gq, (V2*)C, b6);
   return cudaGetLastError();
 }

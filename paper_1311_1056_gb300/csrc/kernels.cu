@@ -1,6 +1,8 @@
 // kernels.cu -- starts, layout conversion, clover field, gauge cooling and
 // observables.  The CL update kernel itself is in k_update.cuh
 // (instantiated by k_update_f64.cu / k_update_f32.cu).
+#include <type_traits>
+
 #include "expm.cuh"
 #include "launch.h"
 #include "lattice.cuh"
@@ -170,6 +172,33 @@ __device__ __forceinline__ void load_herm_mat(mat<T>& m, const T* __restrict__ P
   m.e[7] = cx<T>{e, -f};
 }
 
+template <typename T>
+__device__ __forceinline__ void store_herm_df(T* P, int s, int V, const herm_df& h) {
+  if constexpr (std::is_same<T, df64>::value) {
+    P[0 * (size_t)V + s] = h.d0;
+    P[1 * (size_t)V + s] = h.d1;
+    P[2 * (size_t)V + s] = h.d2;
+    P[3 * (size_t)V + s] = h.o01.re;
+    P[4 * (size_t)V + s] = h.o01.im;
+    P[5 * (size_t)V + s] = h.o02.re;
+    P[6 * (size_t)V + s] = h.o02.im;
+    P[7 * (size_t)V + s] = h.o12.re;
+    P[8 * (size_t)V + s] = h.o12.im;
+  }
+}
+// H = c * sum_a g_a lambda_a in double-float.
+__device__ __forceinline__ herm_df herm_from_algebra_df(const df64* g, df64 c) {
+  const df64 r3 = df_const(0.57735026918962576451);
+  herm_df h;
+  h.d0 = c * (g[2] + g[7] * r3);
+  h.d1 = c * (g[7] * r3 - g[2]);
+  h.d2 = -(c * df_ldexp(g[7] * r3, 1));
+  h.o01 = cx<df64>{c * g[0], -(c * g[1])};
+  h.o02 = cx<df64>{c * g[3], -(c * g[4])};
+  h.o12 = cx<df64>{c * g[5], -(c * g[6])};
+  return h;
+}
+
 // H = c * sum_a g_a lambda_a (Hermitian, traceless), g real.
 __device__ __forceinline__ herm herm_from_algebra(const double* g, double c) {
   const double r3 = 0.57735026918962576451;
@@ -194,6 +223,27 @@ __global__ void k_gauge_omega(Geo g, T* Om, T* Omi, uint64_t seed, double sigma)
   expm_hermitian_pair(om, omi, h);
   store_herm(Om, s, g.V, om);
   store_herm(Omi, s, g.V, omi);
+}
+
+// The CL noise of links (site0 + i, mu) as form T draws it (a diagnostic).
+template <typename T>
+__global__ void k_noise_sample(int site0, int n, uint64_t seed, uint32_t step, uint32_t mu, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const uint32_t s = (uint32_t)(site0 + i);
+  if constexpr (std::is_same<T, double>::value) {
+    normals_f64<4>(out + 8 * (size_t)i, seed, step, s, mu, STREAM_CL);
+  } else if constexpr (std::is_same<T, float>::value) {
+    float e[8];
+    normals_f32<4>(e, seed, step, s, mu, STREAM_CL);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) out[8 * (size_t)i + j] = (double)e[j];
+  } else {
+    df64 e[8];
+    normals_df64<4>(e, seed, step, s, mu, STREAM_CL);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) out[8 * (size_t)i + j] = (double)e[j];
+  }
 }
 
 // ------------------------------------------------------------ conversion
@@ -224,6 +274,94 @@ __global__ void k_soa_to_aos(Geo g, const typename vec2_of<T>::type* __restrict_
 }
 
 // --------------------------------------------------------------- cooling
+// The gradient of the DF64 form: G_x accumulated entry by entry in
+// double-float (dacc, renormalised after every link), f stored as hi + lo
+// float pairs, the rule's sums kept per thread in double-float and widened
+// to FP64 once for the block reduction.
+__device__ __forceinline__ void dacc_add_abs2(dacc& a, cx<df64> z, bool neg) {
+  dacc_add(a, neg ? -z.re : z.re, z.re);
+  dacc_add(a, neg ? -z.im : z.im, z.im);
+}
+// a += sign * x conj(y)
+__device__ __forceinline__ void dacc_add_xcy(dacc& re, dacc& im, cx<df64> x, cx<df64> y, bool neg) {
+  const df64 xr = neg ? -x.re : x.re, xi = neg ? -x.im : x.im;
+  dacc_add(re, xr, y.re);
+  dacc_add(re, xi, y.im);
+  dacc_add(im, xi, y.re);
+  dacc_add(im, -xr, y.im);
+}
+__device__ __forceinline__ void cool_grad_df(const Geo& g, const float4* __restrict__ U, float2* f,
+                                             double* v) {
+  df64 s_abs(0.0f, 0.0f), s_sq(0.0f, 0.0f), s_un(0.0f, 0.0f);
+  int bad = 0;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    int x[4];
+    site_coords(g, s, x);
+    dacc G[9];  // 00, 11, 22, 01re, 01im, 02re, 02im, 12re, 12im
+#pragma unroll
+    for (int q = 0; q < 9; ++q) G[q] = dacc{0.0f, 0.0f};
+    bool ok = true;
+    df64 un(0.0f, 0.0f);
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+#pragma unroll
+      for (int mu = 0; mu < 4; ++mu) {
+        mat<df64> u;
+        load(u, U, mu, dir == 0 ? s : hop(g, s, x, mu, -1), g.V);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          // + U U^+ (rows of the forward link), - U^+ U (columns of the backward link)
+          const cx<df64> r0 = dir == 0 ? u.e[k] : u.e[3 * k], r1 = dir == 0 ? u.e[3 + k] : u.e[3 * k + 1],
+                         r2 = dir == 0 ? u.e[6 + k] : u.e[3 * k + 2];
+          const bool neg = dir == 1;
+          dacc_add_abs2(G[0], r0, neg);
+          dacc_add_abs2(G[1], r1, neg);
+          dacc_add_abs2(G[2], r2, neg);
+          // + r_i conj(r_j) forward; - conj(c_i) c_j = - x conj(y) with x = conj(c_i),
+          // y = conj(c_j) backward
+          if (dir == 0) {
+            dacc_add_xcy(G[3], G[4], r0, r1, false);
+            dacc_add_xcy(G[5], G[6], r0, r2, false);
+            dacc_add_xcy(G[7], G[8], r1, r2, false);
+          } else {
+            const cx<df64> q0 = {r0.re, -r0.im}, q1 = {r1.re, -r1.im}, q2 = {r2.re, -r2.im};
+            dacc_add_xcy(G[3], G[4], q0, q1, true);
+            dacc_add_xcy(G[5], G[6], q0, q2, true);
+            dacc_add_xcy(G[7], G[8], q1, q2, true);
+          }
+        }
+#pragma unroll
+        for (int q = 0; q < 9; ++q) dacc_norm(G[q]);
+      }
+      if (dir == 0) un = dacc_get(G[0]) + dacc_get(G[1]) + dacc_get(G[2]);
+    }
+    const df64 g00 = dacc_get(G[0]), g11 = dacc_get(G[1]), g22 = dacc_get(G[2]);
+    df64 fa[8];
+    fa[0] = df_ldexp(dacc_get(G[3]), 2);
+    fa[1] = -df_ldexp(dacc_get(G[4]), 2);
+    fa[2] = df_ldexp(g00 - g11, 1);
+    fa[3] = df_ldexp(dacc_get(G[5]), 2);
+    fa[4] = -df_ldexp(dacc_get(G[6]), 2);
+    fa[5] = df_ldexp(dacc_get(G[7]), 2);
+    fa[6] = -df_ldexp(dacc_get(G[8]), 2);
+    fa[7] = df_ldexp(df_const(0.57735026918962576451) * (g00 + g11 - df_ldexp(g22, 1)), 1);
+    ok = ok && isfinite(un);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      f[(size_t)a * g.V + s] = make_float2(fa[a].hi, fa[a].lo);
+      s_abs = s_abs + (fa[a].hi < 0.0f ? -fa[a] : fa[a]);
+      s_sq = fma(fa[a], fa[a], s_sq);
+      ok = ok && isfinite(fa[a]);
+    }
+    s_un = s_un + un;
+    bad += ok ? 0 : 1;
+  }
+  v[0] = (double)s_abs;
+  v[1] = (double)s_sq;
+  v[2] = (double)s_un * (1.0 / 3.0);
+  v[3] = (double)bad;
+}
+
 // f_ax = 2 Tr[lambda_a G_x], G_x = sum_mu (U_{x,mu} U_{x,mu}^+ - U_{x-mu,mu}^+ U_{x-mu,mu})
 // (Sec. 2, eq. "eq:24"); per block: sum |f|, sum f^2, sum (1/3) Tr U U^+ of
 // the links at x, nonfinite count.
@@ -233,67 +371,71 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename
                                                           const CoolState* cs) {
   if (cs && cs->done) return;
   double v[NQ_COOL] = {0.0, 0.0, 0.0, 0.0};
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
-    int x[4];
-    site_coords(g, s, x);
-    T g00 = T(0), g11 = T(0), g22 = T(0);
-    cx<T> g01 = {T(0), T(0)}, g02 = {T(0), T(0)}, g12 = {T(0), T(0)};
+  if constexpr (std::is_same<T, df64>::value) {
+    cool_grad_df(g, U, reinterpret_cast<float2*>(f), v);
+  } else {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+      int x[4];
+      site_coords(g, s, x);
+      T g00 = T(0), g11 = T(0), g22 = T(0);
+      cx<T> g01 = {T(0), T(0)}, g02 = {T(0), T(0)}, g12 = {T(0), T(0)};
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      mat<T> u;
-      load(u, U, mu, s, g.V);
-      // + U U^+ : (i,j) = sum_k U_ik conj(U_jk)
+      for (int mu = 0; mu < 4; ++mu) {
+        mat<T> u;
+        load(u, U, mu, s, g.V);
+        // + U U^+ : (i,j) = sum_k U_ik conj(U_jk)
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        cx<T> r0 = u.e[k], r1 = u.e[3 + k], r2 = u.e[6 + k];
-        g00 = fma(r0.re, r0.re, fma(r0.im, r0.im, g00));
-        g11 = fma(r1.re, r1.re, fma(r1.im, r1.im, g11));
-        g22 = fma(r2.re, r2.re, fma(r2.im, r2.im, g22));
-        g01 = cfma(r0, cx<T>{r1.re, -r1.im}, g01);
-        g02 = cfma(r0, cx<T>{r2.re, -r2.im}, g02);
-        g12 = cfma(r1, cx<T>{r2.re, -r2.im}, g12);
+        for (int k = 0; k < 3; ++k) {
+          cx<T> r0 = u.e[k], r1 = u.e[3 + k], r2 = u.e[6 + k];
+          g00 = fma(r0.re, r0.re, fma(r0.im, r0.im, g00));
+          g11 = fma(r1.re, r1.re, fma(r1.im, r1.im, g11));
+          g22 = fma(r2.re, r2.re, fma(r2.im, r2.im, g22));
+          g01 = cfma(r0, cx<T>{r1.re, -r1.im}, g01);
+          g02 = cfma(r0, cx<T>{r2.re, -r2.im}, g02);
+          g12 = cfma(r1, cx<T>{r2.re, -r2.im}, g12);
+        }
       }
-    }
-    // sum over the four links at x of Tr U U^+ = the diagonal accumulated so far
-    const T un = g00 + g11 + g22;
+      // sum over the four links at x of Tr U U^+ = the diagonal accumulated so far
+      const T un = g00 + g11 + g22;
 #pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      mat<T> u;
-      load(u, U, mu, hop(g, s, x, mu, -1), g.V);
-      // - U^+ U : (i,j) = sum_k conj(U_ki) U_kj
+      for (int mu = 0; mu < 4; ++mu) {
+        mat<T> u;
+        load(u, U, mu, hop(g, s, x, mu, -1), g.V);
+        // - U^+ U : (i,j) = sum_k conj(U_ki) U_kj
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        cx<T> c0 = u.e[3 * k], c1 = u.e[3 * k + 1], c2 = u.e[3 * k + 2];
-        g00 = fma(-c0.re, c0.re, fma(-c0.im, c0.im, g00));
-        g11 = fma(-c1.re, c1.re, fma(-c1.im, c1.im, g11));
-        g22 = fma(-c2.re, c2.re, fma(-c2.im, c2.im, g22));
-        g01 = cfms(cx<T>{c0.re, -c0.im}, c1, g01);
-        g02 = cfms(cx<T>{c0.re, -c0.im}, c2, g02);
-        g12 = cfms(cx<T>{c1.re, -c1.im}, c2, g12);
+        for (int k = 0; k < 3; ++k) {
+          cx<T> c0 = u.e[3 * k], c1 = u.e[3 * k + 1], c2 = u.e[3 * k + 2];
+          g00 = fma(-c0.re, c0.re, fma(-c0.im, c0.im, g00));
+          g11 = fma(-c1.re, c1.re, fma(-c1.im, c1.im, g11));
+          g22 = fma(-c2.re, c2.re, fma(-c2.im, c2.im, g22));
+          g01 = cfms(cx<T>{c0.re, -c0.im}, c1, g01);
+          g02 = cfms(cx<T>{c0.re, -c0.im}, c2, g02);
+          g12 = cfms(cx<T>{c1.re, -c1.im}, c2, g12);
+        }
       }
-    }
-    const T r3 = (T)0.57735026918962576451;
-    T fa[8];
-    const T two = T(2), four = T(4);
-    fa[0] = four * g01.re;
-    fa[1] = -(four * g01.im);
-    fa[2] = two * (g00 - g11);
-    fa[3] = four * g02.re;
-    fa[4] = -(four * g02.im);
-    fa[5] = four * g12.re;
-    fa[6] = -(four * g12.im);
-    fa[7] = two * r3 * (g00 + g11 - two * g22);
-    bool ok = isfinite(un);
+      const T r3 = (T)0.57735026918962576451;
+      T fa[8];
+      const T two = T(2), four = T(4);
+      fa[0] = four * g01.re;
+      fa[1] = -(four * g01.im);
+      fa[2] = two * (g00 - g11);
+      fa[3] = four * g02.re;
+      fa[4] = -(four * g02.im);
+      fa[5] = four * g12.re;
+      fa[6] = -(four * g12.im);
+      fa[7] = two * r3 * (g00 + g11 - two * g22);
+      bool ok = isfinite(un);
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const double d = (double)fa[a];
-      f[(size_t)a * g.V + s] = d;
-      v[0] += fabs(d);
-      v[1] = fma(d, d, v[1]);
-      ok = ok && isfinite(fa[a]);
+      for (int a = 0; a < 8; ++a) {
+        const double d = (double)fa[a];
+        f[(size_t)a * g.V + s] = d;
+        v[0] += fabs(d);
+        v[1] = fma(d, d, v[1]);
+        ok = ok && isfinite(fa[a]);
+      }
+      v[2] += (double)un * (1.0 / 3.0);
+      v[3] += ok ? 0.0 : 1.0;
     }
-    v[2] += (double)un * (1.0 / 3.0);
-    v[3] += ok ? 0.0 : 1.0;
   }
   block_reduce_store<NQ_COOL, -1>(v, partials);
 }
@@ -362,13 +504,28 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_omega(Geo g, const doub
   if (cs->done) return;
   int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
-  double fa[8];
+  if constexpr (std::is_same<T, df64>::value) {
+    // DF64: f as hi + lo pairs, the exponential pair in double-float
+    const float2* fp = reinterpret_cast<const float2*>(f);
+    df64 fa[8];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) fa[a] = __ldg(f + (size_t)a * g.V + s);
-  herm h = herm_from_algebra(fa, -eps * cs->alpha_ad), om, omi;
-  expm_hermitian_pair(om, omi, h);
-  store_herm(Om, s, g.V, om);
-  store_herm(Omi, s, g.V, omi);
+    for (int a = 0; a < 8; ++a) {
+      const float2 w = __ldg(fp + (size_t)a * g.V + s);
+      fa[a] = df64(w.x, w.y);
+    }
+    herm_df h = herm_from_algebra_df(fa, df64(-eps * cs->alpha_ad)), om, omi;
+    expm_hermitian_pair_df(om, omi, h);
+    store_herm_df(Om, s, g.V, om);
+    store_herm_df(Omi, s, g.V, omi);
+  } else {
+    double fa[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) fa[a] = __ldg(f + (size_t)a * g.V + s);
+    herm h = herm_from_algebra(fa, -eps * cs->alpha_ad), om, omi;
+    expm_hermitian_pair(om, omi, h);
+    store_herm(Om, s, g.V, om);
+    store_herm(Omi, s, g.V, omi);
+  }
 }
 
 // U_{x,mu} <- Omega_x U_{x,mu} Omega_{x+mu}^{-1}, all links at once (in place:
@@ -387,8 +544,13 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_apply(Geo g, typename v
   load_herm_mat(o, Om, s, g.V);
   load_herm_mat(oi, Omi, hop(g, s, x, mu, 1), g.V);
   load(u, U, mu, s, g.V);
-  mul_herm_left(t, o, u);
-  mul_herm_right(u, t, oi);
+  if constexpr (std::is_same<T, df64>::value) {
+    mul_herm_left_df(t, o, u);
+    mul_herm_right_df(u, t, oi);
+  } else {
+    mul_herm_left(t, o, u);
+    mul_herm_right(u, t, oi);
+  }
   store(U, mu, s, g.V, u);
 }
 
@@ -547,6 +709,15 @@ cudaError_t launch_soa_to_aos(int prec, const GeoH& h, const void* U, double* ao
   return by_prec(prec, [&](auto t) {
     using T = decltype(t);
     k_soa_to_aos<T><<<blocks, 256, 0, st>>>(g, (const typename vec2_of<T>::type*)U, aos, nplanes);
+  });
+}
+
+cudaError_t launch_noise_sample(int prec, int site0, int n, uint64_t seed, uint32_t step, int mu, double* out,
+                                cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  return by_prec(prec, [&](auto t) {
+    using T = decltype(t);
+    k_noise_sample<T><<<(n + 127) / 128, 128, 0, st>>>(site0, n, seed, step, (uint32_t)mu, out);
   });
 }
 

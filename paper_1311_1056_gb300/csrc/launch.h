@@ -73,6 +73,11 @@ cudaError_t launch_soa_to_aos(int prec, const GeoH& g, const void* U, double* ao
 // the per-plaquette drift contributions C (24 planes: 4 links x 6 planes);
 // then per link the gather of its six contributions followed by the update
 // (mode 0) or by storing the drift matrix X_S (mode 1).
+// Lets the double-float link-algebra kernels take their shared-memory matrix
+// workspace (up to 5 x 144 B per thread); called before the first DF64 launch.
+cudaError_t prepare_df64_kernels();
+cudaError_t launch_noise_sample(int prec, int site0, int n, uint64_t seed, uint32_t step, int mu, double* out,
+                                cudaStream_t st);
 cudaError_t launch_link_inverse(int prec, const GeoH& g, const void* U, void* Ui, cudaStream_t st);
 cudaError_t launch_plaq(int prec, const GeoH& g, const void* U, const void* Ui, void* Pq, void* Dq,
                         cudaStream_t st);

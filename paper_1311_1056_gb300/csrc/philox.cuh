@@ -14,6 +14,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "df64.cuh"
+
 namespace clgc {
 
 enum { STREAM_CL = 0, STREAM_GAUGE = 1, STREAM_HOT = 2 };
@@ -52,6 +54,35 @@ __device__ __forceinline__ void normals_f64(double* g, uint64_t seed, uint32_t s
     double rad = sqrt(-2.0 * log(u1));
     double s, c;
     sincospi(2.0 * u2, &s, &c);
+    g[2 * j] = rad * c;
+    g[2 * j + 1] = rad * s;
+  }
+}
+
+// The 52-bit uniform (k + 1/2) 2^-52 in double-float from three exact float
+// pieces: bits 51..28 of k, bits 27..4, and bits 3..0 plus the half.
+__device__ __forceinline__ df64 uniform52_df(uint32_t hi, uint32_t lo) {
+  const uint32_t h = hi >> 6, l = lo >> 6;  // k = h 2^26 + l
+  const float A = (float)(h >> 2) * 5.9604644775390625e-8f;                                // 2^-24
+  const float B = (float)(((h & 3u) << 22) | (l >> 4)) * 3.5527136788005009e-15f;         // 2^-48
+  const float C = ((float)(l & 15u) + 0.5f) * 2.220446049250313080847e-16f;              // 2^-52
+  return df_two_sum(A, B) + df64(C, 0.0f);
+}
+
+// The same numbers in double-float (~2^-46 relative), with no FP64
+// instruction: ln, sqrt and sincospi of df64.cuh.  Used by the DF64 form.
+template <int NP>
+__device__ __forceinline__ void normals_df64(df64* g, uint64_t seed, uint32_t step, uint32_t site,
+                                             uint32_t slot, uint32_t stream) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    uint4 w = philox_words(seed, step, site, slot, stream, (uint32_t)j);
+    // 1 - u1 = (k' + 1/2) 2^-52 with k' the 52-bit complement of k: exact
+    const df64 u1 = uniform52_df(w.x, w.y), v1 = uniform52_df(~w.x, ~w.y);
+    const df64 u2 = uniform52_df(w.z, w.w);
+    const df64 rad = df_sqrt(df_ldexp(-df_log_unit(u1, v1), 1));
+    df64 s, c;
+    df_sincospi(df_ldexp(u2, 1), &s, &c);
     g[2 * j] = rad * c;
     g[2 * j + 1] = rad * s;
   }

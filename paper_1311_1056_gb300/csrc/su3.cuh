@@ -21,9 +21,41 @@ struct cx {
   T re, im;
 };
 
+// A double-float complex entry is one 16-byte vector (re.hi, re.lo, im.hi,
+// im.lo): aligned so that it moves with one 128-bit load or store.
+template <>
+struct alignas(16) cx<df64> {
+  df64 re, im;
+};
+
 template <typename T>
 struct mat {
   cx<T> e[9];
+};
+
+// The 3x3 matrices a kernel works on.  FP64 and FP32: plain locals, which the
+// compiler keeps in registers.  Double-float: the out-of-line products take
+// their operands by address, which would place every matrix of the kernel in
+// the per-thread stack (local memory); with hundreds of threads per SM that
+// stack outgrows L1 and its dirty lines reach DRAM.  The slots live in
+// dynamic shared memory instead, 144 bytes per slot and thread: slot i of
+// thread t at mat index (first + i) * blockDim.x + t.  144 bytes is an odd
+// multiple of 16, so the 16-byte accesses of a quarter warp to the same
+// entry of consecutive threads' slots hit distinct banks.
+template <typename T, int N>
+struct Work {
+  mat<T> m[N];
+  __device__ __forceinline__ explicit Work(int) {}
+  __device__ __forceinline__ mat<T>& operator[](int i) { return m[i]; }
+};
+template <int N>
+struct Work<df64, N> {
+  mat<df64>* base;
+  __device__ __forceinline__ explicit Work(int first) {
+    extern __shared__ mat<df64> df_work_slots[];
+    base = df_work_slots + first * blockDim.x + threadIdx.x;
+  }
+  __device__ __forceinline__ mat<df64>& operator[](int i) { return base[i * blockDim.x]; }
 };
 
 template <typename T> struct vec2_of;
@@ -158,8 +190,9 @@ __device__ __forceinline__ void mul_herm_right(mat<T>& c, const mat<T>& u, const
 // Double-float products as out-of-line functions.  Inlined, one double-float
 // 3x3 product is ~1,400 instructions and the force kernels no longer fit the
 // instruction cache (the warps then wait on instruction fetch); called, every
-// product site shares one body and the operands travel through the (L1-
-// resident) stack.  The FP64 and FP32 forms keep their inlined products.
+// product site shares one body and takes its operands by address (in the
+// kernels' shared-memory workspace, Work above).  The FP64 and FP32 forms
+// keep their inlined products.
 static __device__ __noinline__ void mul_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b);
 static __device__ __noinline__ void mul_acc_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b, int sign);
 template <>
@@ -174,15 +207,107 @@ template <>
 __device__ __forceinline__ void mul_acc<-1, df64>(mat<df64>& c, const mat<df64>& a, const mat<df64>& b) {
   mul_acc_df(c, a, b, -1);
 }
+// One entry of a double-float product, sum_k x_k y_k over its six real terms
+// (three complex products), accumulated as in the Dot2 algorithm of Ogita,
+// Rump and Oishi (SIAM J. Sci. Comput. 26, 2005): each term split exactly
+// into p + e (FMA), the p's summed by Knuth's two-sum into s, every rounding
+// error and every e gathered in one float lo, and s + lo renormalised once at
+// the end.  The dependency chain through s is one add per term, so the terms
+// of the real and the imaginary part overlap instead of waiting on a
+// renormalised accumulator (~9 dependent operations per double-float FMA);
+// the result carries ~2^-48 of sum |term|, as the chained form does.
+struct dacc {
+  float s, lo;
+};
+__device__ __forceinline__ void dacc_prod_terms(float& p, float& e, df64 x, df64 y) {
+  p = __fmul_rn(x.hi, y.hi);
+  e = fmaf(x.hi, y.hi, -p);
+  e = fmaf(x.hi, y.lo, e);
+  e = fmaf(x.lo, y.hi, e);
+}
+__device__ __forceinline__ dacc dacc_first(df64 x, df64 y) {
+  dacc a;
+  dacc_prod_terms(a.s, a.lo, x, y);
+  return a;
+}
+__device__ __forceinline__ void dacc_add(dacc& a, df64 x, df64 y) {
+  float p, e;
+  dacc_prod_terms(p, e, x, y);
+  const float t = a.s + p;
+  const float bb = t - a.s;
+  const float err = (a.s - (t - bb)) + (p - bb);
+  a.s = t;
+  a.lo += err + e;
+}
+__device__ __forceinline__ df64 dacc_get(const dacc& a) { return df_two_sum(a.s, a.lo); }
+// Folds lo back into s; over long sums (the cooling gradient's 48 terms per
+// entry) this every few terms keeps lo, and so its own rounding, small.
+__device__ __forceinline__ void dacc_norm(dacc& a) {
+  const df64 t = df_two_sum(a.s, a.lo);
+  a.s = t.hi;
+  a.lo = t.lo;
+}
+
+// c = h u and c = u h for Hermitian h in double-float: five real terms per
+// part of each entry, accumulated as above (inlined: the cooling apply has
+// no other product).
+__device__ __forceinline__ void mul_herm_left_df(mat<df64>& c, const mat<df64>& h, const mat<df64>& u) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const df64 d = h.e[4 * i].re;
+      dacc re = dacc_first(d, u.e[3 * i + j].re), im = dacc_first(d, u.e[3 * i + j].im);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k != i) {
+          const cx<df64> x = h.e[3 * i + k], y = u.e[3 * k + j];
+          dacc_add(re, x.re, y.re);
+          dacc_add(re, -x.im, y.im);
+          dacc_add(im, x.re, y.im);
+          dacc_add(im, x.im, y.re);
+        }
+      c.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
+    }
+}
+__device__ __forceinline__ void mul_herm_right_df(mat<df64>& c, const mat<df64>& u, const mat<df64>& h) {
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const df64 d = h.e[4 * j].re;
+      dacc re = dacc_first(d, u.e[3 * i + j].re), im = dacc_first(d, u.e[3 * i + j].im);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k != j) {
+          const cx<df64> x = u.e[3 * i + k], y = h.e[3 * k + j];
+          dacc_add(re, x.re, y.re);
+          dacc_add(re, -x.im, y.im);
+          dacc_add(im, x.re, y.im);
+          dacc_add(im, x.im, y.re);
+        }
+      c.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
+    }
+}
+
 static __device__ __noinline__ void mul_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b) {
 #pragma unroll 1
   for (int i = 0; i < 3; ++i)  // rolled: one entry's code in the instruction cache
 #pragma unroll 1
     for (int j = 0; j < 3; ++j) {
-      cx<df64> s = cmul(a.e[3 * i], b.e[j]);
-      s = cfma(a.e[3 * i + 1], b.e[3 + j], s);
-      s = cfma(a.e[3 * i + 2], b.e[6 + j], s);
-      c.e[3 * i + j] = s;
+      const cx<df64> x0 = a.e[3 * i], y0 = b.e[j];
+      dacc re = dacc_first(x0.re, y0.re), im = dacc_first(x0.re, y0.im);
+      dacc_add(re, -x0.im, y0.im);
+      dacc_add(im, x0.im, y0.re);
+#pragma unroll
+      for (int k = 1; k < 3; ++k) {
+        const cx<df64> x = a.e[3 * i + k], y = b.e[3 * k + j];
+        dacc_add(re, x.re, y.re);
+        dacc_add(re, -x.im, y.im);
+        dacc_add(im, x.re, y.im);
+        dacc_add(im, x.im, y.re);
+      }
+      c.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
     }
 }
 static __device__ __noinline__ void mul_acc_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b, int sign) {
@@ -190,11 +315,19 @@ static __device__ __noinline__ void mul_acc_df(mat<df64>& c, const mat<df64>& a,
   for (int i = 0; i < 3; ++i)
 #pragma unroll 1
     for (int j = 0; j < 3; ++j) {
-      cx<df64> s = c.e[3 * i + j];
+      const cx<df64> c0 = c.e[3 * i + j];
+      dacc re = {c0.re.hi, c0.re.lo}, im = {c0.im.hi, c0.im.lo};
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        s = sign > 0 ? cfma(a.e[3 * i + k], b.e[3 * k + j], s) : cfms(a.e[3 * i + k], b.e[3 * k + j], s);
-      c.e[3 * i + j] = s;
+      for (int k = 0; k < 3; ++k) {
+        cx<df64> x = a.e[3 * i + k];
+        if (sign < 0) x = cx<df64>{-x.re, -x.im};
+        const cx<df64> y = b.e[3 * k + j];
+        dacc_add(re, x.re, y.re);
+        dacc_add(re, -x.im, y.im);
+        dacc_add(im, x.re, y.im);
+        dacc_add(im, x.im, y.re);
+      }
+      c.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
     }
 }
 

@@ -41,6 +41,11 @@ def test_invalid_arguments_fail_without_device_work():
     assert "extent" in cl.cl_last_error()
     with pytest.raises(cl.CLError):
         cl.cl_step(None, 0.01, 1)
+    for args in ((7, 1, 0, 0, 0, 4), (cl.CL_DF64, 1, 0, 4, 0, 4), (cl.CL_FP64, 1, 0, 0, -1, 4),
+                 (cl.CL_FP64, 1, 0, 0, 0, -2)):  # precision, direction, site range
+        with pytest.raises(cl.CLError) as e:
+            cl.noise_sample(*args)
+        assert e.value.status == cl.CL_ERR_INVALID
 
 
 def test_struct_layouts_match_the_header(tmp_path):
