@@ -133,9 +133,10 @@ __device__ __forceinline__ void expm_traceless(mat<T>& E, const mat<T>& A, float
 }
 
 // The same exponential entirely in double-float (the DF64 form): the scalar
-// recurrences too, with the coefficients of c_invfact_df.
-__device__ __forceinline__ void expm_traceless_df(mat<df64>& E, const mat<df64>& A) {
-  mat<df64> A2;
+// recurrences too, with the coefficients of c_invfact_df.  A2 is the
+// caller's workspace for A^2; E may be A itself (E is formed entry by entry
+// from the same entries of A and A^2).
+__device__ __forceinline__ void expm_traceless_df(mat<df64>& E, const mat<df64>& A, mat<df64>& A2) {
   mul(A2, A, A);
   const cx<df64> t1 = trace(A2), t0 = trace_mul(A2, A);
   const df64 third = df_const(1.0 / 3.0);

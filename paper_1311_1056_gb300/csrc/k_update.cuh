@@ -436,7 +436,8 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const t
   const int s = s_raw < g.V ? s_raw : g.V - 1;
   int x[4];
   site_coords(g, s, x);
-  mat<T> X, t;
+  Work<T, 2> ws(0);
+  mat<T>&X = ws[0], &t = ws[1];
   if (MODE == MODE_UPDATE_X) {
     load(X, C, MU, s, g.V);  // the drift stored by the MODE_DRIFTMAX pass
   } else {
@@ -489,8 +490,11 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const t
     df64 eta[8];
     normals_df64<4>(eta, a.seed, step, (uint32_t)s, (uint32_t)MU, STREAM_CL);
     exponent<df64>(X, eta, df64(eps), df64(sqrt_eps));
-    mat<df64> E, Ul, Un;
-    expm_traceless_df(E, X);
+    // three workspace slots: E overwrites X (entry by entry), the link U
+    // takes the slot of X^2 once E is formed
+    Work<df64, 1> wu(2);
+    mat<df64>&E = X, &Ul = t, &Un = wu[0];
+    expm_traceless_df(E, X, t);
     load(Ul, U, MU, s, g.V);
     mul(Un, E, Ul);
     const cx<df64> z = det_inv_cuberoot_df(det(Un));

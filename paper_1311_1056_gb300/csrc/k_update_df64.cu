@@ -18,7 +18,7 @@ inline df64 df_host(double d) {
 inline dim3 grid(int V, int planes, int bs) { return dim3((unsigned)(((V + bs - 1) / bs) * planes)); }
 // dynamic shared memory of a kernel with nslot workspace matrices per thread
 inline size_t ws_bytes(int nslot, int bs) { return (size_t)nslot * sizeof(mat<df64>) * (size_t)bs; }
-const int NSLOT_PLAQ = 5, NSLOT_CLOVER = 4, NSLOT_WILSON = 4, NSLOT_FORCE = 5;
+const int NSLOT_PLAQ = 5, NSLOT_CLOVER = 4, NSLOT_WILSON = 4, NSLOT_FORCE = 5, NSLOT_UPDATE = 3;
 
 template <typename K>
 cudaError_t allow_ws(K kernel, int nslot) {
@@ -37,6 +37,10 @@ cudaError_t prepare_df64_kernels() {
   if (e == cudaSuccess) e = allow_ws(k_plaq_force_wilson<df64>, NSLOT_WILSON);
   if (e == cudaSuccess) e = allow_ws(k_plaq_force_a<df64>, NSLOT_FORCE);
   if (e == cudaSuccess) e = allow_ws(k_plaq_force_b<df64>, NSLOT_FORCE);
+  if (e == cudaSuccess) e = allow_ws(k_update_gather<df64, MODE_UPDATE>, NSLOT_UPDATE);
+  if (e == cudaSuccess) e = allow_ws(k_update_gather<df64, MODE_DRIFT>, NSLOT_UPDATE);
+  if (e == cudaSuccess) e = allow_ws(k_update_gather<df64, MODE_DRIFTMAX>, NSLOT_UPDATE);
+  if (e == cudaSuccess) e = allow_ws(k_update_gather<df64, MODE_UPDATE_X>, NSLOT_UPDATE);
   return e;
 }
 
@@ -93,14 +97,15 @@ cudaError_t launch_update_gather_df64(int mode, const GeoH& h, const void* U, co
   a.adaptive = adaptive ? 1 : 0;
   const int bs = block_of(h, TUNE_UPDATE);
   const dim3 gr = grid(g.V, 4, bs);
+  const size_t sm = ws_bytes(NSLOT_UPDATE, bs);
   const V2* u = (const V2*)U;
   const V2* c = (const V2*)C;
   V2* o = (V2*)out;
   switch (mode) {
-    case MODE_DRIFT: k_update_gather<df64, MODE_DRIFT><<<gr, bs, 0, st>>>(g, u, c, o, a); break;
-    case MODE_DRIFTMAX: k_update_gather<df64, MODE_DRIFTMAX><<<gr, bs, 0, st>>>(g, u, c, o, a); break;
-    case MODE_UPDATE_X: k_update_gather<df64, MODE_UPDATE_X><<<gr, bs, 0, st>>>(g, u, c, o, a); break;
-    default: k_update_gather<df64, MODE_UPDATE><<<gr, bs, 0, st>>>(g, u, c, o, a); break;
+    case MODE_DRIFT: k_update_gather<df64, MODE_DRIFT><<<gr, bs, sm, st>>>(g, u, c, o, a); break;
+    case MODE_DRIFTMAX: k_update_gather<df64, MODE_DRIFTMAX><<<gr, bs, sm, st>>>(g, u, c, o, a); break;
+    case MODE_UPDATE_X: k_update_gather<df64, MODE_UPDATE_X><<<gr, bs, sm, st>>>(g, u, c, o, a); break;
+    default: k_update_gather<df64, MODE_UPDATE><<<gr, bs, sm, st>>>(g, u, c, o, a); break;
   }
   return cudaGetLastError();
 }

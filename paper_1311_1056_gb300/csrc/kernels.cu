@@ -306,13 +306,15 @@ __device__ __forceinline__ void cool_grad_df(const Geo& g, const float4* __restr
     for (int dir = 0; dir < 2; ++dir) {
 #pragma unroll
       for (int mu = 0; mu < 4; ++mu) {
-        mat<df64> u;
-        load(u, U, mu, dir == 0 ? s : hop(g, s, x, mu, -1), g.V);
+        // entry e of the link at p[e V]; three entries at a time keep the
+        // registers for one more resident block
+        const float4* p = U + (size_t)mu * 9 * g.V + (dir == 0 ? s : hop(g, s, x, mu, -1));
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          // + U U^+ (rows of the forward link), - U^+ U (columns of the backward link)
-          const cx<df64> r0 = dir == 0 ? u.e[k] : u.e[3 * k], r1 = dir == 0 ? u.e[3 + k] : u.e[3 * k + 1],
-                         r2 = dir == 0 ? u.e[6 + k] : u.e[3 * k + 2];
+          // + U U^+: column k of the forward link; - U^+ U: row k of the backward link
+          const int e0 = dir == 0 ? k : 3 * k, e1 = dir == 0 ? 3 + k : 3 * k + 1, e2 = dir == 0 ? 6 + k : 3 * k + 2;
+          const cx<df64> r0 = unpack(__ldg(p + (size_t)e0 * g.V)), r1 = unpack(__ldg(p + (size_t)e1 * g.V)),
+                         r2 = unpack(__ldg(p + (size_t)e2 * g.V));
           const bool neg = dir == 1;
           dacc_add_abs2(G[0], r0, neg);
           dacc_add_abs2(G[1], r1, neg);
@@ -371,71 +373,67 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename
                                                           const CoolState* cs) {
   if (cs && cs->done) return;
   double v[NQ_COOL] = {0.0, 0.0, 0.0, 0.0};
-  if constexpr (std::is_same<T, df64>::value) {
-    cool_grad_df(g, U, reinterpret_cast<float2*>(f), v);
-  } else {
-    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
-      int x[4];
-      site_coords(g, s, x);
-      T g00 = T(0), g11 = T(0), g22 = T(0);
-      cx<T> g01 = {T(0), T(0)}, g02 = {T(0), T(0)}, g12 = {T(0), T(0)};
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    int x[4];
+    site_coords(g, s, x);
+    T g00 = T(0), g11 = T(0), g22 = T(0);
+    cx<T> g01 = {T(0), T(0)}, g02 = {T(0), T(0)}, g12 = {T(0), T(0)};
 #pragma unroll
-      for (int mu = 0; mu < 4; ++mu) {
-        mat<T> u;
-        load(u, U, mu, s, g.V);
-        // + U U^+ : (i,j) = sum_k U_ik conj(U_jk)
+    for (int mu = 0; mu < 4; ++mu) {
+      mat<T> u;
+      load(u, U, mu, s, g.V);
+      // + U U^+ : (i,j) = sum_k U_ik conj(U_jk)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          cx<T> r0 = u.e[k], r1 = u.e[3 + k], r2 = u.e[6 + k];
-          g00 = fma(r0.re, r0.re, fma(r0.im, r0.im, g00));
-          g11 = fma(r1.re, r1.re, fma(r1.im, r1.im, g11));
-          g22 = fma(r2.re, r2.re, fma(r2.im, r2.im, g22));
-          g01 = cfma(r0, cx<T>{r1.re, -r1.im}, g01);
-          g02 = cfma(r0, cx<T>{r2.re, -r2.im}, g02);
-          g12 = cfma(r1, cx<T>{r2.re, -r2.im}, g12);
-        }
+      for (int k = 0; k < 3; ++k) {
+        cx<T> r0 = u.e[k], r1 = u.e[3 + k], r2 = u.e[6 + k];
+        g00 = fma(r0.re, r0.re, fma(r0.im, r0.im, g00));
+        g11 = fma(r1.re, r1.re, fma(r1.im, r1.im, g11));
+        g22 = fma(r2.re, r2.re, fma(r2.im, r2.im, g22));
+        g01 = cfma(r0, cx<T>{r1.re, -r1.im}, g01);
+        g02 = cfma(r0, cx<T>{r2.re, -r2.im}, g02);
+        g12 = cfma(r1, cx<T>{r2.re, -r2.im}, g12);
       }
-      // sum over the four links at x of Tr U U^+ = the diagonal accumulated so far
-      const T un = g00 + g11 + g22;
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) {
-        mat<T> u;
-        load(u, U, mu, hop(g, s, x, mu, -1), g.V);
-        // - U^+ U : (i,j) = sum_k conj(U_ki) U_kj
-#pragma unroll
-        for (int k = 0; k < 3; ++k) {
-          cx<T> c0 = u.e[3 * k], c1 = u.e[3 * k + 1], c2 = u.e[3 * k + 2];
-          g00 = fma(-c0.re, c0.re, fma(-c0.im, c0.im, g00));
-          g11 = fma(-c1.re, c1.re, fma(-c1.im, c1.im, g11));
-          g22 = fma(-c2.re, c2.re, fma(-c2.im, c2.im, g22));
-          g01 = cfms(cx<T>{c0.re, -c0.im}, c1, g01);
-          g02 = cfms(cx<T>{c0.re, -c0.im}, c2, g02);
-          g12 = cfms(cx<T>{c1.re, -c1.im}, c2, g12);
-        }
-      }
-      const T r3 = (T)0.57735026918962576451;
-      T fa[8];
-      const T two = T(2), four = T(4);
-      fa[0] = four * g01.re;
-      fa[1] = -(four * g01.im);
-      fa[2] = two * (g00 - g11);
-      fa[3] = four * g02.re;
-      fa[4] = -(four * g02.im);
-      fa[5] = four * g12.re;
-      fa[6] = -(four * g12.im);
-      fa[7] = two * r3 * (g00 + g11 - two * g22);
-      bool ok = isfinite(un);
-#pragma unroll
-      for (int a = 0; a < 8; ++a) {
-        const double d = (double)fa[a];
-        f[(size_t)a * g.V + s] = d;
-        v[0] += fabs(d);
-        v[1] = fma(d, d, v[1]);
-        ok = ok && isfinite(fa[a]);
-      }
-      v[2] += (double)un * (1.0 / 3.0);
-      v[3] += ok ? 0.0 : 1.0;
     }
+    // sum over the four links at x of Tr U U^+ = the diagonal accumulated so far
+    const T un = g00 + g11 + g22;
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      mat<T> u;
+      load(u, U, mu, hop(g, s, x, mu, -1), g.V);
+      // - U^+ U : (i,j) = sum_k conj(U_ki) U_kj
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        cx<T> c0 = u.e[3 * k], c1 = u.e[3 * k + 1], c2 = u.e[3 * k + 2];
+        g00 = fma(-c0.re, c0.re, fma(-c0.im, c0.im, g00));
+        g11 = fma(-c1.re, c1.re, fma(-c1.im, c1.im, g11));
+        g22 = fma(-c2.re, c2.re, fma(-c2.im, c2.im, g22));
+        g01 = cfms(cx<T>{c0.re, -c0.im}, c1, g01);
+        g02 = cfms(cx<T>{c0.re, -c0.im}, c2, g02);
+        g12 = cfms(cx<T>{c1.re, -c1.im}, c2, g12);
+      }
+    }
+    const T r3 = (T)0.57735026918962576451;
+    T fa[8];
+    const T two = T(2), four = T(4);
+    fa[0] = four * g01.re;
+    fa[1] = -(four * g01.im);
+    fa[2] = two * (g00 - g11);
+    fa[3] = four * g02.re;
+    fa[4] = -(four * g02.im);
+    fa[5] = four * g12.re;
+    fa[6] = -(four * g12.im);
+    fa[7] = two * r3 * (g00 + g11 - two * g22);
+    bool ok = isfinite(un);
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const double d = (double)fa[a];
+      f[(size_t)a * g.V + s] = d;
+      v[0] += fabs(d);
+      v[1] = fma(d, d, v[1]);
+      ok = ok && isfinite(fa[a]);
+    }
+    v[2] += (double)un * (1.0 / 3.0);
+    v[3] += ok ? 0.0 : 1.0;
   }
   block_reduce_store<NQ_COOL, -1>(v, partials);
 }
@@ -497,6 +495,17 @@ __global__ void k_cool_adapt(Geo g, const double* partials, int nb, CoolArgs a, 
   cs->un_prev = un;
 }
 
+// The DF64 gradient kernel: its own launch bound, so that the whole
+// reduction grid (8 blocks per SM) is resident in one wave.
+__global__ void __launch_bounds__(RED_THREADS, RED_MAX_BLOCKS / 152) k_cool_grad_df(Geo g, const float4* __restrict__ U,
+                                                                             float2* __restrict__ f, double* partials,
+                                                                             const CoolState* cs) {
+  if (cs && cs->done) return;
+  double v[NQ_COOL] = {0.0, 0.0, 0.0, 0.0};
+  cool_grad_df(g, U, f, v);
+  block_reduce_store<NQ_COOL, -1>(v, partials);
+}
+
 // Omega_x = exp(-eps alpha_ad f_ax lambda_a) and its inverse, FP64.
 template <typename T>
 __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_omega(Geo g, const double* __restrict__ f, T* Om, T* Omi,
@@ -544,14 +553,65 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_apply(Geo g, typename v
   load_herm_mat(o, Om, s, g.V);
   load_herm_mat(oi, Omi, hop(g, s, x, mu, 1), g.V);
   load(u, U, mu, s, g.V);
-  if constexpr (std::is_same<T, df64>::value) {
-    mul_herm_left_df(t, o, u);
-    mul_herm_right_df(u, t, oi);
-  } else {
-    mul_herm_left(t, o, u);
-    mul_herm_right(u, t, oi);
-  }
+  mul_herm_left(t, o, u);
+  mul_herm_right(u, t, oi);
   store(U, mu, s, g.V, u);
+}
+
+const int DF_APPLY_BLOCK = 128;  // the DF64 apply's largest block (its launch bound)
+
+// The DF64 apply: row i of Omega U (five real terms per part of each entry,
+// Dot2-accumulated), then row i of (Omega U) Omega'^{-1}, stored at once; the
+// whole link is read before the first row is written.  (Capping it at 96
+// registers for a fifth block per SM spills and gains nothing.)
+__global__ void __launch_bounds__(DF_APPLY_BLOCK, 4) k_cool_apply_df(Geo g, float4* U, const df64* __restrict__ Om,
+                                                                  const df64* __restrict__ Omi,
+                                                                  const CoolState* cs) {
+  if (cs && cs->done) return;
+  const int mu = blockIdx.x % 4;
+  const int s = (blockIdx.x / 4) * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int x[4];
+  site_coords(g, s, x);
+  mat<df64> o, oi, u;
+  load_herm_mat(o, Om, s, g.V);
+  load_herm_mat(oi, Omi, hop(g, s, x, mu, 1), g.V);
+  load(u, U, mu, s, g.V);
+  float4* p = U + (size_t)mu * 9 * g.V + s;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    cx<df64> t[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {  // t_j = (Omega U)_ij, Omega_ii real
+      const df64 d = o.e[4 * i].re;
+      dacc re = dacc_first(d, u.e[3 * i + j].re), im = dacc_first(d, u.e[3 * i + j].im);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k != i) {
+          const cx<df64> a = o.e[3 * i + k], b = u.e[3 * k + j];
+          dacc_add(re, a.re, b.re);
+          dacc_add(re, -a.im, b.im);
+          dacc_add(im, a.re, b.im);
+          dacc_add(im, a.im, b.re);
+        }
+      t[j] = cx<df64>{dacc_get(re), dacc_get(im)};
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {  // (t Omega'^{-1})_j, Omega'^{-1}_jj real
+      const df64 d = oi.e[4 * j].re;
+      dacc re = dacc_first(t[j].re, d), im = dacc_first(t[j].im, d);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k != j) {
+          const cx<df64> a = t[k], b = oi.e[3 * k + j];
+          dacc_add(re, a.re, b.re);
+          dacc_add(re, -a.im, b.im);
+          dacc_add(im, a.re, b.im);
+          dacc_add(im, a.im, b.re);
+        }
+      p[(size_t)(3 * i + j) * g.V] = pack(cx<df64>{dacc_get(re), dacc_get(im)});
+    }
+  }
 }
 
 // ----------------------------------------------------------- observables
@@ -726,8 +786,11 @@ cudaError_t launch_cool_grad(int prec, const GeoH& h, const void* U, void* f, do
   Geo g = to_geo(h);
   return by_prec(prec, [&](auto t) {
     using T = decltype(t);
-    k_cool_grad<T><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const typename vec2_of<T>::type*)U, (double*)f,
-                                                              partials, cs);
+    if constexpr (std::is_same<T, df64>::value)
+      k_cool_grad_df<<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const float4*)U, (float2*)f, partials, cs);
+    else
+      k_cool_grad<T><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const typename vec2_of<T>::type*)U, (double*)f,
+                                                                partials, cs);
   });
 }
 
@@ -756,7 +819,12 @@ cudaError_t launch_cool_apply(int prec, const GeoH& h, void* U, const void* Om, 
   const dim3 grid((unsigned)(((g.V + bs - 1) / bs) * 4));
   return by_prec(prec, [&](auto t) {
     using T = decltype(t);
-    k_cool_apply<T><<<grid, bs, 0, st>>>(g, (typename vec2_of<T>::type*)U, (const T*)Om, (const T*)Omi, cs);
+    if constexpr (std::is_same<T, df64>::value) {
+      const int b = bs < DF_APPLY_BLOCK ? bs : DF_APPLY_BLOCK;
+      const dim3 gd((unsigned)(((g.V + b - 1) / b) * 4));
+      k_cool_apply_df<<<gd, b, 0, st>>>(g, (float4*)U, (const df64*)Om, (const df64*)Omi, cs);
+    } else
+      k_cool_apply<T><<<grid, bs, 0, st>>>(g, (typename vec2_of<T>::type*)U, (const T*)Om, (const T*)Omi, cs);
   });
 }
 

@@ -248,48 +248,6 @@ __device__ __forceinline__ void dacc_norm(dacc& a) {
   a.lo = t.lo;
 }
 
-// c = h u and c = u h for Hermitian h in double-float: five real terms per
-// part of each entry, accumulated as above (inlined: the cooling apply has
-// no other product).
-__device__ __forceinline__ void mul_herm_left_df(mat<df64>& c, const mat<df64>& h, const mat<df64>& u) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const df64 d = h.e[4 * i].re;
-      dacc re = dacc_first(d, u.e[3 * i + j].re), im = dacc_first(d, u.e[3 * i + j].im);
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (k != i) {
-          const cx<df64> x = h.e[3 * i + k], y = u.e[3 * k + j];
-          dacc_add(re, x.re, y.re);
-          dacc_add(re, -x.im, y.im);
-          dacc_add(im, x.re, y.im);
-          dacc_add(im, x.im, y.re);
-        }
-      c.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
-    }
-}
-__device__ __forceinline__ void mul_herm_right_df(mat<df64>& c, const mat<df64>& u, const mat<df64>& h) {
-#pragma unroll
-  for (int i = 0; i < 3; ++i)
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const df64 d = h.e[4 * j].re;
-      dacc re = dacc_first(d, u.e[3 * i + j].re), im = dacc_first(d, u.e[3 * i + j].im);
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (k != j) {
-          const cx<df64> x = u.e[3 * i + k], y = h.e[3 * k + j];
-          dacc_add(re, x.re, y.re);
-          dacc_add(re, -x.im, y.im);
-          dacc_add(im, x.re, y.im);
-          dacc_add(im, x.im, y.re);
-        }
-      c.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
-    }
-}
-
 static __device__ __noinline__ void mul_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b) {
 #pragma unroll 1
   for (int i = 0; i < 3; ++i)  // rolled: one entry's code in the instruction cache
