@@ -122,6 +122,69 @@ def dram_traffic(kernel, prec):
         return None
 
 
+# Kernels of each roofline family, per form (a family's bytes per launch sum
+# over its kernels: the split force runs a then b once per step).
+TRAFFIC_FAMILIES = {
+    "fp64": {"force": ("k_plaq_force_a<double>", "k_plaq_force_b<double>"),
+             "update": ("k_update_gather<double, 0>",), "cool_apply": ("k_cool_apply<double>",),
+             "cool_grad": ("k_cool_grad<double>",), "cool_omega": ("k_cool_omega<double>",)},
+    "fp32": {"force": ("k_plaq_force_ab<float>",), "update": ("k_update_gather<float, 0>",),
+             "cool_apply": ("k_cool_apply<float>",), "cool_grad": ("k_cool_grad<float>",),
+             "cool_omega": ("k_cool_omega<float>",)},
+    "df64": {"force": ("k_plaq_force_a<df64>", "k_plaq_force_b<df64>"),
+             "update": ("k_update_gather<df64, 0>",), "cool_apply": ("k_cool_apply_df",),
+             "cool_grad": ("k_cool_grad_df",), "cool_omega": ("k_cool_omega<df64>",)},
+}
+
+
+def ingest_ncu(path):
+    """Reads an ncu launch list (--csv, metrics gpu__time_duration.sum and
+    dram__bytes_{read,write}.sum, --kernel-name-base demangled), prints its
+    per-kernel summary as a markdown table and writes the per-launch DRAM bytes
+    of each roofline family to profiles/dram_traffic.json, stamped with the
+    current kernel-source hash."""
+    import csv
+    import re
+    rows = list(csv.reader(line for line in open(path) if line.startswith('"')))
+    hdr, rows = rows[0], rows[1:]
+    col = {h: i for i, h in enumerate(hdr)}
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-6, "nsecond": 1e-6, "us": 1e-3,
+             "usecond": 1e-3, "ms": 1.0, "msecond": 1.0, "s": 1e3, "second": 1e3}
+    launches = {}
+    for r in rows:
+        name = r[col["Kernel Name"]]
+        name = name.split("(clgc::Geo")[0] if "(clgc::Geo" in name else name.split("(")[0]
+        name = re.sub(r"^void ", "", name)
+        for ns in ("(anonymous namespace)::", "<unnamed>::", "unnamed>::", "clgc::"):
+            name = name.replace(ns, "")
+        name = name.strip()
+        d = launches.setdefault(r[col["ID"]], {"name": name})
+        d[r[col["Metric Name"]]] = float(r[col["Metric Value"]].replace(",", "")) * scale[r[col["Metric Unit"]]]
+    agg = {}
+    for d in launches.values():
+        a = agg.setdefault(d["name"], {"n": 0, "ms": 0.0, "rd": 0.0, "wr": 0.0})
+        a["n"] += 1
+        a["ms"] += d.get("gpu__time_duration.sum", 0.0)
+        a["rd"] += d.get("dram__bytes_read.sum", 0.0)
+        a["wr"] += d.get("dram__bytes_write.sum", 0.0)
+    tot = sum(a["ms"] for a in agg.values())
+    print("%d launches, %.1f ms of kernel time" % (len(launches), tot))
+    print("| kernel | launches | total ms | share | ms / launch | DRAM read GB / launch | DRAM write GB / launch |")
+    print("|---|---:|---:|---:|---:|---:|---:|")
+    for n, a in sorted(agg.items(), key=lambda kv: -kv[1]["ms"]):
+        print("| %s | %d | %.2f | %.1f %% | %.3f | %.3f | %.3f |" % (
+            n, a["n"], a["ms"], 100 * a["ms"] / tot, a["ms"] / a["n"], a["rd"] / a["n"] / 1e9, a["wr"] / a["n"] / 1e9))
+    h = kernel_source_hash()
+    out = {"source_hash": h}
+    for form, fams in TRAFFIC_FAMILIES.items():
+        for fam, kernels in fams.items():
+            if all(k in agg for k in kernels):
+                b = sum((agg[k]["rd"] + agg[k]["wr"]) / agg[k]["n"] for k in kernels)
+                out.setdefault(form, {})[fam] = {"bytes_per_launch": b, "source_hash": h}
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as fh:
+        json.dump(out, fh, indent=1)
+
+
 class ClockSampler:
     """nvidia-smi samples (200 ms) during the timed region."""
 
@@ -720,7 +783,11 @@ def main():
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--chains", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--ingest-ncu", metavar="CSV", default=None,
+                    help="summarise an ncu launch list with DRAM bytes and update profiles/dram_traffic.json")
     args = ap.parse_args()
+    if args.ingest_ncu:
+        return ingest_ncu(args.ingest_ncu)
     if args.mode == "batch":
         return batch_mode(args)
     if args.mode == "serve":

@@ -304,8 +304,8 @@ __device__ __forceinline__ void cool_grad_df(const Geo& g, const float4* __restr
     df64 un(0.0f, 0.0f);
 #pragma unroll
     for (int dir = 0; dir < 2; ++dir) {
-#pragma unroll
-      for (int mu = 0; mu < 4; ++mu) {
+#pragma unroll 1
+      for (int mu = 0; mu < 4; ++mu) {  // rolled: unrolled, the code outgrows the instruction cache
         // entry e of the link at p[e V]; three entries at a time keep the
         // registers for one more resident block
         const float4* p = U + (size_t)mu * 9 * g.V + (dir == 0 ? s : hop(g, s, x, mu, -1));
