@@ -74,8 +74,8 @@ __device__ __forceinline__ df64 uniform52_df(uint32_t hi, uint32_t lo) {
 template <int NP>
 __device__ __forceinline__ void normals_df64(df64* g, uint64_t seed, uint32_t step, uint32_t site,
                                              uint32_t slot, uint32_t stream) {
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
+#pragma unroll 1
+  for (int j = 0; j < NP; ++j) {  // rolled: one pair's ~450 instructions, not NP copies, in the instruction cache
     uint4 w = philox_words(seed, step, site, slot, stream, (uint32_t)j);
     // 1 - u1 = (k' + 1/2) 2^-52 with k' the 52-bit complement of k: exact
     const df64 u1 = uniform52_df(w.x, w.y), v1 = uniform52_df(~w.x, ~w.y);
