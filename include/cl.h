@@ -34,10 +34,10 @@
  *    det U = 1 re-projection and every global reduction.  CL_DF64 stores
  *    links as double-float pairs (hi + lo floats, ~48 significant bits) and
  *    does the link algebra (products, inverses, plaquettes, clover, drift,
- *    cooling transformations) in double-float arithmetic on the FP32 pipe,
- *    with the exponentials, the noise, the re-projection and the reductions
- *    in FP64 as in CL_FP64; its results agree with CL_FP64 to ~1e-14 per
- *    step.
+ *    cooling transformations), the noise, the exponentials and the
+ *    re-projection in double-float arithmetic on the FP32 pipe, with only
+ *    the reductions' final sums in FP64; its results agree with CL_FP64 to
+ *    ~1e-14 per step.
  *  - Noise: Philox4x32-10 keyed by (seed, step, site, mu), so results do not
  *    depend on launch shape, and a run resumed from cl_get_links /
  *    cl_get_step reproduces the uninterrupted one.

@@ -5,9 +5,10 @@
 // GB300 executes FP32 at ~58x its FP64 rate, so a product or sum carried as
 // two floats with error-free transformations (Dekker's product via FMA,
 // Knuth's two-sum) is far faster than the FP64 instruction it replaces while
-// keeping ~1e-14 relative accuracy.  Used for the link algebra of the DF64
-// form (links stored as hi/lo float pairs); the exponentials, the noise, the
-// determinant re-projection and every reduction stay in FP64.
+// keeping ~1e-14 relative accuracy.  Used by the DF64 form (links stored as
+// hi/lo float pairs) for the link algebra, the noise (ln, sqrt, sincospi
+// below), the exponentials and the determinant re-projection; only the
+// reductions' final sums are FP64.
 //
 // Error-free building blocks (exact for finite inputs without overflow):
 //   two_sum(a, b):      s + e = a + b exactly, s = fl(a + b)        (Knuth)

@@ -1,5 +1,6 @@
-// expm.cuh -- FP64 matrix exponentials of traceless 3x3 matrices and the
-// det = 1 re-projection.
+// expm.cuh -- matrix exponentials of traceless 3x3 matrices and the det = 1
+// re-projection: FP64 (the FP64 and FP32-storage forms) and double-float
+// (the *_df variants of the DF64 form, same steps).
 //
 // Method (Cayley-Hamilton reduction): a traceless 3x3 A satisfies
 //   A^3 = c1 A + c0 1,  c1 = Tr(A^2)/2,  c0 = det A = Tr(A^3)/3,

@@ -1,6 +1,7 @@
 // k_update_df64.cu -- the CL-step kernels (k_update.cuh) for double-float
-// links (df64.cuh): the link algebra on the FP32 pipe, the exponential, the
-// noise and the re-projection in FP64 as in the FP64 form.
+// links (df64.cuh): the link algebra, the noise, the exponential and the
+// re-projection in double-float on the FP32 pipe, the matrices of the
+// out-of-line products in a shared-memory workspace (Work, su3.cuh).
 #include "k_update.cuh"
 #include "launch.h"
 

@@ -506,7 +506,8 @@ __global__ void __launch_bounds__(RED_THREADS, RED_MAX_BLOCKS / 152) k_cool_grad
   block_reduce_store<NQ_COOL, -1>(v, partials);
 }
 
-// Omega_x = exp(-eps alpha_ad f_ax lambda_a) and its inverse, FP64.
+// Omega_x = exp(-eps alpha_ad f_ax lambda_a) and its inverse: FP64, or
+// double-float in the DF64 form.
 template <typename T>
 __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_omega(Geo g, const double* __restrict__ f, T* Om, T* Omi,
                                                            double eps, const CoolState* cs) {

@@ -1,7 +1,7 @@
 // su3.cuh -- 3x3 complex matrix algebra for the CL / gauge-cooling kernels.
 //
 // Templated on the real type T (double for the FP64 form, float for the
-// FP32-storage form).  Every product is written as explicit fused
+// FP32-storage form, df64 for the double-float form).  Every product is written as explicit fused
 // multiply-adds so the FP64 instruction count of a kernel can be read off the
 // code: a complex multiply-accumulate is 4 FMA, a 3x3 matrix product 108.
 //
