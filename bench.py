@@ -131,7 +131,7 @@ TRAFFIC_FAMILIES = {
     "fp32": {"force": ("k_plaq_force_ab<float>",), "update": ("k_update_gather<float, 0>",),
              "cool_apply": ("k_cool_apply<float>",), "cool_grad": ("k_cool_grad<float>",),
              "cool_omega": ("k_cool_omega<float>",)},
-    "df64": {"force": ("k_plaq_force_a<df64>", "k_plaq_force_b<df64>"),
+    "df64": {"force": ("k_plaq_force_a_df", "k_plaq_force_b_df"),
              "update": ("k_update_gather<df64, 0>",), "cool_apply": ("k_cool_apply_df",),
              "cool_grad": ("k_cool_grad_df",), "cool_omega": ("k_cool_omega<df64>",)},
 }

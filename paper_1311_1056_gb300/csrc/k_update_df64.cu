@@ -19,7 +19,177 @@ inline df64 df_host(double d) {
 inline dim3 grid(int V, int planes, int bs) { return dim3((unsigned)(((V + bs - 1) / bs) * planes)); }
 // dynamic shared memory of a kernel with nslot workspace matrices per thread
 inline size_t ws_bytes(int nslot, int bs) { return (size_t)nslot * sizeof(mat<df64>) * (size_t)bs; }
-const int NSLOT_PLAQ = 5, NSLOT_CLOVER = 4, NSLOT_WILSON = 4, NSLOT_FORCE = 5, NSLOT_UPDATE = 3;
+const int NSLOT_PLAQ = 3, NSLOT_CLOVER = 4, NSLOT_WILSON = 4, NSLOT_FORCE = 4, NSLOT_UPDATE = 3;
+const int DF_FORCE_BLOCK = 128;  // the DF64 force kernels' largest block (their launch bound)
+
+// Plaquettes of the DF64 form in three workspace slots (four blocks of 128
+// per SM): P = ((U_mu(x) U_nu(x+mu)) U_mu(x+nu)^{-1}) U_nu(x)^{-1}, the same
+// three products as k_plaq associated to the left.
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_df(Geo g, const float4* __restrict__ U,
+                                                       const float4* __restrict__ Ui, float4* __restrict__ Pq,
+                                                       float4* __restrict__ Dq) {
+  const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p);
+  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int x[4];
+  site_coords(g, s, x);
+  Work<df64, 3> ws(0);
+  mat<df64>&a = ws[0], &b = ws[1], &c = ws[2];
+  load(a, U, mu, s, g.V);
+  load(b, U, nu, hop(g, s, x, mu, 1), g.V);
+  mul(c, a, b);  // U_mu(x) U_nu(x+mu)
+  load(a, Ui, mu, hop(g, s, x, nu, 1), g.V);
+  mul(b, c, a);
+  load(a, Ui, nu, s, g.V);
+  mul(c, b, a);  // P
+  store(Pq, p, s, g.V, c);
+  adj(b, c);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) c.e[k] = csub(c.e[k], b.e[k]);
+  store(Dq, p, s, g.V, c);
+}
+
+// The theta force of the DF64 form: the stages of k_update.cuh rescheduled so
+// that four workspace slots suffice (Gh and three more; the FP64 stages hold
+// five matrices at their peak), which lets three blocks of 128 threads share
+// an SM instead of two.  The matrices given up early are re-read from memory
+// (D from Dq, the slot-0 partial from C), and (ab) G2 (ab)^{-1} is formed as
+// ((ab) G2 b^{-1}) a^{-1}, the same four products.
+__device__ __forceinline__ void force_stage_a_df(mat<df64>& Gh, const Geo& g, int s, const int x[4], int p,
+                                                 const float4* __restrict__ U, const float4* __restrict__ Ui,
+                                                 const float4* __restrict__ Dq, const float4* __restrict__ F,
+                                                 float4* C, df64 beta6) {
+  const int mu = plane_mu(p), nu = plane_nu(p), pc = 5 - p;
+  const unsigned long long m = (p == 1 || p == 4) ? 0x8000000000000000ull : 0ull;
+  const int c1 = hop(g, s, x, mu, 1);
+  Work<df64, 3> ws(1);  // slot 0 holds Gh
+  mat<df64>&D = ws[0], &t = ws[1], &q = ws[2];
+  // corner c0: slot 0 partial = [D, G0] - (beta/6) D, formed in t
+  load(D, Dq, p, s, g.V);
+  load_signed(Gh, F, pc, s, g.V, m);
+  scaled(t, -beta6, D);
+  commutator_acc(t, D, Gh);
+  store(C, 4 * p + 0, s, g.V, t);
+  // corner c1: G1^ = a G1 a^{-1}; slot 2 partial = slot 0 partial + [D, G1^]
+  load_signed(t, F, pc, c1, g.V, m);
+  load(q, U, mu, s, g.V);
+  mul(D, q, t);  // a G1
+  load(q, Ui, mu, s, g.V);
+  mul(t, D, q);  // G1^
+#pragma unroll
+  for (int k = 0; k < 9; ++k) Gh.e[k] = cadd(Gh.e[k], t.e[k]);
+  load(D, Dq, p, s, g.V);
+  load_rw(q, C, 4 * p + 0, s, g.V);
+  commutator_acc(q, D, t);
+  store(C, 4 * p + 2, s, g.V, q);
+  // corner c2: G2^ = ((ab) G2 b^{-1}) a^{-1}
+  load(q, U, mu, s, g.V);
+  load(t, U, nu, c1, g.V);
+  mul(D, q, t);  // ab
+  load_signed(q, F, pc, hop(g, c1, x, nu, 1), g.V, m);
+  mul(t, D, q);  // ab G2
+  load(q, Ui, nu, c1, g.V);
+  mul(D, t, q);  // ab G2 b^{-1}
+  load(q, Ui, mu, s, g.V);
+  mul_acc<+1>(Gh, D, q);
+}
+
+__device__ __forceinline__ void force_stage_b_df(mat<df64>& Gh, const Geo& g, int s, const int x[4], int p,
+                                                 const float4* __restrict__ U, const float4* __restrict__ Ui,
+                                                 const float4* __restrict__ Pq, const float4* __restrict__ Dq,
+                                                 const float4* __restrict__ F, float4* C, df64 beta6) {
+  const int mu = plane_mu(p), nu = plane_nu(p), pc = 5 - p;
+  const unsigned long long m = (p == 1 || p == 4) ? 0x8000000000000000ull : 0ull;
+  const int c3 = hop(g, s, x, nu, 1);
+  Work<df64, 3> ws(1);  // slot 0 holds Gh
+  mat<df64>&D = ws[0], &t = ws[1], &q = ws[2];
+  // corner c3: G3r = u G3 u^{-1} (in q); slot 3 partial = [D, G3r] + (beta/6) D
+  load_signed(q, F, pc, c3, g.V, m);
+  load(D, U, nu, s, g.V);
+  mul(t, D, q);
+  load(D, Ui, nu, s, g.V);
+  mul(q, t, D);
+  load(D, Dq, p, s, g.V);
+  scaled(t, beta6, D);
+  commutator_acc(t, D, q);
+  store(C, 4 * p + 3, s, g.V, t);
+  // G^ += P G3r P^{-1}, P^{-1} = P - D; the plaquette's D then lives in q
+  load(t, Pq, p, s, g.V);
+  mul(D, t, q);  // P G3r
+  load(q, Dq, p, s, g.V);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) t.e[k] = csub(t.e[k], q.e[k]);  // P^{-1}
+  mul_acc<+1>(Gh, D, t);
+  // K = P^{-1} G^ + G^ P, in D
+  mul(D, t, Gh);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) t.e[k] = cadd(t.e[k], q.e[k]);  // P again
+  mul_acc<+1>(D, Gh, t);
+  // slot 1: -K + (beta/6) D
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    t.e[k].re = fma(beta6, q.e[k].re, -D.e[k].re);
+    t.e[k].im = fma(beta6, q.e[k].im, -D.e[k].im);
+  }
+  store(C, 4 * p + 1, s, g.V, t);
+  // slot 0: K + partial
+  load_rw(t, C, 4 * p + 0, s, g.V);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) t.e[k] = cadd(t.e[k], D.e[k]);
+  store(C, 4 * p + 0, s, g.V, t);
+  // slot 2: a^{-1} (K + partial) a
+  load_rw(t, C, 4 * p + 2, s, g.V);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) t.e[k] = cadd(t.e[k], D.e[k]);
+  load(Gh, Ui, mu, s, g.V);
+  mul(q, Gh, t);
+  load(Gh, U, mu, s, g.V);
+  mul(t, q, Gh);
+  store(C, 4 * p + 2, s, g.V, t);
+  // slot 3: u^{-1} (-K + partial) u
+  load_rw(t, C, 4 * p + 3, s, g.V);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) t.e[k] = csub(t.e[k], D.e[k]);
+  load(Gh, Ui, nu, s, g.V);
+  mul(q, Gh, t);
+  load(Gh, U, nu, s, g.V);
+  mul(t, q, Gh);
+  store(C, 4 * p + 3, s, g.V, t);
+}
+
+__global__ void __launch_bounds__(DF_FORCE_BLOCK, 3) k_plaq_force_a_df(Geo g, const float4* __restrict__ U,
+                                                                    const float4* __restrict__ Ui,
+                                                                    const float4* __restrict__ Dq,
+                                                                    const float4* __restrict__ F,
+                                                                    float4* __restrict__ Gq, float4* C,
+                                                                    df64 beta6) {
+  const int p = blockIdx.x % 6;
+  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int x[4];
+  site_coords(g, s, x);
+  Work<df64, 1> wg(0);
+  mat<df64>& Gh = wg[0];
+  force_stage_a_df(Gh, g, s, x, p, U, Ui, Dq, F, C, beta6);
+  store(Gq, p, s, g.V, Gh);
+}
+__global__ void __launch_bounds__(DF_FORCE_BLOCK, 3) k_plaq_force_b_df(Geo g, const float4* __restrict__ U,
+                                                                    const float4* __restrict__ Ui,
+                                                                    const float4* __restrict__ Pq,
+                                                                    const float4* __restrict__ Dq,
+                                                                    const float4* __restrict__ F,
+                                                                    const float4* __restrict__ Gq, float4* C,
+                                                                    df64 beta6) {
+  const int p = blockIdx.x % 6;
+  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int x[4];
+  site_coords(g, s, x);
+  Work<df64, 1> wg(0);
+  mat<df64>& Gh = wg[0];
+  load(Gh, Gq, p, s, g.V);
+  force_stage_b_df(Gh, g, s, x, p, U, Ui, Pq, Dq, F, C, beta6);
+}
 
 template <typename K>
 cudaError_t allow_ws(K kernel, int nslot) {
@@ -33,11 +203,11 @@ cudaError_t allow_ws(K kernel, int nslot) {
 }  // namespace
 
 cudaError_t prepare_df64_kernels() {
-  cudaError_t e = allow_ws(k_plaq<df64>, NSLOT_PLAQ);
+  cudaError_t e = allow_ws(k_plaq_df, NSLOT_PLAQ);
   if (e == cudaSuccess) e = allow_ws(k_clover_rot<df64>, NSLOT_CLOVER);
   if (e == cudaSuccess) e = allow_ws(k_plaq_force_wilson<df64>, NSLOT_WILSON);
-  if (e == cudaSuccess) e = allow_ws(k_plaq_force_a<df64>, NSLOT_FORCE);
-  if (e == cudaSuccess) e = allow_ws(k_plaq_force_b<df64>, NSLOT_FORCE);
+  if (e == cudaSuccess) e = allow_ws(k_plaq_force_a_df, NSLOT_FORCE);
+  if (e == cudaSuccess) e = allow_ws(k_plaq_force_b_df, NSLOT_FORCE);
   if (e == cudaSuccess) e = allow_ws(k_update_gather<df64, MODE_UPDATE>, NSLOT_UPDATE);
   if (e == cudaSuccess) e = allow_ws(k_update_gather<df64, MODE_DRIFT>, NSLOT_UPDATE);
   if (e == cudaSuccess) e = allow_ws(k_update_gather<df64, MODE_DRIFTMAX>, NSLOT_UPDATE);
@@ -55,7 +225,7 @@ cudaError_t launch_plaq_df64(const GeoH& h, const void* U, const void* Ui, void*
                            cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
   const int bs = block_of(h, TUNE_CLOVER);
-  k_plaq<df64><<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_PLAQ, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (V2*)Pq, (V2*)Dq);
+  k_plaq_df<<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_PLAQ, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (V2*)Pq, (V2*)Dq);
   return cudaGetLastError();
 }
 
@@ -79,10 +249,12 @@ cudaError_t launch_plaq_force_df64(bool theta, const GeoH& h, const void* U, con
                                                          (V2*)C, b6);
     return cudaGetLastError();
   }
-  k_plaq_force_a<df64><<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_FORCE, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
-                                                  (const V2*)F, (V2*)Gq, (V2*)C, b6);
-  k_plaq_force_b<df64><<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_FORCE, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
-                                                  (const V2*)Dq, (const V2*)F, (const V2*)Gq, (V2*)C, b6);
+  const int bf = bs < DF_FORCE_BLOCK ? bs : DF_FORCE_BLOCK;
+  k_plaq_force_a_df<<<grid(g.V, 6, bf), bf, ws_bytes(NSLOT_FORCE, bf), st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+                                                                            (const V2*)F, (V2*)Gq, (V2*)C, b6);
+  k_plaq_force_b_df<<<grid(g.V, 6, bf), bf, ws_bytes(NSLOT_FORCE, bf), st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Pq,
+                                                                            (const V2*)Dq, (const V2*)F, (const V2*)Gq,
+                                                                            (V2*)C, b6);
   return cudaGetLastError();
 }
 
