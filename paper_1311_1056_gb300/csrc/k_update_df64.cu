@@ -19,7 +19,7 @@ inline df64 df_host(double d) {
 inline dim3 grid(int V, int planes, int bs) { return dim3((unsigned)(((V + bs - 1) / bs) * planes)); }
 // dynamic shared memory of a kernel with nslot workspace matrices per thread
 inline size_t ws_bytes(int nslot, int bs) { return (size_t)nslot * sizeof(mat<df64>) * (size_t)bs; }
-const int NSLOT_PLAQ = 3, NSLOT_CLOVER = 4, NSLOT_WILSON = 4, NSLOT_FORCE = 4, NSLOT_UPDATE = 3;
+const int NSLOT_PLAQ = 3, NSLOT_CLOVER = 3, NSLOT_WILSON = 4, NSLOT_FORCE = 4, NSLOT_UPDATE = 3;
 const int DF_FORCE_BLOCK = 128;  // the DF64 force kernels' largest block (their launch bound)
 
 // Plaquettes of the DF64 form in three workspace slots (four blocks of 128
@@ -47,6 +47,48 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_df(Geo g, const float4*
 #pragma unroll
   for (int k = 0; k < 9; ++k) c.e[k] = csub(c.e[k], b.e[k]);
   store(Dq, p, s, g.V, c);
+}
+
+// The clover field of the DF64 form (k_clover_rot's leaves) in three
+// workspace slots: the carried leaves are formed with in-place left
+// products, w <- w d, so no product needs a slot of its own.
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_clover_rot_df(Geo g, const float4* __restrict__ U,
+                                                             const float4* __restrict__ Ui,
+                                                             const float4* __restrict__ Dq, float4* __restrict__ F,
+                                                             df64 sre, df64 sim) {
+  const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p);
+  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+  if (s >= g.V) return;
+  int x[4];
+  site_coords(g, s, x);
+  const int xmm = hop(g, s, x, mu, -1), xmn = hop(g, s, x, nu, -1);
+  const int xmm_mn = hop2(g, s, x, mu, -1, nu, -1);
+  Work<df64, 3> ws(0);
+  mat<df64>&acc = ws[0], &w = ws[1], &d = ws[2];
+  load(acc, Dq, p, s, g.V);
+  // L2 = U_mu(x-mu)^{-1} D(x-mu) U_mu(x-mu)
+  load(w, Ui, mu, xmm, g.V);
+  load(d, Dq, p, xmm, g.V);
+  mul_left_inplace_df(w, d);
+  load(d, U, mu, xmm, g.V);
+  mul_acc<+1>(acc, w, d);
+  // L3 + L4 = U_nu(x-nu)^{-1} [D(x-nu) + U_mu(x-mu-nu)^{-1} D(x-mu-nu) U_mu(x-mu-nu)] U_nu(x-nu)
+  load(w, Ui, mu, xmm_mn, g.V);
+  load(d, Dq, p, xmm_mn, g.V);
+  mul_left_inplace_df(w, d);
+  load(d, U, mu, xmm_mn, g.V);
+  mul_left_inplace_df(w, d);
+  load(d, Dq, p, xmn, g.V);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) d.e[k] = cadd(d.e[k], w.e[k]);
+  load(w, Ui, nu, xmn, g.V);
+  mul_left_inplace_df(w, d);
+  load(d, U, nu, xmn, g.V);
+  mul_acc<+1>(acc, w, d);
+  const cx<df64> sc = {sre, sim};
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc.e[k] = cmul(acc.e[k], sc);
+  store(F, p, s, g.V, acc);
 }
 
 // The theta force of the DF64 form: the stages of k_update.cuh rescheduled so
@@ -204,7 +246,7 @@ cudaError_t allow_ws(K kernel, int nslot) {
 
 cudaError_t prepare_df64_kernels() {
   cudaError_t e = allow_ws(k_plaq_df, NSLOT_PLAQ);
-  if (e == cudaSuccess) e = allow_ws(k_clover_rot<df64>, NSLOT_CLOVER);
+  if (e == cudaSuccess) e = allow_ws(k_clover_rot_df, NSLOT_CLOVER);
   if (e == cudaSuccess) e = allow_ws(k_plaq_force_wilson<df64>, NSLOT_WILSON);
   if (e == cudaSuccess) e = allow_ws(k_plaq_force_a_df, NSLOT_FORCE);
   if (e == cudaSuccess) e = allow_ws(k_plaq_force_b_df, NSLOT_FORCE);
@@ -233,8 +275,8 @@ cudaError_t launch_clover_rot_df64(const GeoH& h, const void* U, const void* Ui,
                                  void* F, double sre, double sim, cudaStream_t st) {
   Geo g = make_geo(h.L, h.V);
   const int bs = block_of(h, TUNE_CLOVER);
-  k_clover_rot<df64><<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_CLOVER, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
-                                                  (V2*)F, sre, sim);
+  k_clover_rot_df<<<grid(g.V, 6, bs), bs, ws_bytes(NSLOT_CLOVER, bs), st>>>(g, (const V2*)U, (const V2*)Ui, (const V2*)Dq,
+                                                                           (V2*)F, df_host(sre), df_host(sim));
   return cudaGetLastError();
 }
 

@@ -268,6 +268,30 @@ static __device__ __noinline__ void mul_df(mat<df64>& c, const mat<df64>& a, con
       c.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
     }
 }
+// a <- a b in place: each row of a is read into registers before it is
+// overwritten (the other rows are untouched), so one workspace slot fewer.
+static __device__ __noinline__ void mul_left_inplace_df(mat<df64>& a, const mat<df64>& b) {
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+    const cx<df64> x0 = a.e[3 * i], x1 = a.e[3 * i + 1], x2 = a.e[3 * i + 2];
+#pragma unroll 1
+    for (int j = 0; j < 3; ++j) {
+      const cx<df64> y0 = b.e[j], y1 = b.e[3 + j], y2 = b.e[6 + j];
+      dacc re = dacc_first(x0.re, y0.re), im = dacc_first(x0.re, y0.im);
+      dacc_add(re, -x0.im, y0.im);
+      dacc_add(im, x0.im, y0.re);
+      dacc_add(re, x1.re, y1.re);
+      dacc_add(re, -x1.im, y1.im);
+      dacc_add(im, x1.re, y1.im);
+      dacc_add(im, x1.im, y1.re);
+      dacc_add(re, x2.re, y2.re);
+      dacc_add(re, -x2.im, y2.im);
+      dacc_add(im, x2.re, y2.im);
+      dacc_add(im, x2.im, y2.re);
+      a.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
+    }
+  }
+}
 static __device__ __noinline__ void mul_acc_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b, int sign) {
 #pragma unroll 1
   for (int i = 0; i < 3; ++i)
