@@ -23,13 +23,14 @@ def _lattice(L, beta, theta, prec, U, seed):
     return lat
 
 
+@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_DF64])
 @pytest.mark.parametrize("L,theta", [((4, 3, 4, 5), 1.0), ((3, 3, 3, 3), 0.5j), ((4, 4, 4, 4), 0.0)])
-def test_adaptive_steps_against_the_oracle(L, theta):
+def test_adaptive_steps_against_the_oracle(L, theta, prec):
     beta, eps, seed = 6.0, 0.02, 21
     U = LI.sl3c_lattice(L, seed=4, spread=0.2)
     _, _, k0 = O.cl_step_adaptive(L, U, beta, theta, eps, 0.0, seed, 0)
     k_ref = 0.6 * k0  # the rule engages on the first steps
-    with _lattice(L, beta, theta, cl.CL_FP64, U, seed) as lat:
+    with _lattice(L, beta, theta, prec, U, seed) as lat:
         lat.set_adaptive_step(k_ref)
         t_ref = 0.0
         for step in range(5):
@@ -48,7 +49,7 @@ def test_adaptive_steps_against_the_oracle(L, theta):
 def test_large_reference_is_the_plain_step_bit_for_bit():
     L, beta, theta, eps, seed = (4, 4, 3, 5), 6.0, 1.0, 0.01, 3
     U = LI.sl3c_lattice(L, seed=8, spread=0.2)
-    for prec in (cl.CL_FP64, cl.CL_FP32_STORAGE):
+    for prec in (cl.CL_FP64, cl.CL_FP32_STORAGE, cl.CL_DF64):
         with _lattice(L, beta, theta, prec, U, seed) as a, _lattice(L, beta, theta, prec, U, seed) as b:
             b.set_adaptive_step(1e12)
             a.step(eps, 3)

@@ -24,7 +24,7 @@ def _lat(prec, theta=1.0, L=(6, 4, 4, 6)):
                       gauge_sigma=0.05, own_stream=True)
 
 
-@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_FP32_STORAGE])
+@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_FP32_STORAGE, cl.CL_DF64])
 def test_autotune_leaves_state_and_picks_candidates(prec):
     cp = cl.make_cool(**ADAPT)
     with _lat(prec) as a, _lat(prec) as b:
@@ -51,7 +51,7 @@ def test_autotune_leaves_state_and_picks_candidates(prec):
 
 
 @pytest.mark.parametrize("prec,theta", [(cl.CL_FP64, 1.0), (cl.CL_FP32_STORAGE, 0.5),
-                                        (cl.CL_FP64, 0.0)])
+                                        (cl.CL_FP64, 0.0), (cl.CL_DF64, 1.0), (cl.CL_DF64, 0.0)])
 def test_every_block_size_gives_the_same_links(prec, theta):
     cp = cl.make_cool(**ADAPT)
     ref = None

@@ -26,13 +26,14 @@ def _from(U, L, beta=6.0, theta=0.0, prec=cl.CL_FP64, seed=1):
     return lat
 
 
+@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_DF64])
 @pytest.mark.parametrize("L", [(1, 4, 4, 4), (2, 1, 3, 1), (1, 1, 1, 1), (3, 1, 1, 2)])
 @pytest.mark.parametrize("theta", [0.0, 1.0])
-def test_extents_of_one(L, theta):
+def test_extents_of_one(L, theta, prec):
     U = LI.sl3c_lattice(L, seed=5, spread=0.2)
     beta, eps, seed = 6.0, 0.01, 4
     cpar = dict(eps=eps, alpha=1.0, mode=cl.CL_D1, forced_sweeps=2)
-    with _from(U, L, beta, theta, seed=seed) as lat:
+    with _from(U, L, beta, theta, prec=prec, seed=seed) as lat:
         X = lat.drift()
         f = lat.cool_gradient()
         o = lat.observables()
@@ -65,7 +66,7 @@ def test_zero_steps_and_zero_sweeps():
         assert len(obs) == 0 and lat.step_count == 0
 
 
-@pytest.mark.parametrize("prec,tol", [(cl.CL_FP32_STORAGE, 3e-5), (cl.CL_FP64, 1e-12)])
+@pytest.mark.parametrize("prec,tol", [(cl.CL_FP32_STORAGE, 3e-5), (cl.CL_FP64, 1e-12), (cl.CL_DF64, 1e-12)])
 def test_largest_tiled_lattice(prec, tol):
     small, reps = (4, 4, 4, 4), (16, 16, 16, 16)
     L = tuple(a * r for a, r in zip(small, reps))  # 64^4 = 16,777,216 sites

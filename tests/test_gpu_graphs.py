@@ -26,7 +26,7 @@ def _lat(L=(4, 4, 4, 6), beta=6.0, theta=1.0, prec=cl.CL_FP64, seed=3, sigma=0.0
 ADAPT = dict(eps=0.01, alpha=1.0, mode=cl.CL_D2_MEANABS, n_min=1, n_max=6, tol_rel=0.05)
 
 
-@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_FP32_STORAGE])
+@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_FP32_STORAGE, cl.CL_DF64])
 @pytest.mark.parametrize("cool", [None, ADAPT])
 def test_replay_equals_eager(prec, cool):
     cp = cl.make_cool(**cool) if cool else None

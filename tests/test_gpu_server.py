@@ -55,7 +55,7 @@ def _serve(reqs, prec, **kw):
     return {r["tag"]: r for r in res}, st
 
 
-@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_FP32_STORAGE])
+@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_FP32_STORAGE, cl.CL_DF64])
 def test_each_result_same_alone_and_in_the_mix(prec):
     reqs = _requests()
     got, st = _serve(reqs, prec)
