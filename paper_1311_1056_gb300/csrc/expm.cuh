@@ -182,8 +182,8 @@ __device__ __forceinline__ void expm_traceless_df(mat<df64>& E, const mat<df64>&
     b = cx<df64>{df_ldexp(b.re, -s), df_ldexp(b.im, -s)};
     c = cx<df64>{df_ldexp(c.re, -2 * s), df_ldexp(c.im, -2 * s)};
   }
-#pragma unroll
-  for (int k = 0; k < 9; ++k) {
+#pragma unroll 1
+  for (int k = 0; k < 9; ++k) {  // rolled: the matrices are in memory (the DF64 workspace)
     cx<df64> v = cmul(b, A.e[k]);
     v = cfma(c, A2.e[k], v);
     if (k % 4 == 0) v = cadd(v, a);

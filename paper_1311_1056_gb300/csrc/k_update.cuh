@@ -498,8 +498,8 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const t
     load(Ul, U, MU, s, g.V);
     mul(Un, E, Ul);
     const cx<df64> z = det_inv_cuberoot_df(det(Un));
-#pragma unroll
-    for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], z);
+#pragma unroll 1
+    for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], z);  // rolled, like the loops above: code size
     store(out, MU, s, g.V, Un);
     return;
   }
