@@ -499,7 +499,7 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const t
     mul(Un, E, Ul);
     const cx<df64> z = det_inv_cuberoot_df(det(Un));
 #pragma unroll 1
-    for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], z);  // rolled, like the loops above: code size
+    for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], z);  // rolled: Un is in the workspace; saves code
     store(out, MU, s, g.V, Un);
     return;
   }
