@@ -653,12 +653,17 @@ def serve_mode(args):
     # warm-up: a few small requests through both configurations
     warm = workloads.trace(4, rate=1000.0, seed=1, steps=(20, 20), l_range=(4, 8))
     _serve_once(cl, warm, cl.CL_FP32_STORAGE, args.slots, True, True)
+    if not args.no_serve_df64:
+        _serve_once(cl, warm, cl.CL_DF64, args.slots, True, True)
     _serve_once(cl, warm, cl.CL_FP64, 1, False, False)
     sampler = ClockSampler(0)
     sampler.start()
     arms = {}
     _log("serve: served_fp32")
     arms["served_fp32"] = _serve_once(cl, trace, cl.CL_FP32_STORAGE, args.slots, True, True)
+    if not args.no_serve_df64:
+        _log("serve: served_df64")
+        arms["served_df64"] = _serve_once(cl, trace, cl.CL_DF64, args.slots, True, True)
     _log("serve: one_at_a_time_fp64")
     arms["one_at_a_time_fp64"] = _serve_once(cl, trace, cl.CL_FP64, 1, False, False)
     _log("serve: done")
@@ -694,6 +699,11 @@ def serve_mode(args):
             "vs_one_at_a_time_fp64": {"throughput_x": a["value"] / b["value"], "p50_x": b["p50_s"] / a["p50_s"],
                                       "p99_x": b["p99_s"] / a["p99_s"]},
             "arms": out, "clocks": clocks}
+    if "served_df64" in out:  # the same serving at FP64-grade accuracy (double-float links)
+        c = out["served_df64"]
+        line["served_df64_vs_one_at_a_time_fp64"] = {"throughput_x": c["value"] / b["value"],
+                                                     "p50_x": b["p50_s"] / c["p50_s"],
+                                                     "p99_x": b["p99_s"] / c["p99_s"]}
     print(json.dumps(line), flush=True)
 
 
@@ -783,6 +793,7 @@ def main():
     ap.add_argument("--slots", type=int, default=64)
     ap.add_argument("--chains", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=200)
+    ap.add_argument("--no-serve-df64", action="store_true", help="serve: skip the double-float arm")
     ap.add_argument("--ingest-ncu", metavar="CSV", default=None,
                     help="summarise an ncu launch list with DRAM bytes and update profiles/dram_traffic.json")
     args = ap.parse_args()
