@@ -580,6 +580,7 @@ def batch_mode(args):
     sampler.start()
     arms = {}
     for name, prec, batched in (("batched_fp32", cl.CL_FP32_STORAGE, True), ("batched_fp64", cl.CL_FP64, True),
+                                ("batched_df64", cl.CL_DF64, True),
                                 ("alone_fp32", cl.CL_FP32_STORAGE, False), ("alone_fp64", cl.CL_FP64, False)):
         _log("arm %s" % name)
         arms[name] = _run_chains(cl, torch, chains, prec, n_steps, batched, batched)
@@ -610,6 +611,7 @@ def batch_mode(args):
                    "sites_per_step": total // n_steps,
                    "sizes": {str(L): sum(1 for c in chains if c["L"][0] == L) for L in workloads.ENSEMBLE_SIZES}},
         "speedup_vs_alone_fp64": res["batched_fp32"]["value"] / res["alone_fp64"]["value"],
+        "df64_speedup_vs_alone_fp64": res["batched_df64"]["value"] / res["alone_fp64"]["value"],
         "arms": res, "clocks": clocks,
     }
     print(json.dumps(line), flush=True)
