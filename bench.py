@@ -137,7 +137,7 @@ TRAFFIC_FAMILIES = {
 }
 
 
-def ingest_ncu(path):
+def ingest_ncu(path, out_json=None):
     """Reads an ncu launch list (--csv, metrics gpu__time_duration.sum and
     dram__bytes_{read,write}.sum, --kernel-name-base demangled), prints its
     per-kernel summary as a markdown table and writes the per-launch DRAM bytes
@@ -181,8 +181,9 @@ def ingest_ncu(path):
             if all(k in agg for k in kernels):
                 b = sum((agg[k]["rd"] + agg[k]["wr"]) / agg[k]["n"] for k in kernels)
                 out.setdefault(form, {})[fam] = {"bytes_per_launch": b, "source_hash": h}
-    with open(os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as fh:
+    with open(out_json or os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as fh:
         json.dump(out, fh, indent=1)
+    return agg, out
 
 
 class ClockSampler:
