@@ -763,15 +763,17 @@ def theta_scan_mode(args):
 
 
 def precision_mode(args):
-    """The FP32-storage form against the FP64 form, every observable."""
+    """The FP32-storage and DF64 forms against the FP64 form, every observable."""
     from paper_1311_1056_gb300 import build, cl, studies
 
     build.build()
     cl.load()
     L = tuple(args.L) if args.L else WORKLOAD["L"]
     tab = studies.precision_table(L=L, checkpoints=(1, 10, 100))
+    tab_df = studies.precision_table(L=L, checkpoints=(1, 10, 100), prec=cl.CL_DF64)
     print(json.dumps({"metric": "FP32-storage error vs FP64 on identical noise", "workload": WORKLOAD_NAME,
-                      "lattice": list(L), "table": {str(k): v for k, v in tab.items()}}), flush=True)
+                      "lattice": list(L), "table": {str(k): v for k, v in tab.items()},
+                      "df64_table": {str(k): v for k, v in tab_df.items()}}), flush=True)
 
 
 def main():

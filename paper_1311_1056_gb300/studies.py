@@ -104,16 +104,16 @@ OBS_KEYS = ("plaq_re", "plaq_im", "un", "q_re", "q_im", "sw_re", "sw_im", "s_re"
 
 
 def precision_table(L=(32, 32, 32, 32), beta=6.2, theta=1.0, eps=0.005, sweeps=10, checkpoints=(1, 10, 100),
-                    seed=1):
-    """FP32-storage vs FP64 on the same workload as the throughput bench
-    (Haar start, fixed count of D_1 sweeps).  Returns {n_steps: {"links":
-    max abs difference, observable: (fp64 value, abs difference, relative
-    difference)}}."""
+                    seed=1, prec=None):
+    """A reduced-precision form (FP32 storage by default, or DF64) vs FP64 on
+    the same workload as the throughput bench (Haar start, fixed count of D_1
+    sweeps).  Returns {n_steps: {"links": max abs difference, observable:
+    (fp64 value, abs difference, relative difference)}}."""
+    prec = cl.CL_FP32_STORAGE if prec is None else prec
     cp = cl.make_cool(eps, 1.0, cl.CL_D1, forced_sweeps=sweeps)
     out = {}
     with cl.Lattice(L, beta=beta, theta=theta, prec=cl.CL_FP64, seed=seed, start=cl.CL_START_HOT) as a, \
-            cl.Lattice(L, beta=beta, theta=theta, prec=cl.CL_FP32_STORAGE, seed=seed,
-                       start=cl.CL_START_HOT) as b:
+            cl.Lattice(L, beta=beta, theta=theta, prec=prec, seed=seed, start=cl.CL_START_HOT) as b:
         done = 0
         for n in sorted(checkpoints):
             for lat in (a, b):
