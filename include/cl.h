@@ -405,8 +405,8 @@ cl_status cl_cool_gradient(cl_lattice* lat, double* host_f);
 /* The standard normal numbers of the CL noise as the kernels of form prec
  * draw them (Philox4x32-10 stream 0, Box-Muller): for each of the nsites
  * sites site0 .. site0 + nsites - 1 and direction mu, the 8 numbers of link
- * (site, mu) at step `step` (eta_a = sqrt(2) times them, a = 1..8; Sec. 2
- * noise normalisation), host doubles [site][8].  FP64 draws them in FP64,
+ * (site, mu) at step `step` (the update's eta_a = sqrt(2) times them, a =
+ * 1..8, so that <eta_a eta_b> = 2 delta_ab), host doubles [site][8].  FP64 draws them in FP64,
  * DF64 in double-float, FP32 storage in float.  A diagnostic: it uses the
  * current device and the legacy default stream, allocates and frees its own
  * device buffer, and synchronises.  Errors: CL_ERR_INVALID (NULL out, bad
