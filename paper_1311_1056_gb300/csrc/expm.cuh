@@ -138,7 +138,7 @@ __device__ __forceinline__ void expm_traceless(mat<T>& E, const mat<T>& A, float
 // caller's workspace for A^2; E may be A itself (E is formed entry by entry
 // from the same entries of A and A^2).
 __device__ __forceinline__ void expm_traceless_df(mat<df64>& E, const mat<df64>& A, mat<df64>& A2) {
-  mul(A2, A, A);
+  mul_df_compact(A2, A, A);
   const cx<df64> t1 = trace(A2), t0 = trace_mul(A2, A);
   const df64 third = df_const(1.0 / 3.0);
   const cx<df64> c1 = {df_ldexp(t1.re, -1), df_ldexp(t1.im, -1)};

@@ -496,7 +496,7 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const t
     mat<df64>&E = X, &Ul = t, &Un = wu[0];
     expm_traceless_df(E, X, t);
     load(Ul, U, MU, s, g.V);
-    mul(Un, E, Ul);
+    mul_df_compact(Un, E, Ul);
     const cx<df64> z = det_inv_cuberoot_df(det(Un));
 #pragma unroll 1
     for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], z);  // rolled: Un is in the workspace; saves code

@@ -248,9 +248,45 @@ __device__ __forceinline__ void dacc_norm(dacc& a) {
   a.lo = t.lo;
 }
 
+// The products run row by row: row i of a in registers, the row's three
+// entries accumulated side by side (six independent chains per row, and a's
+// row read once), the row written at the end.  So c may be a itself
+// (mul_left_inplace_df), and each entry adds its terms in the same order as
+// an entry-by-entry product would.
 static __device__ __noinline__ void mul_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b) {
 #pragma unroll 1
-  for (int i = 0; i < 3; ++i)  // rolled: one entry's code in the instruction cache
+  for (int i = 0; i < 3; ++i) {  // rolled: one row's code in the instruction cache
+    const cx<df64> x0 = a.e[3 * i], x1 = a.e[3 * i + 1], x2 = a.e[3 * i + 2];
+    dacc re[3], im[3];
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const cx<df64> y = b.e[j];
+      re[j] = dacc_first(x0.re, y.re);
+      im[j] = dacc_first(x0.re, y.im);
+      dacc_add(re[j], -x0.im, y.im);
+      dacc_add(im[j], x0.im, y.re);
+    }
+#pragma unroll
+    for (int k = 1; k < 3; ++k) {
+      const cx<df64> x = k == 1 ? x1 : x2;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const cx<df64> y = b.e[3 * k + j];
+        dacc_add(re[j], x.re, y.re);
+        dacc_add(re[j], -x.im, y.im);
+        dacc_add(im[j], x.re, y.im);
+        dacc_add(im[j], x.im, y.re);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) c.e[3 * i + j] = cx<df64>{dacc_get(re[j]), dacc_get(im[j])};
+  }
+}
+// The same product one entry at a time (both loops rolled): a third of the
+// code, for kernels that already wait on instruction fetch (the update).
+static __device__ __noinline__ void mul_df_compact(mat<df64>& c, const mat<df64>& a, const mat<df64>& b) {
+#pragma unroll 1
+  for (int i = 0; i < 3; ++i)
 #pragma unroll 1
     for (int j = 0; j < 3; ++j) {
       const cx<df64> x0 = a.e[3 * i], y0 = b.e[j];
@@ -268,49 +304,36 @@ static __device__ __noinline__ void mul_df(mat<df64>& c, const mat<df64>& a, con
       c.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
     }
 }
-// a <- a b in place: each row of a is read into registers before it is
-// overwritten (the other rows are untouched), so one workspace slot fewer.
-static __device__ __noinline__ void mul_left_inplace_df(mat<df64>& a, const mat<df64>& b) {
-#pragma unroll 1
-  for (int i = 0; i < 3; ++i) {
-    const cx<df64> x0 = a.e[3 * i], x1 = a.e[3 * i + 1], x2 = a.e[3 * i + 2];
-#pragma unroll 1
-    for (int j = 0; j < 3; ++j) {
-      const cx<df64> y0 = b.e[j], y1 = b.e[3 + j], y2 = b.e[6 + j];
-      dacc re = dacc_first(x0.re, y0.re), im = dacc_first(x0.re, y0.im);
-      dacc_add(re, -x0.im, y0.im);
-      dacc_add(im, x0.im, y0.re);
-      dacc_add(re, x1.re, y1.re);
-      dacc_add(re, -x1.im, y1.im);
-      dacc_add(im, x1.re, y1.im);
-      dacc_add(im, x1.im, y1.re);
-      dacc_add(re, x2.re, y2.re);
-      dacc_add(re, -x2.im, y2.im);
-      dacc_add(im, x2.re, y2.im);
-      dacc_add(im, x2.im, y2.re);
-      a.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
-    }
-  }
-}
+// a <- a b in place (row i of a is in registers before it is overwritten):
+// one workspace slot fewer.
+static __device__ __forceinline__ void mul_left_inplace_df(mat<df64>& a, const mat<df64>& b) { mul_df(a, a, b); }
 static __device__ __noinline__ void mul_acc_df(mat<df64>& c, const mat<df64>& a, const mat<df64>& b, int sign) {
 #pragma unroll 1
-  for (int i = 0; i < 3; ++i)
-#pragma unroll 1
+  for (int i = 0; i < 3; ++i) {
+    cx<df64> x[3] = {a.e[3 * i], a.e[3 * i + 1], a.e[3 * i + 2]};
+    if (sign < 0)
+#pragma unroll
+      for (int k = 0; k < 3; ++k) x[k] = cx<df64>{-x[k].re, -x[k].im};
+    dacc re[3], im[3];
+#pragma unroll
     for (int j = 0; j < 3; ++j) {
       const cx<df64> c0 = c.e[3 * i + j];
-      dacc re = {c0.re.hi, c0.re.lo}, im = {c0.im.hi, c0.im.lo};
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        cx<df64> x = a.e[3 * i + k];
-        if (sign < 0) x = cx<df64>{-x.re, -x.im};
-        const cx<df64> y = b.e[3 * k + j];
-        dacc_add(re, x.re, y.re);
-        dacc_add(re, -x.im, y.im);
-        dacc_add(im, x.re, y.im);
-        dacc_add(im, x.im, y.re);
-      }
-      c.e[3 * i + j] = cx<df64>{dacc_get(re), dacc_get(im)};
+      re[j] = dacc{c0.re.hi, c0.re.lo};
+      im[j] = dacc{c0.im.hi, c0.im.lo};
     }
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const cx<df64> y = b.e[3 * k + j];
+        dacc_add(re[j], x[k].re, y.re);
+        dacc_add(re[j], -x[k].im, y.im);
+        dacc_add(im[j], x[k].re, y.im);
+        dacc_add(im[j], x[k].im, y.re);
+      }
+#pragma unroll
+    for (int j = 0; j < 3; ++j) c.e[3 * i + j] = cx<df64>{dacc_get(re[j]), dacc_get(im[j])};
+  }
 }
 
 // Adjugate: adj(a) a = det(a) 1; for det a = 1 it is the inverse.
