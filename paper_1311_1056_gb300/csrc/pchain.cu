@@ -46,12 +46,6 @@ __device__ __forceinline__ M2 m2mul(const M2& x, const M2& y) {
   r.e[3] = cfma(x.e[3], y.e[3], cmul(x.e[2], y.e[1]));
   return r;
 }
-__device__ __forceinline__ M2 m2ident() {
-  M2 r;
-  r.e[0] = r.e[3] = C{1.0, 0.0};
-  r.e[1] = r.e[2] = C{0.0, 0.0};
-  return r;
-}
 __device__ __forceinline__ C cscale(C a, double s) { return C{a.re * s, a.im * s}; }
 __device__ __forceinline__ C cconj(C a) { return C{a.re, -a.im}; }
 __device__ __forceinline__ C m2det(const M2& x) { return cfms(x.e[1], x.e[2], cmul(x.e[0], x.e[3])); }
