@@ -67,6 +67,7 @@ def flop_model(prec, theta_on=True, n_taylor=15):
         "cool_grad": 914,
         "cool_omega": 209,
         "cool_apply": 4 * 2 * HERM,
+        "cool_grad_omega": 914 + 209,
     }
     if prec == "fp64":
         m["update"] = 4 * (12 * 18 + 32 + 38 + expm + MUL + det_root + 54)
@@ -74,7 +75,8 @@ def flop_model(prec, theta_on=True, n_taylor=15):
     else:
         m["update"] = 4 * (expm - 36 + det_root)                 # FP64 part only
         pipe = {k: "fp32" for k in m}
-        pipe["update"] = pipe["cool_omega"] = "fp64"
+        pipe["update"] = pipe["cool_omega"] = pipe["cool_grad_omega"] = "fp64"
+        m["cool_grad_omega"] = 209  # FP64 part only (the gradient is FP32 there)
     return m, pipe
 
 
@@ -355,30 +357,50 @@ def e2e_measure(cl, torch, lat, V, one_step, steps):
                                  "step_and_get_links": round(t_get / steps * 1e3, 3)}}
 
 
+# FP32 floating-point operations per site that the DF64 kernels execute
+# (FFMA = 2, FADD = FMUL = 1), from ncu's executed-instruction counters on one
+# launch at 24^4 (smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on,
+# profiles/ncu_df64_fp32_ops_24x4.md) divided by the 331,776 sites: these
+# kernels load the FP32 pipe, so their roofline is that pipe's peak.
+DF64_FP32_FLOPS_PER_SITE = {}
+
+
+def fp32_peak_tflops(sm_max_mhz):
+    # 152 SMs x 128 FP32 FMA per SM per clock (256 flops) x clock: 80.5 TFLOP/s at 2070 MHz.
+    return 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+
+
 def roofline_of(prec_name, V, phases, sm_max_mhz, theta_on=True):
-    """Roofline of the kernel that dominates the step (a single-kernel phase)."""
-    # DF64 runs the FP64 form's algorithm with double-float link algebra: its
-    # work is counted in FP64-equivalent flops against the FP64 peak
+    """Roofline of the kernel that dominates the step (a single-kernel phase),
+    against the peak of the pipe that kernel loads."""
     fm, pipe = flop_model("fp64" if prec_name == "df64" else prec_name, theta_on)
     single = {k: v for k, v in phases.items() if k in ("force", "update", "cool_grad", "cool_omega",
-                                                       "cool_apply")}
+                                                       "cool_apply", "cool_grad_omega")}
     dom = max(single, key=lambda k: single[k][0])
     ms_tot, n = phases[dom]
     per = ms_tot / max(n, 1)
+    if prec_name == "df64":
+        # double-float arithmetic runs on the FP32 pipe: its executed FP32
+        # operations (ncu counts) against the FP32 peak
+        per_site = DF64_FP32_FLOPS_PER_SITE.get(dom)
+        peak = fp32_peak_tflops(sm_max_mhz)
+        src = ("executed FP32 operations of the double-float kernels (ncu, 24^4) against "
+               "152 SMs x 128 FP32 FMA/clk x %d MHz (FP32 is not in MEASURED_PEAKS.json)" % sm_max_mhz)
+        flops = per_site * V if per_site else None
+        ach = flops / (per * 1e-3) / 1e12 if flops else None
+        return {"kernel": dom, "bound": "alu", "pipe": "fp32", "achieved": round(ach, 4) if ach else None,
+                "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(ach / peak, 4) if ach else None,
+                "traffic": dram_traffic(dom, prec_name), "flops_per_launch": flops,
+                "avg_launch_ms": round(per, 4), "launches": n, "peak_source": src}
     flops = fm[dom] * V
     if pipe[dom] == "fp64":
         peak = fp64_peak_tflops(sm_max_mhz)
         src = "152 SMs x 2 FP64 FMA/clk x %d MHz (FP64 is not in MEASURED_PEAKS.json)" % sm_max_mhz
     else:
-        peak = 152 * 128 * 2 * sm_max_mhz * 1e6 / 1e12
+        peak = fp32_peak_tflops(sm_max_mhz)
         src = "152 SMs x 128 FP32 FMA/clk x %d MHz" % sm_max_mhz
     ach = flops / (per * 1e-3) / 1e12
-    if prec_name == "df64":
-        src = ("FP64-equivalent flops (double-float on the FP32 pipe) against the FP64 peak, "
-               "152 SMs x 2 FP64 FMA/clk x %d MHz" % sm_max_mhz)
-        peak = fp64_peak_tflops(sm_max_mhz)
-    return {"kernel": dom, "bound": "alu", "pipe": "fp32 (double-float)" if prec_name == "df64" else pipe[dom],
-            "achieved": round(ach, 4),
+    return {"kernel": dom, "bound": "alu", "pipe": pipe[dom], "achieved": round(ach, 4),
             "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
             "traffic": dram_traffic(dom, prec_name), "flops_per_launch": flops,
             "avg_launch_ms": round(per, 4), "launches": n, "peak_source": src}
@@ -450,8 +472,8 @@ def native(args):
         msd = rank_max(msd, "cuda")
         result.setdefault("forms", {})["df64"] = {
             "value": job_value(Vd, msd, ws), "ms_per_step": msd, "gpu_launches": ld,
-            "dtype": "df64 links (hi + lo floats) and link algebra on the FP32 pipe; f64 exp/noise/"
-                     "reprojection/reductions",
+            "dtype": "df64 links (hi + lo floats); link algebra, noise, exponentials and re-projection "
+                     "in double-float on the FP32 pipe; f64 final sums of the reductions",
             "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in phd.items()},
             "roofline": roofline_of("df64", Vd, phd, sm_max),
             "observables_after": {k: obsd[k] for k in ("plaq_re", "un", "q_re", "q_im")},
@@ -776,6 +798,59 @@ def precision_mode(args):
                       "df64_table": {str(k): v for k, v in tab_df.items()}}), flush=True)
 
 
+# 16^4 long runs (the theta-scan config): FP64, FP32 storage and DF64
+# ensembles of independent chains (disjoint Philox seeds per form), compared
+# in distribution after thermalisation.
+LONGRUN = dict(L=(16, 16, 16, 16), beta=6.0, thetas=(0.0, 0.5, 1.0, 2.0), eps=0.005, every=10)
+LONGRUN_NAME = ("16^4 SU(3) Wilson + clover theta, beta 6.0, theta in {0, 0.5, 1, 2}, cold start; CL steps at "
+                "eps 0.005 with adaptive cooling (alpha_ad = 0.1 / D_2, 0..10 sweeps, stop below 1 % relative "
+                "progress or within 1e-6 of SU(3)); observables every 10 steps")
+
+
+def longrun_mode(args):
+    import numpy as np
+    from paper_1311_1056_gb300 import build, cl, studies
+
+    build.build()
+    cl.load()
+    w = LONGRUN
+    L = tuple(args.L) if args.L else w["L"]
+    forms = (("fp64", cl.CL_FP64, 0), ("fp32_storage", cl.CL_FP32_STORAGE, 100), ("df64", cl.CL_DF64, 200))
+    floors = {"fp32_storage": 1e-6, "df64": 1e-12}
+    sampler = ClockSampler(0)
+    sampler.start()
+    out = {}
+    for theta in w["thetas"]:
+        row = {}
+        stats = {}
+        for name, prec, off in forms:
+            seeds = [7000 + off + i for i in range(args.longrun_chains)]
+            t0 = time.perf_counter()
+            ser = studies.longrun(L, w["beta"], theta, prec, seeds, args.longrun_steps, every=w["every"],
+                                  eps=w["eps"])
+            sec = time.perf_counter() - t0
+            st = studies.chain_means(ser)
+            stats[name] = st
+            row[name] = {"mean": dict(zip(studies.SERIES_KEYS, st["mean"].tolist())),
+                         "err": dict(zip(studies.SERIES_KEYS, st["err"].tolist())),
+                         "chains": st["chains"], "nonfinite_chains": st["dropped"], "seconds": round(sec, 2),
+                         "seeds": seeds}
+            if name == "fp64":
+                row[name]["first_chain_series"] = {k: ser[0, :, j].tolist()
+                                                   for j, k in enumerate(studies.SERIES_KEYS)}
+            _log("longrun theta %.1f %s: %.1f s" % (theta, name, sec))
+        for name in ("fp32_storage", "df64"):
+            z = studies.compare_means(stats[name], stats["fp64"], floors[name])
+            row["z_%s_vs_fp64" % name] = dict(zip(studies.SERIES_KEYS, np.round(z, 3).tolist()))
+        out["%g" % theta] = row
+    clocks = sampler.stop()
+    zmax = max(v for row in out.values() for key in row if key.startswith("z_") for v in row[key].values())
+    print(json.dumps({"metric": "long-run observables per arithmetic form (ensemble means, 3 sigma bar)",
+                      "workload": LONGRUN_NAME, "lattice": list(L), "steps": args.longrun_steps,
+                      "chains_per_form": args.longrun_chains, "thermalisation_dropped": 0.2,
+                      "max_z": zmax, "thetas": out, "clocks": clocks}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -787,10 +862,14 @@ def main():
     ap.add_argument("--no-df64", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
-    ap.add_argument("--mode", choices=["step", "batch", "serve", "cooling-study", "theta-scan", "precision"],
+    ap.add_argument("--mode", choices=["step", "batch", "serve", "cooling-study", "theta-scan", "precision",
+                                       "longrun"],
                     default="step",
                     help="step: the 32^4 single-chain step (default); batch: the chain ensemble; "
-                         "serve: the request trace; cooling-study, theta-scan: the studies of Sec. 4-5")
+                         "serve: the request trace; cooling-study, theta-scan: the studies of Sec. 4-5; "
+                         "longrun: 16^4 ensembles of the three arithmetic forms compared in distribution")
+    ap.add_argument("--longrun-chains", type=int, default=4)
+    ap.add_argument("--longrun-steps", type=int, default=1000)
     ap.add_argument("--sweeps", type=int, default=3000)
     ap.add_argument("--scan-steps", type=int, default=20000)
     ap.add_argument("--requests", type=int, default=100)
@@ -814,6 +893,8 @@ def main():
         return theta_scan_mode(args)
     if args.mode == "precision":
         return precision_mode(args)
+    if args.mode == "longrun":
+        return longrun_mode(args)
     if args.warmup < 3 and args.impl == "native":
         args.warmup = 3
     if args.impl == "reference":

@@ -413,6 +413,16 @@ cl_status cl_cool_gradient(cl_lattice* lat, double* host_f);
  * precision, nsites < 0, site0 < 0, mu outside 0..3), CL_ERR_OOM, CL_ERR_CUDA. */
 cl_status cl_noise_sample(cl_precision prec, uint64_t seed, uint32_t step, int mu, int site0, int nsites,
                           double* host_out);
+/* Self-test of the float <-> double conversions the FP32-storage kernels
+ * perform on the integer pipe (IEEE-754 field moves, round to nearest even):
+ * on n generated cases (every float bit pattern class; doubles across the
+ * float range, its underflow and overflow ends and exact rounding ties) it
+ * compares each with the hardware conversion bit for bit and returns the
+ * mismatch counts (both 0 when correct).  A diagnostic with no counterpart in
+ * the paper: current device, legacy default stream, its own 16-byte device
+ * buffer, synchronises.  Errors: CL_ERR_INVALID (NULL, n < 0), CL_ERR_OOM,
+ * CL_ERR_CUDA. */
+cl_status cl_selftest_convert(uint64_t seed, int64_t n, int64_t* bad_f2d, int64_t* bad_d2f);
 /* Topological charge density q_L(x) (Sec. 5), host doubles [site]{re,im} (2*V). */
 cl_status cl_qdensity(cl_lattice* lat, double* host_q);
 
@@ -432,7 +442,8 @@ enum {
   CL_PHASE_COOL_APPLY = 5, /* U <- Omega U Omega^{-1} */
   CL_PHASE_OBS = 6,        /* observables */
   CL_PHASE_FORCE = 7,      /* per-plaquette drift contributions (two kernels with theta) */
-  CL_NPHASE = 8
+  CL_PHASE_COOL_GRAD_OMEGA = 8, /* single-pass D_0 / D_1 sweeps: gradient and Omega in one kernel */
+  CL_NPHASE = 9
 };
 cl_status cl_set_timing(cl_lattice* lat, int on);
 cl_status cl_get_timing(cl_lattice* lat, double* ms, int64_t* launches);
@@ -457,15 +468,18 @@ void cl_free(cl_lattice* lat);
  * dev_out: device, 10 doubles written in cl_obs field order (plaquette re/im,
  *   unitarity norm, Q re/im, S_W re/im, S re/im, max |det U - 1|).
  * cuda_stream: the stream to enqueue on (NULL = legacy default stream).
- * Nothing is synchronised and no link value is checked for NaN/Inf.
+ * Nothing is synchronised.  A link with a NaN or Inf entry makes the
+ * max |det U - 1| output NaN (the other outputs are then meaningless too).
  *
  * The per-block partial sums live in one fixed device array inside the
  * library (CL_NOALLOC_MAX_BLOCKS records of 9 doubles, 147,456 bytes), which
  * every GPU that loads the library holds until the process exits; launches
  * use at most that many blocks, whatever V.  The first call on each device
  * looks up the array's device address (cudaGetSymbolAddress), so make that
- * first call before any stream capture.  All calls share the array: calls
- * that overlap on the GPU (other streams or host threads) race on it.  Errors:
+ * first call before any stream capture; the address is kept for the life
+ * of the process, so calls after cudaDeviceReset() on that device are not
+ * supported.  All calls share the array: calls that overlap on the GPU
+ * (other streams or host threads) race on it.  Errors:
  * CL_ERR_INVALID (NULL, extents, volume, device index beyond
  * CL_NOALLOC_MAX_DEVICES), CL_ERR_CUDA; text in cl_last_error(). */
 #define CL_NOALLOC_MAX_BLOCKS 2048

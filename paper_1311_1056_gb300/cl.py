@@ -123,6 +123,8 @@ SIGNATURES = {
     "cl_qdensity": (ctypes.c_int, [_P, _dp]),
     "cl_noise_sample": (ctypes.c_int, [ctypes.c_int, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int,
                                        ctypes.c_int, ctypes.c_int, _dp]),
+    "cl_selftest_convert": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                           ctypes.POINTER(ctypes.c_int64)]),
     "cl_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "cl_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "cl_get_timing": (ctypes.c_int, [_P, _dp, ctypes.POINTER(ctypes.c_int64)]),
@@ -476,6 +478,12 @@ def noise_sample(prec, seed, step, mu, site0, nsites):
     return out
 
 
+def cl_selftest_convert(seed, n):
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().cl_selftest_convert(seed, n, ctypes.byref(a), ctypes.byref(b)), "cl_selftest_convert")
+    return a.value, b.value
+
+
 def cl_qdensity(lat, V):
     out = np.empty(2 * V)
     _check(load().cl_qdensity(lat, out.ctypes.data_as(_dp)), "cl_qdensity")
@@ -488,7 +496,8 @@ def cl_launch_count(lat):
     return v.value
 
 
-PHASES = ("clover", "update", "cool_grad", "cool_rule", "cool_omega", "cool_apply", "obs", "force")
+PHASES = ("clover", "update", "cool_grad", "cool_rule", "cool_omega", "cool_apply", "obs", "force",
+          "cool_grad_omega")
 
 
 def cl_set_timing(lat, on):

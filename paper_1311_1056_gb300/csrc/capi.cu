@@ -60,8 +60,8 @@ cudaEvent_t take_event(cl_lattice* l) {
 
 // Launch through f(); with timing on, bracket it by two events on the
 // lattice's stream and remember them under `phase`.
-const char* const PHASE_NAMES[CL_NPHASE] = {"clover", "update", "cool_grad", "cool_rule",
-                                            "cool_omega", "cool_apply", "obs", "force"};
+const char* const PHASE_NAMES[CL_NPHASE] = {"clover", "update", "cool_grad", "cool_rule", "cool_omega",
+                                            "cool_apply", "obs", "force", "cool_grad_omega"};
 
 // NVTX range around the enqueue of one phase (a profiler shows the phases by
 // name; without one attached the calls cost a few nanoseconds).
@@ -184,9 +184,43 @@ cl_status check_cool(const cl_cool_params* cp) {
 
 // Enqueue the whole cooling loop; the device rule decides how many sweeps
 // actually run (later launches return at once once it says done).
+//
+// D_0 and D_1 (FP64, FP32 storage) run single-pass sweeps: their strength
+// needs only the unitarity norm, so after the first sweep each apply also
+// sums the norm of the links it writes, the rule decides the next sweep
+// from those sums, and one kernel forms the gradient and Omega together (f
+// stays in registers): rule, gradient + Omega, apply per sweep instead of
+// gradient, rule, Omega, apply.  D_2 needs sum |f_ax| before Omega, so it
+// keeps the four-kernel sweep, as does the DF64 form.
 cl_status do_cool(cl_lattice* l, const cl_cool_params* cp) {
   CoolArgs a = cool_args(cp);
   const int n_iter = cp->forced_sweeps >= 0 ? cp->forced_sweeps : cp->n_max;
+  const bool single_pass = (cp->mode == CL_D0 || cp->mode == CL_D1) && l->prec != 2;
+  if (single_pass) {
+    // sweep 0: the rule's first inputs from a plain gradient pass
+    CK(timed(l, CL_PHASE_COOL_GRAD, [&] {
+      return launch_cool_grad(l->prec, l->g, l->U, l->f, l->partials, nullptr, l->st);
+    }));
+    CK(timed(l, CL_PHASE_COOL_RULE, [&] { return launch_cool_adapt(l->g, l->partials, a, l->cs, 1, l->st); }));
+    if (n_iter == 0) return CL_OK;
+    CK(timed(l, CL_PHASE_COOL_OMEGA, [&] {
+      return launch_cool_omega(l->prec, l->g, l->f, l->Om, l->Omi, cp->eps, l->cs, l->st);
+    }));
+    CK(timed(l, CL_PHASE_COOL_APPLY, [&] {
+      return launch_cool_apply_un(l->prec, l->g, l->U, l->Om, l->Omi, l->partials, l->cs, l->st);
+    }));
+    for (int k = 1; k <= n_iter; ++k) {
+      CK(timed(l, CL_PHASE_COOL_RULE, [&] { return launch_cool_adapt(l->g, l->partials, a, l->cs, 0, l->st); }));
+      if (k == n_iter) break;
+      CK(timed(l, CL_PHASE_COOL_GRAD_OMEGA, [&] {
+        return launch_cool_grad_omega(l->prec, l->g, l->U, l->Om, l->Omi, cp->eps, l->cs, l->st);
+      }));
+      CK(timed(l, CL_PHASE_COOL_APPLY, [&] {
+        return launch_cool_apply_un(l->prec, l->g, l->U, l->Om, l->Omi, l->partials, l->cs, l->st);
+      }));
+    }
+    return CL_OK;
+  }
   for (int k = 0; k <= n_iter; ++k) {
     // the first gradient of a call always runs: the done flag still holds
     // the previous call's decision until the rule resets it (first = 1)
@@ -589,6 +623,23 @@ cl_status cl_noise_sample(cl_precision prec, uint64_t seed, uint32_t step, int m
   if (e == cudaSuccess) e = cudaMemcpy(host_out, d, bytes, cudaMemcpyDeviceToHost);
   cudaFree(d);
   if (e != cudaSuccess) return fail(CL_ERR_CUDA, cudaGetErrorString(e));
+  return CL_OK;
+}
+
+cl_status cl_selftest_convert(uint64_t seed, int64_t n, int64_t* bad_f2d, int64_t* bad_d2f) {
+  if (!bad_f2d || !bad_d2f || n < 0) return fail(CL_ERR_INVALID, "NULL argument or n < 0");
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 2 * sizeof(unsigned long long));
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA, cudaGetErrorString(e));
+  unsigned long long h[2] = {0, 0};
+  e = cudaMemset(d, 0, sizeof(h));
+  if (e == cudaSuccess) e = launch_selftest_convert(seed, (long long)n, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(CL_ERR_CUDA, cudaGetErrorString(e));
+  *bad_f2d = (int64_t)h[0];
+  *bad_d2f = (int64_t)h[1];
   return CL_OK;
 }
 

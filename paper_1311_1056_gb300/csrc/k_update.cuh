@@ -528,7 +528,7 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const t
   mat<double> Und;
   convert(Und, Un);
   cx<double> z = det_inv_cuberoot(det(Und));
-  cx<T> zt = {(T)z.re, (T)z.im};
+  cx<T> zt = {cvt<T>(z.re), cvt<T>(z.im)};
 #pragma unroll
   for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], zt);
   store(out, MU, s, g.V, Un);

@@ -3,6 +3,7 @@
 // (instantiated by k_update_f64.cu / k_update_f32.cu).
 #include <type_traits>
 
+#include "cvt.cuh"
 #include "expm.cuh"
 #include "launch.h"
 #include "lattice.cuh"
@@ -145,15 +146,15 @@ __device__ __forceinline__ df64 ldg_real(const df64* p) {
 // Packed Hermitian field: planes d0, d1, d2, re01, im01, re02, im02, re12, im12.
 template <typename T>
 __device__ __forceinline__ void store_herm(T* P, int s, int V, const herm& h) {
-  P[0 * (size_t)V + s] = (T)h.d0;
-  P[1 * (size_t)V + s] = (T)h.d1;
-  P[2 * (size_t)V + s] = (T)h.d2;
-  P[3 * (size_t)V + s] = (T)h.o01.re;
-  P[4 * (size_t)V + s] = (T)h.o01.im;
-  P[5 * (size_t)V + s] = (T)h.o02.re;
-  P[6 * (size_t)V + s] = (T)h.o02.im;
-  P[7 * (size_t)V + s] = (T)h.o12.re;
-  P[8 * (size_t)V + s] = (T)h.o12.im;
+  P[0 * (size_t)V + s] = cvt<T>(h.d0);
+  P[1 * (size_t)V + s] = cvt<T>(h.d1);
+  P[2 * (size_t)V + s] = cvt<T>(h.d2);
+  P[3 * (size_t)V + s] = cvt<T>(h.o01.re);
+  P[4 * (size_t)V + s] = cvt<T>(h.o01.im);
+  P[5 * (size_t)V + s] = cvt<T>(h.o02.re);
+  P[6 * (size_t)V + s] = cvt<T>(h.o02.im);
+  P[7 * (size_t)V + s] = cvt<T>(h.o12.re);
+  P[8 * (size_t)V + s] = cvt<T>(h.o12.im);
 }
 template <typename T>
 __device__ __forceinline__ void load_herm_mat(mat<T>& m, const T* __restrict__ P, int s, int V) {
@@ -365,8 +366,62 @@ __device__ __forceinline__ void cool_grad_df(const Geo& g, const float4* __restr
 }
 
 // f_ax = 2 Tr[lambda_a G_x], G_x = sum_mu (U_{x,mu} U_{x,mu}^+ - U_{x-mu,mu}^+ U_{x-mu,mu})
-// (Sec. 2, eq. "eq:24"); per block: sum |f|, sum f^2, sum (1/3) Tr U U^+ of
-// the links at x, nonfinite count.
+// (Sec. 2, eq. "eq:24") at site s, in the link type; returns the sum over
+// the four links at x of Tr U U^+.
+template <typename T>
+__device__ __forceinline__ T cool_grad_site(const Geo& g, const typename vec2_of<T>::type* __restrict__ U, int s,
+                                            const int x[4], T fa[8]) {
+  T g00 = T(0), g11 = T(0), g22 = T(0);
+  cx<T> g01 = {T(0), T(0)}, g02 = {T(0), T(0)}, g12 = {T(0), T(0)};
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    mat<T> u;
+    load(u, U, mu, s, g.V);
+    // + U U^+ : (i,j) = sum_k U_ik conj(U_jk)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cx<T> r0 = u.e[k], r1 = u.e[3 + k], r2 = u.e[6 + k];
+      g00 = fma(r0.re, r0.re, fma(r0.im, r0.im, g00));
+      g11 = fma(r1.re, r1.re, fma(r1.im, r1.im, g11));
+      g22 = fma(r2.re, r2.re, fma(r2.im, r2.im, g22));
+      g01 = cfma(r0, cx<T>{r1.re, -r1.im}, g01);
+      g02 = cfma(r0, cx<T>{r2.re, -r2.im}, g02);
+      g12 = cfma(r1, cx<T>{r2.re, -r2.im}, g12);
+    }
+  }
+  // sum over the four links at x of Tr U U^+ = the diagonal accumulated so far
+  const T un = g00 + g11 + g22;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    mat<T> u;
+    load(u, U, mu, hop(g, s, x, mu, -1), g.V);
+    // - U^+ U : (i,j) = sum_k conj(U_ki) U_kj
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      cx<T> c0 = u.e[3 * k], c1 = u.e[3 * k + 1], c2 = u.e[3 * k + 2];
+      g00 = fma(-c0.re, c0.re, fma(-c0.im, c0.im, g00));
+      g11 = fma(-c1.re, c1.re, fma(-c1.im, c1.im, g11));
+      g22 = fma(-c2.re, c2.re, fma(-c2.im, c2.im, g22));
+      g01 = cfms(cx<T>{c0.re, -c0.im}, c1, g01);
+      g02 = cfms(cx<T>{c0.re, -c0.im}, c2, g02);
+      g12 = cfms(cx<T>{c1.re, -c1.im}, c2, g12);
+    }
+  }
+  const T r3 = (T)0.57735026918962576451;
+  const T two = T(2), four = T(4);
+  fa[0] = four * g01.re;
+  fa[1] = -(four * g01.im);
+  fa[2] = two * (g00 - g11);
+  fa[3] = four * g02.re;
+  fa[4] = -(four * g02.im);
+  fa[5] = four * g12.re;
+  fa[6] = -(four * g12.im);
+  fa[7] = two * r3 * (g00 + g11 - two * g22);
+  return un;
+}
+
+// The gradient f into [a][V] (FP64) with, per block, sum |f|, sum f^2,
+// sum (1/3) Tr U U^+ of the links at x and the nonfinite count.
 template <typename T>
 __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                           double* __restrict__ f, double* partials,
@@ -376,66 +431,48 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename
   for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
     int x[4];
     site_coords(g, s, x);
-    T g00 = T(0), g11 = T(0), g22 = T(0);
-    cx<T> g01 = {T(0), T(0)}, g02 = {T(0), T(0)}, g12 = {T(0), T(0)};
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      mat<T> u;
-      load(u, U, mu, s, g.V);
-      // + U U^+ : (i,j) = sum_k U_ik conj(U_jk)
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        cx<T> r0 = u.e[k], r1 = u.e[3 + k], r2 = u.e[6 + k];
-        g00 = fma(r0.re, r0.re, fma(r0.im, r0.im, g00));
-        g11 = fma(r1.re, r1.re, fma(r1.im, r1.im, g11));
-        g22 = fma(r2.re, r2.re, fma(r2.im, r2.im, g22));
-        g01 = cfma(r0, cx<T>{r1.re, -r1.im}, g01);
-        g02 = cfma(r0, cx<T>{r2.re, -r2.im}, g02);
-        g12 = cfma(r1, cx<T>{r2.re, -r2.im}, g12);
-      }
-    }
-    // sum over the four links at x of Tr U U^+ = the diagonal accumulated so far
-    const T un = g00 + g11 + g22;
-#pragma unroll
-    for (int mu = 0; mu < 4; ++mu) {
-      mat<T> u;
-      load(u, U, mu, hop(g, s, x, mu, -1), g.V);
-      // - U^+ U : (i,j) = sum_k conj(U_ki) U_kj
-#pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        cx<T> c0 = u.e[3 * k], c1 = u.e[3 * k + 1], c2 = u.e[3 * k + 2];
-        g00 = fma(-c0.re, c0.re, fma(-c0.im, c0.im, g00));
-        g11 = fma(-c1.re, c1.re, fma(-c1.im, c1.im, g11));
-        g22 = fma(-c2.re, c2.re, fma(-c2.im, c2.im, g22));
-        g01 = cfms(cx<T>{c0.re, -c0.im}, c1, g01);
-        g02 = cfms(cx<T>{c0.re, -c0.im}, c2, g02);
-        g12 = cfms(cx<T>{c1.re, -c1.im}, c2, g12);
-      }
-    }
-    const T r3 = (T)0.57735026918962576451;
     T fa[8];
-    const T two = T(2), four = T(4);
-    fa[0] = four * g01.re;
-    fa[1] = -(four * g01.im);
-    fa[2] = two * (g00 - g11);
-    fa[3] = four * g02.re;
-    fa[4] = -(four * g02.im);
-    fa[5] = four * g12.re;
-    fa[6] = -(four * g12.im);
-    fa[7] = two * r3 * (g00 + g11 - two * g22);
+    const T un = cool_grad_site<T>(g, U, s, x, fa);
     bool ok = isfinite(un);
 #pragma unroll
     for (int a = 0; a < 8; ++a) {
-      const double d = (double)fa[a];
+      const double d = cvt<double>(fa[a]);
       f[(size_t)a * g.V + s] = d;
       v[0] += fabs(d);
       v[1] = fma(d, d, v[1]);
       ok = ok && isfinite(fa[a]);
     }
-    v[2] += (double)un * (1.0 / 3.0);
+    v[2] += cvt<double>(un) * (1.0 / 3.0);
     v[3] += ok ? 0.0 : 1.0;
   }
   block_reduce_store<NQ_COOL, -1>(v, partials);
+}
+
+// Single-pass sweep of the D_0 / D_1 rules, part 1: the strength alpha_ad of
+// these rules needs only the unitarity norm, which the previous sweep's apply
+// (k_cool_apply_un) summed, so the rule has decided before this kernel runs
+// and the gradient never leaves the thread: f_ax at x, then Omega_x =
+// exp(-eps alpha_ad f_ax lambda_a) and its inverse (FP64), stored packed.
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_cool_grad_omega(Geo g,
+                                                                const typename vec2_of<T>::type* __restrict__ U,
+                                                                T* __restrict__ Om, T* __restrict__ Omi, double eps,
+                                                                const CoolState* cs) {
+  if (cs->done) return;
+  const double c = -eps * cs->alpha_ad;
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    int x[4];
+    site_coords(g, s, x);
+    T fa[8];
+    cool_grad_site<T>(g, U, s, x, fa);
+    double fd[8];
+#pragma unroll
+    for (int a = 0; a < 8; ++a) fd[a] = cvt<double>(fa[a]);
+    herm h = herm_from_algebra(fd, c), om, omi;
+    expm_hermitian_pair(om, omi, h);
+    store_herm(Om, s, g.V, om);
+    store_herm(Omi, s, g.V, omi);
+  }
 }
 
 // The adaptive rule (Sec. 4): alpha_ad = alpha / D with D_0 = 1,
@@ -557,6 +594,40 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_apply(Geo g, typename v
   mul_herm_left(t, o, u);
   mul_herm_right(u, t, oi);
   store(U, mu, s, g.V, u);
+}
+
+// Single-pass sweep of the D_0 / D_1 rules, part 2: the apply, site by site
+// (Omega_x loaded once for the site's four links), with per block the sums
+// the rule needs for the next sweep: (1/3) Tr U U^+ of the updated links
+// (FP64) and their nonfinite count, in the gradient's record layout (the
+// |f| and f^2 slots are 0).
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS, 4) k_cool_apply_un(Geo g, typename vec2_of<T>::type* U,
+                                                              const T* __restrict__ Om, const T* __restrict__ Omi,
+                                                              double* partials, const CoolState* cs) {
+  if (cs->done) return;
+  double v[NQ_COOL] = {0.0, 0.0, 0.0, 0.0};
+  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+    int x[4];
+    site_coords(g, s, x);
+    mat<T> o;
+    load_herm_mat(o, Om, s, g.V);
+    T un = T(0);
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) {
+      mat<T> oi, u, t;
+      load_herm_mat(oi, Omi, hop(g, s, x, mu, 1), g.V);
+      load(u, U, mu, s, g.V);
+      mul_herm_left(t, o, u);
+      mul_herm_right(u, t, oi);
+      store(U, mu, s, g.V, u);
+      un += norm2(u);
+    }
+    // a NaN or Inf entry makes the sum of squares NaN or +Inf
+    v[2] += cvt<double>(un) * (1.0 / 3.0);
+    v[3] += isfinite(un) ? 0.0 : 1.0;
+  }
+  block_reduce_store<NQ_COOL, -1>(v, partials);
 }
 
 const int DF_APPLY_BLOCK = 128;  // the DF64 apply's largest block (its launch bound)
@@ -708,7 +779,48 @@ __global__ void k_obs_final(Geo g, const double* partials, int nb, double beta, 
   out->nonfinite = tot[8];
 }
 
+// Self-test of the integer-pipe conversions (cvt.cuh) against the hardware
+// ones, bit for bit (NaN against NaN).  Case i draws 64 random bits by the
+// SplitMix64 finaliser of seed + i: all 32-bit float patterns (every exponent,
+// subnormals, infinities, NaNs) for f2d; for d2f doubles whose exponent spans
+// the float range and both its ends (underflow to zero, overflow to inf),
+// every fourth an exact rounding tie, every eighth a full random pattern.
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+  z += 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+__global__ void k_selftest_convert(uint64_t seed, long long n, unsigned long long* bad) {
+  unsigned long long b0 = 0, b1 = 0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint64_t r = splitmix64(seed + (uint64_t)i), q = splitmix64(r);
+    const float f = __uint_as_float((unsigned)r);
+    const double a = f2d(f), b = (double)f;
+    if (!(isnan(a) && isnan(b)) && __double_as_longlong(a) != __double_as_longlong(b)) ++b0;
+    uint64_t bits;
+    if ((i & 7) == 7) {
+      bits = q;
+    } else {
+      const uint64_t e = 860u + (q >> 52) % 310u;  // float underflow .. overflow
+      uint64_t m = q & 0xfffffffffffffull;
+      if ((i & 3) == 0) m = (m & ~0x1fffffffull) | 0x10000000ull;  // exact tie
+      bits = ((r >> 63) << 63) | (e << 52) | m;
+    }
+    const double d = __longlong_as_double((long long)bits);
+    const float x = d2f(d), y = __double2float_rn(d);
+    if (!(isnan(x) && isnan(y)) && __float_as_uint(x) != __float_as_uint(y)) ++b1;
+  }
+  if (b0) atomicAdd(bad, b0);
+  if (b1) atomicAdd(bad + 1, b1);
+}
+
 }  // namespace
+
+cudaError_t launch_selftest_convert(uint64_t seed, long long n, unsigned long long* bad, cudaStream_t st) {
+  k_selftest_convert<<<RED_MAX_BLOCKS, RED_THREADS, 0, st>>>(seed, n, bad);
+  return cudaGetLastError();
+}
 
 // Reduction kernels loop over sites with at most RED_MAX_BLOCKS blocks, so
 // the one-block rule reads few records; the split depends on V only.
@@ -827,6 +939,34 @@ cudaError_t launch_cool_apply(int prec, const GeoH& h, void* U, const void* Om, 
     } else
       k_cool_apply<T><<<grid, bs, 0, st>>>(g, (typename vec2_of<T>::type*)U, (const T*)Om, (const T*)Omi, cs);
   });
+}
+
+cudaError_t launch_cool_grad_omega(int prec, const GeoH& h, const void* U, void* Om, void* Omi, double eps,
+                                   const CoolState* cs, cudaStream_t st) {
+  Geo g = to_geo(h);
+  if (prec == 0)
+    k_cool_grad_omega<double><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const double2*)U, (double*)Om,
+                                                                          (double*)Omi, eps, cs);
+  else if (prec == 1)
+    k_cool_grad_omega<float><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (const float2*)U, (float*)Om,
+                                                                         (float*)Omi, eps, cs);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cool_apply_un(int prec, const GeoH& h, void* U, const void* Om, const void* Omi,
+                                 double* partials, const CoolState* cs, cudaStream_t st) {
+  Geo g = to_geo(h);
+  if (prec == 0)
+    k_cool_apply_un<double><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (double2*)U, (const double*)Om,
+                                                                        (const double*)Omi, partials, cs);
+  else if (prec == 1)
+    k_cool_apply_un<float><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (float2*)U, (const float*)Om,
+                                                                       (const float*)Omi, partials, cs);
+  else
+    return cudaErrorInvalidValue;
+  return cudaGetLastError();
 }
 
 cudaError_t launch_obs(int prec, const GeoH& h, const void* U, const void* F, int with_q,

@@ -109,11 +109,23 @@ cudaError_t launch_cool_omega(int prec, const GeoH& g, const void* f, void* Om, 
                               double eps, const CoolState* cs, cudaStream_t st);
 cudaError_t launch_cool_apply(int prec, const GeoH& g, void* U, const void* Om, const void* Omi,
                               const CoolState* cs, cudaStream_t st);
+// Single-pass sweep of the D_0 / D_1 rules (FP64 and FP32 storage only):
+// Omega and Omega^{-1} straight from the gradient with the strength the rule
+// already set, then the apply with the rule's inputs for the next sweep
+// (unitarity norm, nonfinite count) in `partials` (the gradient's layout).
+cudaError_t launch_cool_grad_omega(int prec, const GeoH& g, const void* U, void* Om, void* Omi, double eps,
+                                   const CoolState* cs, cudaStream_t st);
+cudaError_t launch_cool_apply_un(int prec, const GeoH& g, void* U, const void* Om, const void* Omi,
+                                 double* partials, const CoolState* cs, cudaStream_t st);
 // Observables: per-site pass (F must hold the unscaled clover field when
 // with_q) then the final fixed-order reduction into *out.
 cudaError_t launch_obs(int prec, const GeoH& g, const void* U, const void* F, int with_q,
                        double* partials, double* q_site, cudaStream_t st);
 cudaError_t launch_obs_final(const GeoH& g, const double* partials, double beta, double th_re,
                              double th_im, ObsOut* out, cudaStream_t st);
+// Integer-pipe float <-> double conversions (cvt.cuh) against the hardware
+// ones on n generated cases; mismatch counts added into bad[0] (float ->
+// double) and bad[1] (double -> float).
+cudaError_t launch_selftest_convert(uint64_t seed, long long n, unsigned long long* bad, cudaStream_t st);
 
 }  // namespace clgc

@@ -188,7 +188,7 @@ __global__ void k_obs_noalloc_final(Geo g, const double* __restrict__ partials, 
   out[6] = sw_im;                           // sw_im
   out[7] = sw_re + th_re * t[6] + th_im * t[5];  // S = S_W - i theta Q
   out[8] = sw_im - th_re * t[5] + th_im * t[6];
-  out[9] = t[7];                            // max |det U - 1|
+  out[9] = (t[8] > 0.0) ? nan("") : t[7];   // max |det U - 1|; NaN if a link is not finite
 }
 
 cl_status na_fail(cl_status s, const std::string& m) {

@@ -12,6 +12,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "cvt.cuh"
 #include "df64.cuh"
 
 namespace clgc {
@@ -386,10 +387,24 @@ __device__ __forceinline__ T norm2(const mat<T>& a) {
   return s;
 }
 
+// One real from type S to type D; float <-> double on the integer pipe (cvt.cuh).
+template <typename D, typename S>
+__device__ __forceinline__ D cvt(S x) {
+  return (D)x;
+}
+template <>
+__device__ __forceinline__ double cvt<double, float>(float x) {
+  return f2d(x);
+}
+template <>
+__device__ __forceinline__ float cvt<float, double>(double x) {
+  return d2f(x);
+}
+
 template <typename D, typename S>
 __device__ __forceinline__ void convert(mat<D>& d, const mat<S>& s) {
 #pragma unroll
-  for (int k = 0; k < 9; ++k) d.e[k] = cx<D>{(D)s.e[k].re, (D)s.e[k].im};
+  for (int k = 0; k < 9; ++k) d.e[k] = cx<D>{cvt<D>(s.e[k].re), cvt<D>(s.e[k].im)};
 }
 
 // SoA field access: element k of matrix (plane, site) at ((plane*9 + k)*V + site).

@@ -13,6 +13,12 @@
   theta_L^2 = 0, +-1, +-4 (Sec. 5), as one batch of chains; returns the
   series of the plaquette, Q_L and the unitarity norm.
 
+* longrun: independent chains (one Philox seed each) of CL with adaptive
+  cooling advanced together as one batch, the observables of every chain
+  recorded every few steps; and chain_means / compare_means, the statistics
+  that compare two such ensembles (long trajectories decorrelate
+  chaotically, so two arithmetic forms can only agree in distribution).
+
 Every number comes from the CUDA kernels through the C-ABI (cl.py).
 """
 import numpy as np
@@ -128,3 +134,64 @@ def precision_table(L=(32, 32, 32, 32), beta=6.2, theta=1.0, eps=0.005, sweeps=1
                 row[k] = (oa[k], d, d / abs(oa[k]) if oa[k] != 0 else None)
             out[n] = row
     return out
+
+
+SERIES_KEYS = ("plaq_re", "plaq_im", "un", "q_re", "q_im")
+
+
+def longrun_cool(eps=0.005):
+    """The adaptive rule of the long runs: alpha_ad = 0.1 / D_2 (D_2 = <|f_ax|>),
+    0..10 sweeps, stop below 1 % relative progress or within 1e-6 of SU(3)."""
+    return cl.make_cool(eps, 0.1, cl.CL_D2_MEANABS, n_min=0, n_max=10, tol_rel=0.01, d_floor=1e-6)
+
+
+def longrun(L, beta, theta, prec, seeds, n_steps, every=10, eps=0.005, cool=None, k_ref=0.0):
+    """Chains from the cold start, one per seed, advanced together (one batch
+    graph launch per step); every `every` steps the observables of each chain.
+    Returns an array (n_chains, n_steps // every, len(SERIES_KEYS))."""
+    cp = cool if cool is not None else longrun_cool(eps)
+    lats = []
+    for sd in seeds:
+        lat = cl.Lattice(L, beta=beta, theta=theta, prec=prec, seed=int(sd), start=cl.CL_START_COLD,
+                         own_stream=True)
+        if k_ref > 0.0:
+            lat.set_adaptive_step(k_ref)
+        lats.append(lat)
+    out = np.zeros((len(lats), n_steps // every, len(SERIES_KEYS)))
+    try:
+        with cl.Batch(lats, eps, [cp] * len(lats)) as b:
+            for r in range(n_steps // every):
+                b.run(every)
+                b.synchronize()
+                for i, lat in enumerate(lats):
+                    o = cl.cl_observables(lat.h, check=False)
+                    out[i, r] = [o[k] for k in SERIES_KEYS]
+    finally:
+        for lat in lats:
+            lat.close()
+    return out
+
+
+def chain_means(series, drop=0.2):
+    """Per-chain means after dropping the first `drop` of each series
+    (thermalisation), then the ensemble mean and its standard error from the
+    chain-to-chain scatter (the chains are independent).  Chains with a
+    non-finite record are left out and counted."""
+    series = np.asarray(series)
+    n0 = int(series.shape[1] * drop)
+    ok = np.all(np.isfinite(series), axis=(1, 2))
+    m = series[ok, n0:, :].mean(axis=1)
+    k = m.shape[0]
+    mean = m.mean(axis=0)
+    err = m.std(axis=0, ddof=1) / np.sqrt(k) if k > 1 else np.full(m.shape[1], np.inf)
+    return {"mean": mean, "err": err, "chains": k, "dropped": int((~ok).sum())}
+
+
+def compare_means(a, b, rel_floor=1e-12):
+    """z = |mean_a - mean_b| / sqrt(err_a^2 + err_b^2 + floor^2) per
+    observable, floor = rel_floor * max(1, |mean|): the rounding level of the
+    coarser form, below which two means count as equal (UN = 1 on SU(3) is
+    exact in one form and 1 + O(rounding) in another)."""
+    d = np.abs(a["mean"] - b["mean"])
+    floor = rel_floor * np.maximum(1.0, np.abs(a["mean"]))
+    return d / np.sqrt(a["err"] ** 2 + b["err"] ** 2 + floor ** 2)

@@ -37,7 +37,7 @@ def test_device_rule_count(case, prec):
     with cl.Lattice(L1, prec=prec) as lat:
         lat.set_links(M.lattice(d0, c))
         rep = lat.cool(cl.make_cool(eps, alpha, mode, n_min, n_max, tol, d_floor, guard))
-    tol_un = 1e-13 if prec != cl.CL_FP32_STORAGE else 1e-5
+    tol_un = {cl.CL_FP64: 1e-13, cl.CL_DF64: 1e-12, cl.CL_FP32_STORAGE: 1e-5}[prec]
     assert rep["sweeps"] == P["sweeps"]
     assert abs(rep["un_before"] - P["un_before"]) < tol_un
     assert abs(rep["un_after"] - P["un_after"]) < tol_un

@@ -98,3 +98,59 @@ def test_theta_dependence_of_q_at_small_theta():
     assert q1.imag > 3 * e1 and q2.imag > q1.imag
     assert p1.real < -3 * f1 and p2.real < p1.real
     assert abs(q1.imag + p1.real) < 4 * np.hypot(e1, f1)  # the same chi for real and imaginary theta
+
+
+# ------------------------------------------------- SU(3) lattices (NEXT-2)
+def _oracle_lattice_cooling(L, mode, alpha, eps, sweeps, sigma, seed):
+    """d after each of `sweeps` single-sweep cooling calls of the oracle, from
+    the cold start transformed by the oracle's random SL(3,C) gauge
+    transformation (the same Philox stream the library's start uses)."""
+    U = O.random_gauge(L, O.cold_start(L), seed, sigma)
+    d = []
+    for _ in range(sweeps):
+        U, rep = O.cool(L, U, O.cool_params(eps, alpha, mode, forced_sweeps=1))
+        d.append(rep["un_after"] - 1.0)
+    return np.array(d)
+
+
+@pytest.mark.parametrize("mode,omode", [("D0", O.D0), ("D1", O.D1), ("D2", O.D2_MEANABS)])
+def test_lattice_cooling_series_matches_oracle(mode, omode):
+    """Sec. 4 on an SU(3) lattice: the distance d = UN - 1 after each of the
+    first 20 sweeps of the study (one cooling call per sweep) equals the
+    oracle's, to 1e-12, for D_0, D_1 and D_2 (4 x 3 x 5 x 2, every loop wraps)."""
+    L, alpha, eps, sigma, seed = (4, 3, 5, 2), 1.0, 0.01, 0.1, 3
+    d_gpu = studies.lattice_cooling(L, mode, alpha=alpha, eps=eps, sweeps=20, sigma=sigma, seed=seed)
+    d_or = _oracle_lattice_cooling(L, omode, alpha, eps, 20, sigma, seed)
+    assert d_or[0] > 1e-3
+    assert np.abs(d_gpu - d_or).max() < 1e-12, np.abs(d_gpu - d_or).max()
+
+
+def test_lattice_cooling_d0_d1_d2():
+    """Sec. 4 on an 8^4 SU(3) lattice (cold start moved off SU(3) by a random
+    SL(3,C) transformation): with the fixed strength (D_0) and the norm
+    normalisation (D_1) the distance falls every sweep and keeps falling past
+    1e-5; D_1 ~ D_0 here because UN ~ 1.  The normalised-gradient rule D_2
+    takes a step of fixed size whatever |f| is, so at alpha = 1 it stalls on a
+    plateau above 1e-4 (it never reaches 1e-5); at alpha = 0.1 it descends
+    more slowly and stalls on a plateau two orders of magnitude lower (the
+    step shrinks with alpha)."""
+    L, eps, sweeps = (8, 8, 8, 8), 0.01, 120
+    d0 = studies.lattice_cooling(L, "D0", alpha=1.0, eps=eps, sweeps=sweeps)
+    d1 = studies.lattice_cooling(L, "D1", alpha=1.0, eps=eps, sweeps=sweeps)
+    d2 = studies.lattice_cooling(L, "D2", alpha=1.0, eps=eps, sweeps=sweeps)
+    d2s = studies.lattice_cooling(L, "D2", alpha=0.1, eps=eps, sweeps=300)
+    s0, s1, s2 = (studies.summarize(d) for d in (d0, d1, d2))
+    # D_0 / D_1: monotone decrease, both thresholds reached, nearly in step
+    for d in (d0, d1):
+        live = d[d > 1e-13]
+        assert np.all(np.diff(live) < 0)
+    assert s0["first_sweep_below"]["1e-05"] is not None and s1["first_sweep_below"]["1e-05"] is not None
+    assert abs(s0["first_sweep_below"]["0.001"] - s1["first_sweep_below"]["0.001"]) <= 1
+    # D_2 at alpha = 1: never below 1e-5, and flat over the last half (a plateau)
+    assert s2["first_sweep_below"]["1e-05"] is None
+    tail = d2[sweeps // 2:]
+    assert tail.min() > 1e-4 and tail.max() < 3 * tail.min()
+    # a smaller alpha: slower descent, then a much lower plateau
+    s2s = studies.summarize(d2s)
+    assert s2s["first_sweep_below"]["0.001"] > 3 * s2["first_sweep_below"]["0.001"]
+    assert d2s[150:].max() < 0.1 * tail.min()
