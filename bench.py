@@ -357,12 +357,18 @@ def e2e_measure(cl, torch, lat, V, one_step, steps):
                                  "step_and_get_links": round(t_get / steps * 1e3, 3)}}
 
 
-# FP32 floating-point operations per site that the DF64 kernels execute
-# (FFMA = 2, FADD = FMUL = 1), from ncu's executed-instruction counters on one
-# launch at 24^4 (smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on,
-# profiles/ncu_df64_fp32_ops_24x4.md) divided by the 331,776 sites: these
-# kernels load the FP32 pipe, so their roofline is that pipe's peak.
-DF64_FP32_FLOPS_PER_SITE = {}
+# FP32 instructions per site that the DF64 kernels execute, from ncu's
+# executed-instruction counters on one launch at 24^4
+# (smsp__sass_thread_inst_executed_op_{ffma,fadd,fmul}_pred_on.sum divided by
+# the 331,776 sites; profiles/ncu_df64_fp32_ops_24x4.md).  These kernels load
+# the FP32 pipe, so their roofline is that pipe: flops (FFMA = 2) against the
+# FP32 peak, and FP32-pipe instructions against the pipe's issue rate (the
+# error-free transformations are mostly FADDs, one flop per issue slot).
+DF64_FP32_OPS_PER_SITE = {
+    "force": {"ffma": 43740, "fadd": 126684, "fmul": 14580},
+    "cool_grad": {"ffma": 1323, "fadd": 4211, "fmul": 513},
+    "cool_apply": {"ffma": 2160, "fadd": 5472, "fmul": 720},
+}
 
 
 def fp32_peak_tflops(sm_max_mhz):
@@ -382,14 +388,22 @@ def roofline_of(prec_name, V, phases, sm_max_mhz, theta_on=True):
     if prec_name == "df64":
         # double-float arithmetic runs on the FP32 pipe: its executed FP32
         # operations (ncu counts) against the FP32 peak
-        per_site = DF64_FP32_FLOPS_PER_SITE.get(dom)
+        ops = DF64_FP32_OPS_PER_SITE.get(dom)
         peak = fp32_peak_tflops(sm_max_mhz)
-        src = ("executed FP32 operations of the double-float kernels (ncu, 24^4) against "
+        src = ("executed FP32 operations of the double-float kernels (ncu, 24^4, FFMA = 2 flops) against "
                "152 SMs x 128 FP32 FMA/clk x %d MHz (FP32 is not in MEASURED_PEAKS.json)" % sm_max_mhz)
-        flops = per_site * V if per_site else None
-        ach = flops / (per * 1e-3) / 1e12 if flops else None
-        return {"kernel": dom, "bound": "alu", "pipe": "fp32", "achieved": round(ach, 4) if ach else None,
-                "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(ach / peak, 4) if ach else None,
+        if not ops:
+            return {"kernel": dom, "bound": "alu", "pipe": "fp32", "achieved": None, "peak": round(peak, 4),
+                    "unit": "TFLOP/s", "frac": None, "traffic": dram_traffic(dom, prec_name),
+                    "avg_launch_ms": round(per, 4), "launches": n, "peak_source": src}
+        flops = (2 * ops["ffma"] + ops["fadd"] + ops["fmul"]) * V
+        inst = (ops["ffma"] + ops["fadd"] + ops["fmul"]) * V
+        ach = flops / (per * 1e-3) / 1e12
+        inst_rate = inst / (per * 1e-3) / 1e12
+        inst_peak = peak / 2
+        return {"kernel": dom, "bound": "alu", "pipe": "fp32", "achieved": round(ach, 4),
+                "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
+                "fp32_pipe_inst_per_s": round(inst_rate * 1e12, 1), "fp32_pipe_inst_frac": round(inst_rate / inst_peak, 4),
                 "traffic": dram_traffic(dom, prec_name), "flops_per_launch": flops,
                 "avg_launch_ms": round(per, 4), "launches": n, "peak_source": src}
     flops = fm[dom] * V
