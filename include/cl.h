@@ -112,10 +112,11 @@ typedef struct {
 /* Create a lattice on the current CUDA device and initialise its links
  * (start, then the optional random gauge transformation).  cuda_stream is a
  * cudaStream_t (may be NULL).  On success *out owns the device memory
- * (per site: 60 complex 3x3 matrices -- links, a second link buffer,
- * inverses, plaquettes, their differences, the clover field, the drift
- * contributions and their partial sums -- plus cooling scratch: 8.8 KB in
- * FP64, 4.5 KB in FP32; cl_lattice_bytes gives the exact figure).
+ * (per site: 54 complex 3x3 matrices -- links, a second link buffer,
+ * inverses, plaquettes, their differences, the clover field and the 24 drift
+ * contributions, whose planes also hold the theta force's parked partial
+ * sums and, outside the CL step, the cooling fields: 7,776 bytes in FP64 and
+ * DF64, 3,888 in FP32; cl_lattice_bytes gives the exact figure).
  * Errors: CL_ERR_INVALID (NULL, extents < 1, V*6*9 beyond int range),
  * CL_ERR_OOM, CL_ERR_CUDA. */
 cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice** out);
@@ -128,9 +129,10 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
 cl_status cl_reset_lattice(cl_lattice* lat, const cl_params* params);
 
 /* Device bytes cl_init_lattice allocates for params (links, the second link
- * buffer, link inverses, plaquettes, drift slots, clover field, cooling
- * fields and reduction records; the optional staging buffer of the host link
- * exchange is not included).  Errors: CL_ERR_INVALID. */
+ * buffer, link inverses, plaquettes, drift slots -- which also hold the
+ * cooling fields --, clover field and reduction records; the optional
+ * staging buffer of the host link exchange is not included).
+ * Errors: CL_ERR_INVALID. */
 cl_status cl_lattice_bytes(const cl_params* params, size_t* bytes);
 
 /* n_steps complex Langevin steps, no cooling (Sec. 2; the update

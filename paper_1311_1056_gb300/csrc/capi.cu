@@ -275,9 +275,9 @@ namespace clrt {
 // Device bytes of one lattice (the buffers cl_init_lattice allocates).
 size_t lattice_bytes(int V, int prec) {
   const size_t Vs = (size_t)V, esz = prec == 1 ? 8 : 16, real = prec == 1 ? 4 : 8;
-  return esz * 9 * Vs * (4 + 4 + 4 + 6 + 6 + 24 + 6 + 6) + sizeof(double) * 8 * Vs + real * 9 * Vs * 2 +
-         sizeof(double) * NQ_OBS * (size_t)reduce_blocks(V) + sizeof(CoolState) + sizeof(ObsOut) +
-         sizeof(uint32_t);
+  (void)real;  // the cooling fields and the parked force partials live inside C (see cl_init_lattice)
+  return esz * 9 * Vs * (4 + 4 + 4 + 6 + 6 + 24 + 6) + sizeof(double) * NQ_OBS * (size_t)reduce_blocks(V) +
+         sizeof(CoolState) + sizeof(ObsOut) + sizeof(uint32_t);
 }
 
 // Start field, step counter and cooling state from l->p (cold or Haar start,
@@ -341,11 +341,9 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
   alloc(&l->Pq, l->esz * 6 * 9 * Vs);
   alloc(&l->Dq, l->esz * 6 * 9 * Vs);
   alloc(&l->C, l->esz * 24 * 9 * Vs);
-  alloc(&l->Gq, l->esz * 6 * 9 * Vs);
+
   alloc(&l->F, l->esz * 6 * 9 * Vs);
-  alloc(&l->f, sizeof(double) * 8 * Vs);
-  alloc(&l->Om, real_size(l) * 9 * Vs);
-  alloc(&l->Omi, real_size(l) * 9 * Vs);
+
   alloc((void**)&l->partials, sizeof(double) * NQ_OBS * (size_t)reduce_blocks(l->g.V));
   alloc((void**)&l->cs, sizeof(CoolState));
   alloc((void**)&l->obs, sizeof(ObsOut));
@@ -353,6 +351,23 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
   if (s != CL_OK) {
     cl_free(l);
     return s;
+  }
+  // Buffers that live inside C, whose 24 planes of drift contributions are
+  // dead outside the CL step's force -> update window:
+  //  * Gq, the split force's parked partial sums: plane p at C plane 4p + 1
+  //    (Gq points at plane 1; the force kernels index it GQ_PLANE * p), the
+  //    slot that stage b writes only after reading the partial back;
+  //  * the cooling fields f (8 reals per site, [a][V]) and the packed
+  //    Hermitian Omega, Omega^{-1} (9 reals per site each), used only by the
+  //    cooling sweeps and the start's gauge transformation, never while C
+  //    holds drift contributions.  They need 8 + 8 + 9 * 2 * 8 bytes per site
+  //    at most, C has 24 * 9 * 8 or more.
+  {
+    char* c = (char*)l->C;
+    l->Gq = c + l->esz * 9 * Vs;
+    l->f = c;
+    l->Om = c + sizeof(double) * 8 * Vs;
+    l->Omi = c + sizeof(double) * 8 * Vs + real_size(l) * 9 * Vs;
   }
   cudaError_t e = l->prec == 2 ? prepare_df64_kernels() : cudaSuccess;
   if (e == cudaSuccess) e = init_state(l);
@@ -1254,7 +1269,7 @@ cl_status cl_synchronize(cl_lattice* l) {
 
 void cl_free(cl_lattice* l) {
   if (!l) return;
-  void* bufs[] = {l->U, l->Un, l->Ui, l->Pq, l->Dq, l->C, l->Gq, l->F, l->f, l->Om, l->Omi, l->partials, l->cs, l->obs,
+  void* bufs[] = {l->U, l->Un, l->Ui, l->Pq, l->Dq, l->C, l->F, l->partials, l->cs, l->obs,
                   l->stage, l->qsite, l->sd};
   for (int v = 0; v < 2; ++v)
     if (l->gexec[v]) cudaGraphExecDestroy(l->gexec[v]);

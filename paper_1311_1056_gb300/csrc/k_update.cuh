@@ -332,13 +332,19 @@ __device__ __forceinline__ void force_stage_b(mat<T>& Gh, const Geo& g, int s, c
   store(C, 4 * p + 3, s, g.V, M);
 }
 
-// Split form (FP64): stage a, G^ parked in Gq, stage b.
+// Split form (FP64): stage a, G^ parked in Gq, stage b.  Gq is not a buffer
+// of its own: the partial of plaquette (p, s) sits in plane 4p + 1 of C (Gq
+// points at plane 1 of C, so Gq plane GQ_PLANE * p is C plane 4p + 1), the
+// slot-1 contribution of that same plaquette, which only stage b writes, and
+// only after the same thread has read the partial back.  Gq and C may alias,
+// so neither carries __restrict__ and stage b reads Gq with a plain load.
+const int GQ_PLANE = 4;
 template <typename T>
 __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_a(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                       const typename vec2_of<T>::type* __restrict__ Ui,
                                                       const typename vec2_of<T>::type* __restrict__ Dq,
                                                       const typename vec2_of<T>::type* __restrict__ F,
-                                                      typename vec2_of<T>::type* __restrict__ Gq,
+                                                      typename vec2_of<T>::type* Gq,
                                                       typename vec2_of<T>::type* C, T beta6) {
   const int p = blockIdx.x % 6;
   const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
@@ -348,7 +354,7 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_a(Geo g, const ty
   Work<T, 1> wg(0);
   mat<T>& Gh = wg[0];
   force_stage_a(Gh, g, s, x, p, U, Ui, Dq, F, C, beta6);
-  store(Gq, p, s, g.V, Gh);
+  store(Gq, GQ_PLANE * p, s, g.V, Gh);
 }
 template <typename T>
 __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_b(Geo g, const typename vec2_of<T>::type* __restrict__ U,
@@ -356,7 +362,7 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_b(Geo g, const ty
                                                       const typename vec2_of<T>::type* __restrict__ Pq,
                                                       const typename vec2_of<T>::type* __restrict__ Dq,
                                                       const typename vec2_of<T>::type* __restrict__ F,
-                                                      const typename vec2_of<T>::type* __restrict__ Gq,
+                                                      const typename vec2_of<T>::type* Gq,
                                                       typename vec2_of<T>::type* C, T beta6) {
   const int p = blockIdx.x % 6;
   const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_b(Geo g, const ty
   site_coords(g, s, x);
   Work<T, 1> wg(0);
   mat<T>& Gh = wg[0];
-  load(Gh, Gq, p, s, g.V);
+  load_rw(Gh, Gq, GQ_PLANE * p, s, g.V);  // before stage b writes slot 1 of (p, s) over it
   force_stage_b(Gh, g, s, x, p, U, Ui, Pq, Dq, F, C, beta6);
 }
 // Fused form (FP32, which needs no split to stay in registers).

@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(DF_FORCE_BLOCK, 3) k_plaq_force_a_df(Geo g, co
                                                                     const float4* __restrict__ Ui,
                                                                     const float4* __restrict__ Dq,
                                                                     const float4* __restrict__ F,
-                                                                    float4* __restrict__ Gq, float4* C,
+                                                                    float4* Gq, float4* C,
                                                                     df64 beta6) {
   const int p = blockIdx.x % 6;
   const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
@@ -213,14 +213,14 @@ __global__ void __launch_bounds__(DF_FORCE_BLOCK, 3) k_plaq_force_a_df(Geo g, co
   Work<df64, 1> wg(0);
   mat<df64>& Gh = wg[0];
   force_stage_a_df(Gh, g, s, x, p, U, Ui, Dq, F, C, beta6);
-  store(Gq, p, s, g.V, Gh);
+  store(Gq, GQ_PLANE * p, s, g.V, Gh);  // plane 4p + 1 of C (see k_plaq_force_a)
 }
 __global__ void __launch_bounds__(DF_FORCE_BLOCK, 3) k_plaq_force_b_df(Geo g, const float4* __restrict__ U,
                                                                     const float4* __restrict__ Ui,
                                                                     const float4* __restrict__ Pq,
                                                                     const float4* __restrict__ Dq,
                                                                     const float4* __restrict__ F,
-                                                                    const float4* __restrict__ Gq, float4* C,
+                                                                    const float4* Gq, float4* C,
                                                                     df64 beta6) {
   const int p = blockIdx.x % 6;
   const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
@@ -229,7 +229,7 @@ __global__ void __launch_bounds__(DF_FORCE_BLOCK, 3) k_plaq_force_b_df(Geo g, co
   site_coords(g, s, x);
   Work<df64, 1> wg(0);
   mat<df64>& Gh = wg[0];
-  load(Gh, Gq, p, s, g.V);
+  load_rw(Gh, Gq, GQ_PLANE * p, s, g.V);  // before stage b writes slot 1 of (p, s) over it
   force_stage_b_df(Gh, g, s, x, p, U, Ui, Pq, Dq, F, C, beta6);
 }
 

@@ -22,11 +22,11 @@ struct cl_lattice {
   void* Pq;    // plaquettes [6][9][V]
   void* Dq;    // P - P^{-1} [6][9][V]
   void* C;     // per-plaquette drift contributions [24][9][V]
-  void* Gq;    // partial sums of transported dual fields [6][9][V]
+  void* Gq;    // partial sums of transported dual fields: plane p at C plane 4p + 1 (inside C)
   void* F;     // clover field, SoA [6][9][V]
-  void* f;     // cooling gradient [8][V] (FP64 in both forms)
-  void* Om;    // packed Hermitian Omega [9][V]
-  void* Omi;   // and its inverse
+  void* f;     // cooling gradient [8][V] (FP64 in both forms; inside C)
+  void* Om;    // packed Hermitian Omega [9][V] (inside C)
+  void* Omi;   // and its inverse (inside C)
   double* partials;
   clgc::CoolState* cs;
   clgc::ObsOut* obs;
