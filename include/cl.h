@@ -59,7 +59,7 @@ typedef enum {
   CL_ERR_CUDA = 3,      /* a CUDA runtime error; see cl_last_error() */
   CL_ERR_NONFINITE = 4, /* a NaN/Inf appeared in the links (CL runaway) */
   CL_ERR_RUNAWAY = 5,   /* unitarity norm above the caller's bound */
-  CL_ERR_TIMEOUT = 6    /* a bounded device wait gave up */
+  CL_ERR_TIMEOUT = 6    /* a bounded wait for device work gave up (cl_wait, cl_batch_wait) */
 } cl_status;
 
 typedef enum { CL_FP64 = 0, CL_FP32_STORAGE = 1, CL_DF64 = 2 } cl_precision;
@@ -228,11 +228,12 @@ cl_status cl_stream_destroy(void* stream);
 cl_status cl_capture_step(cl_lattice* lat, double eps, const cl_cool_params* cp);
 cl_status cl_replay(cl_lattice* lat, int n_steps);
 
-/* An ensemble of independent chains advanced together: one CUDA graph forks
- * from an internal stream to every lattice's own stream, records one step of
- * each chain (eps[i], and cooling cps[i] when with_cooling), and joins back,
- * so one graph launch advances every chain by one step and the GPU runs the
- * chains' kernels concurrently.  The lattices stay owned by the caller and
+/* An ensemble of independent chains advanced together: one graph launch
+ * advances every chain by one step (eps[i], and cooling cps[i] when
+ * with_cooling) -- fused launches over all chains' blocks (see
+ * cl_batch_set_fused), or a graph that forks from an internal stream to every
+ * lattice's own stream, records each chain's own kernels and joins back, so
+ * that the GPU runs the chains' kernels concurrently.  The lattices stay owned by the caller and
  * must outlive the batch; while in a batch they are advanced with
  * cl_batch_run (a lattice stepped on its own is detected and refused with
  * CL_ERR_INVALID).  cl_batch_run orders itself after work already queued on
@@ -253,8 +254,25 @@ cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
 cl_status cl_batch_add(cl_batch* batch, cl_lattice* lat, double eps, const cl_cool_params* cp);
 cl_status cl_batch_remove(cl_batch* batch, cl_lattice* lat);
 cl_status cl_batch_size(const cl_batch* batch, int* n);
+/* Fused mode: instead of every chain's own kernels on its own stream, one
+ * launch per kernel family runs the blocks of all chains (each block runs
+ * its chain's kernel body with that chain's geometry, buffers and state, so
+ * every chain's arithmetic, noise and cooling decisions are exactly those of
+ * its own launches); the launches of one step are captured as one graph on
+ * the batch's internal stream.  All members must have the same precision,
+ * FP64 or FP32 storage (CL_ERR_INVALID otherwise; the batch then stays in
+ * its previous mode).  cl_batch_create starts a batch fused when its
+ * members allow it, else with per-chain graphs; cl_batch_add of a member of
+ * another precision switches a fused batch to per-chain graphs.  Setting the
+ * mode re-captures the batch (waits for its pending work).  The launches of
+ * a fused step are counted on the first member's cl_launch_count (the others
+ * share them).  cl_batch_get_fused returns the mode.  Errors:
+ * CL_ERR_INVALID, CL_ERR_OOM, CL_ERR_CUDA. */
+cl_status cl_batch_set_fused(cl_batch* batch, int fused);
+cl_status cl_batch_get_fused(const cl_batch* batch, int* fused);
 cl_status cl_batch_run(cl_batch* batch, int n_steps);
 cl_status cl_batch_synchronize(cl_batch* batch);
+cl_status cl_batch_wait(cl_batch* batch, double timeout_s);  /* as cl_wait, for the batch */
 void cl_batch_free(cl_batch* batch);
 
 /* ------------------------------------------------------ SU(2) Polyakov chain
@@ -454,6 +472,14 @@ cl_status cl_get_timing(cl_lattice* lat, double* ms, int64_t* launches);
 cl_status cl_launch_count(const cl_lattice* lat, int64_t* count);
 /* Wait for the lattice's stream. */
 cl_status cl_synchronize(cl_lattice* lat);
+/* Bounded wait: returns CL_OK once all work queued on the lattice's stream
+ * (or, for cl_batch_wait, the batch's) has finished, or CL_ERR_TIMEOUT when
+ * timeout_s seconds pass first -- the work keeps running and may be waited
+ * for again.  A caller (a server, a watchdog) uses it to detect a chain that
+ * takes longer than it should without blocking on it.  The host polls the
+ * stream; nothing waits on the device.  Errors: CL_ERR_INVALID (NULL,
+ * timeout_s < 0 or NaN), CL_ERR_TIMEOUT, CL_ERR_CUDA. */
+cl_status cl_wait(cl_lattice* lat, double timeout_s);
 /* Release every device buffer of the lattice (NULL is ignored). */
 void cl_free(cl_lattice* lat);
 

@@ -125,6 +125,10 @@ SIGNATURES = {
                                        ctypes.c_int, ctypes.c_int, _dp]),
     "cl_selftest_convert": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int64)]),
+    "cl_wait": (ctypes.c_int, [_P, ctypes.c_double]),
+    "cl_batch_wait": (ctypes.c_int, [_P, ctypes.c_double]),
+    "cl_batch_set_fused": (ctypes.c_int, [_P, ctypes.c_int]),
+    "cl_batch_get_fused": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int)]),
     "cl_launch_count": (ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int64)]),
     "cl_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "cl_get_timing": (ctypes.c_int, [_P, _dp, ctypes.POINTER(ctypes.c_int64)]),
@@ -406,6 +410,33 @@ def cl_batch_synchronize(batch):
     _check(load().cl_batch_synchronize(batch), "cl_batch_synchronize")
 
 
+def cl_wait(lat, timeout_s):
+    """True when the lattice's work has finished, False on CL_ERR_TIMEOUT."""
+    st = load().cl_wait(lat, timeout_s)
+    if st == CL_ERR_TIMEOUT:
+        return False
+    _check(st, "cl_wait")
+    return True
+
+
+def cl_batch_wait(batch, timeout_s):
+    st = load().cl_batch_wait(batch, timeout_s)
+    if st == CL_ERR_TIMEOUT:
+        return False
+    _check(st, "cl_batch_wait")
+    return True
+
+
+def cl_batch_set_fused(batch, fused):
+    _check(load().cl_batch_set_fused(batch, 1 if fused else 0), "cl_batch_set_fused")
+
+
+def cl_batch_get_fused(batch):
+    v = ctypes.c_int()
+    _check(load().cl_batch_get_fused(batch, ctypes.byref(v)), "cl_batch_get_fused")
+    return bool(v.value)
+
+
 def cl_batch_free(batch):
     load().cl_batch_free(batch)
 
@@ -676,10 +707,14 @@ class Batch:
     one step.  The Lattice objects must outlive it and have distinct,
     non-default streams (Lattice(..., own_stream=True))."""
 
-    def __init__(self, lats, eps, cps=None):
+    def __init__(self, lats, eps, cps=None, fused=None):
+        """fused: None keeps the library's default (fused where the members
+        allow it), True / False sets the mode."""
         self.lats = list(lats)
         self.h = None
         self.h = cl_batch_create([l.h for l in self.lats], eps, cps)
+        if fused is not None:
+            cl_batch_set_fused(self.h, fused)
 
     def run(self, n_steps=1):
         cl_batch_run(self.h, n_steps)
@@ -697,6 +732,13 @@ class Batch:
 
     def synchronize(self):
         cl_batch_synchronize(self.h)
+
+    def set_fused(self, fused):
+        cl_batch_set_fused(self.h, fused)
+
+    @property
+    def fused(self):
+        return cl_batch_get_fused(self.h)
 
     def close(self):
         if getattr(self, "h", None):

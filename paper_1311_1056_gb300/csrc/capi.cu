@@ -8,6 +8,9 @@
 #include <cstring>
 #include <string>
 #include <vector>
+#include <algorithm>
+#include <chrono>
+#include <thread>
 #include <array>
 #include <mutex>
 #include <map>
@@ -769,6 +772,9 @@ struct cl_batch {
   std::vector<cudaEvent_t> joins, ready;
   cudaGraphExec_t exec[2];
   std::vector<void*> startU[2];  // per lattice, the link buffer each variant starts from
+  // fused mode: one launch per kernel family over the blocks of every chain
+  int fused;
+  void* dmem;                    // descriptors of both variants, work lists, chain lists (one allocation)
 };
 
 namespace {
@@ -779,6 +785,10 @@ void drop_graphs(cl_batch* b) {
       cudaGraphExecDestroy(b->exec[v]);
       b->exec[v] = nullptr;
     }
+  if (b->dmem) {
+    cudaFree(b->dmem);
+    b->dmem = nullptr;
+  }
   for (cudaEvent_t e : b->joins)
     if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : b->ready)
@@ -796,11 +806,235 @@ cl_status check_batch_member(const cl_batch* b, const cl_lattice* l, double eps,
   return CL_OK;
 }
 
+// ---- fused mode
+// Host plan of a fused step: the work lists of every kernel family and the
+// chain lists of the per-chain kernels, offsets into one device allocation.
+struct FusedPlan {
+  std::vector<WorkItem> items;
+  std::vector<int> ints;
+  struct List {
+    size_t off;
+    int n;
+  };
+  List fam[ENS_NFAM + 3];  // + the gradient of the first sweep (all chains), the first Omega (all), spare
+  List all_chains, adaptive_chains, adaptive_flags;
+  int n_iter;
+  bool any_adaptive;
+};
+enum { ENS_FIRST_GRAD = ENS_NFAM, ENS_FIRST_OMEGA = ENS_NFAM + 1 };
+
+bool single_pass_chain(const cl_lattice* l, const cl_cool_params& cp) {
+  return (cp.mode == CL_D0 || cp.mode == CL_D1) && l->prec != 2;
+}
+
+FusedPlan plan_fused(const cl_batch* b) {
+  FusedPlan P;
+  const int n = (int)b->lats.size();
+  auto add = [&](int fam, auto pred, auto blocks) {
+    P.fam[fam].off = P.items.size();
+    for (int i = 0; i < n; ++i)
+      if (pred(i)) {
+        const int nb = blocks(b->lats[i]->g.V);
+        for (int vb = 0; vb < nb; ++vb) P.items.push_back(WorkItem{i, vb});
+      }
+    P.fam[fam].n = (int)(P.items.size() - P.fam[fam].off);
+  };
+  auto th = [&](int i) { return theta_nonzero(b->lats[i]); };
+  auto ad = [&](int i) { return b->lats[i]->k_ref > 0.0; };
+  auto sp = [&](int i) { return b->with_cooling && single_pass_chain(b->lats[i], b->cps[i]); };
+  auto cool = [&](int i) { return b->with_cooling != 0; };
+  auto four = [&](int i) { return b->with_cooling && !single_pass_chain(b->lats[i], b->cps[i]); };
+  auto all = [&](int) { return true; };
+  auto tiles = [](int V) { return (V + ENS_BLOCK - 1) / ENS_BLOCK; };
+  auto x4 = [&](int V) { return 4 * tiles(V); };
+  auto x6 = [&](int V) { return 6 * tiles(V); };
+  auto red = [](int V) { return reduce_blocks(V); };
+  add(ENS_INVERSE, all, x4);
+  add(ENS_PLAQ, all, x6);
+  add(ENS_CLOVER, th, x6);
+  add(ENS_FORCE_WILSON, [&](int i) { return !th(i); }, x6);
+  add(ENS_FORCE_THETA, th, x6);
+  add(ENS_UPDATE, [&](int i) { return !ad(i); }, x4);
+  add(ENS_DRIFTMAX, ad, x4);
+  add(ENS_UPDATE_X, ad, x4);
+  add(ENS_FIRST_GRAD, cool, red);
+  add(ENS_FIRST_OMEGA, cool, tiles);
+  add(ENS_COOL_GRAD, four, red);
+  add(ENS_COOL_OMEGA, four, tiles);
+  add(ENS_COOL_APPLY, four, x4);
+  add(ENS_COOL_GRAD_OMEGA, sp, red);
+  add(ENS_COOL_APPLY_UN, sp, red);
+  P.all_chains.off = P.ints.size();
+  for (int i = 0; i < n; ++i) P.ints.push_back(i);
+  P.all_chains.n = n;
+  P.adaptive_chains.off = P.ints.size();
+  for (int i = 0; i < n; ++i)
+    if (ad(i)) P.ints.push_back(i);
+  P.adaptive_chains.n = (int)(P.ints.size() - P.adaptive_chains.off);
+  P.adaptive_flags.off = P.ints.size();
+  for (int i = 0; i < n; ++i) P.ints.push_back(ad(i) ? 1 : 0);
+  P.adaptive_flags.n = n;
+  P.any_adaptive = P.adaptive_chains.n > 0;
+  P.n_iter = 0;
+  if (b->with_cooling)
+    for (const cl_cool_params& cp : b->cps) P.n_iter = std::max(P.n_iter, cp.forced_sweeps >= 0 ? cp.forced_sweeps : cp.n_max);
+  return P;
+}
+
+ChainDesc describe(const cl_lattice* l, double eps, const cl_cool_params& cp, bool swapped) {
+  ChainDesc c;
+  std::memset(&c, 0, sizeof(c));
+  int st = 1;
+  for (int mu = 0; mu < 4; ++mu) {
+    c.L[mu] = l->g.L[mu];
+    c.stride[mu] = st;
+    st *= l->g.L[mu];
+  }
+  c.V = l->g.V;
+  c.U = swapped ? l->Un : l->U;
+  c.Un = swapped ? l->U : l->Un;
+  c.Ui = l->Ui;
+  c.Pq = l->Pq;
+  c.Dq = l->Dq;
+  c.F = l->F;
+  c.C = l->C;
+  c.Gq = l->Gq;
+  c.f = l->f;
+  c.Om = l->Om;
+  c.Omi = l->Omi;
+  c.partials = l->partials;
+  c.cs = l->cs;
+  c.sd = l->sd;
+  c.beta = l->p.beta;
+  c.sre = KAPPA_Q * l->p.theta_im;  // F^ = -i theta kappa F, as in do_steps
+  c.sim = -KAPPA_Q * l->p.theta_re;
+  c.eps = eps;
+  c.sqrt_eps = sqrt(eps);
+  c.k_ref = l->k_ref;
+  c.seed = l->p.seed;
+  c.ca = cool_args(&cp);
+  return c;
+}
+
+// One fused step of every chain, enqueued on st from descriptor table cd.
+// Each chain runs exactly the kernels and the order of its own step: the CL
+// step (force by theta, update by step-size mode), then its cooling sweeps,
+// single-pass for D_0 / D_1 and four kernels otherwise, up to the largest
+// sweep count of the batch (a chain's own rule marks it done at its count;
+// later launches skip its blocks).  Returns the number of launches.
+cl_status enqueue_fused_step(const cl_batch* b, const FusedPlan& P, const ChainDesc* cd, const WorkItem* w,
+                             const int* ints, cudaStream_t st, int64_t* launches) {
+  const int prec = b->lats[0]->prec;
+  int64_t nl = 0;
+  auto fam = [&](int f, int list, int arg) -> cudaError_t {
+    if (P.fam[list].n == 0) return cudaSuccess;
+    nl += (f == ENS_FORCE_THETA && prec == 0) ? 2 : 1;
+    return launch_ens(prec, f, cd, w + P.fam[list].off, P.fam[list].n, arg, st);
+  };
+  CK(fam(ENS_INVERSE, ENS_INVERSE, 0));
+  CK(fam(ENS_PLAQ, ENS_PLAQ, 0));
+  CK(fam(ENS_CLOVER, ENS_CLOVER, 0));
+  CK(fam(ENS_FORCE_WILSON, ENS_FORCE_WILSON, 0));
+  CK(fam(ENS_FORCE_THETA, ENS_FORCE_THETA, 0));
+  if (P.any_adaptive) {
+    CK(fam(ENS_DRIFTMAX, ENS_DRIFTMAX, 0));
+    CK(launch_ens_step_eps(cd, ints + P.adaptive_chains.off, P.adaptive_chains.n, st));
+    ++nl;
+    CK(fam(ENS_UPDATE_X, ENS_UPDATE_X, 0));
+  }
+  CK(fam(ENS_UPDATE, ENS_UPDATE, 0));
+  CK(launch_ens_step_bump(cd, ints + P.all_chains.off, ints + P.adaptive_flags.off, P.all_chains.n, st));
+  ++nl;
+  if (b->with_cooling) {
+    const int* all = ints + P.all_chains.off;
+    const int n = P.all_chains.n;
+    CK(fam(ENS_COOL_GRAD, ENS_FIRST_GRAD, 1));
+    CK(launch_ens_cool_adapt(cd, all, n, 1, st));
+    ++nl;
+    if (P.n_iter > 0) {
+      CK(fam(ENS_COOL_OMEGA, ENS_FIRST_OMEGA, 0));
+      CK(fam(ENS_COOL_APPLY, ENS_COOL_APPLY, 0));
+      CK(fam(ENS_COOL_APPLY_UN, ENS_COOL_APPLY_UN, 0));
+    }
+    for (int k = 1; k <= P.n_iter; ++k) {
+      CK(fam(ENS_COOL_GRAD, ENS_COOL_GRAD, 0));
+      CK(launch_ens_cool_adapt(cd, all, n, 0, st));
+      ++nl;
+      if (k == P.n_iter) break;
+      CK(fam(ENS_COOL_OMEGA, ENS_COOL_OMEGA, 0));
+      CK(fam(ENS_COOL_GRAD_OMEGA, ENS_COOL_GRAD_OMEGA, 0));
+      CK(fam(ENS_COOL_APPLY, ENS_COOL_APPLY, 0));
+      CK(fam(ENS_COOL_APPLY_UN, ENS_COOL_APPLY_UN, 0));
+    }
+  }
+  *launches = nl;
+  return CL_OK;
+}
+
+// Fused launches need members of one precision, FP64 or FP32 storage.
+bool fusable(const cl_batch* b) {
+  for (const cl_lattice* l : b->lats)
+    if (l->prec == 2 || l->prec != b->lats[0]->prec) return false;
+  return true;
+}
+
+// Fused capture: the plan and both descriptor variants go to the device in
+// one allocation; each variant's step is captured from the origin stream.
+cl_status capture_batch_fused(cl_batch* b) {
+  const int n = (int)b->lats.size();
+  if (!fusable(b)) return fail(CL_ERR_INVALID, "fused batches need FP64 or FP32-storage members of one precision");
+  for (int i = 0; i < n; ++i) CK(cudaStreamSynchronize(b->lats[i]->st));
+  FusedPlan P = plan_fused(b);
+  std::vector<ChainDesc> cd(2 * (size_t)n);
+  for (int v = 0; v < 2; ++v)
+    for (int i = 0; i < n; ++i) cd[(size_t)v * n + i] = describe(b->lats[i], b->eps[i], b->cps[i], v == 1);
+  const size_t cd_bytes = sizeof(ChainDesc) * cd.size(), w_bytes = sizeof(WorkItem) * P.items.size(),
+               i_bytes = sizeof(int) * P.ints.size();
+  const size_t w_off = (cd_bytes + 255) / 256 * 256, i_off = w_off + (w_bytes + 255) / 256 * 256;
+  CK(cudaMalloc(&b->dmem, i_off + i_bytes + 16));
+  char* base = (char*)b->dmem;
+  CK(cudaMemcpy(base, cd.data(), cd_bytes, cudaMemcpyHostToDevice));
+  if (w_bytes) CK(cudaMemcpy(base + w_off, P.items.data(), w_bytes, cudaMemcpyHostToDevice));
+  if (i_bytes) CK(cudaMemcpy(base + i_off, P.ints.data(), i_bytes, cudaMemcpyHostToDevice));
+  const WorkItem* w = (const WorkItem*)(base + w_off);
+  const int* ints = (const int*)(base + i_off);
+  cl_status s = CL_OK;
+  int64_t nl = 0;
+  for (int v = 0; v < 2 && s == CL_OK; ++v) {
+    b->startU[v].assign(n, nullptr);
+    for (int i = 0; i < n; ++i) b->startU[v][i] = v == 0 ? b->lats[i]->U : b->lats[i]->Un;
+    cudaError_t e = cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return fail(CL_ERR_CUDA, std::string("fused capture: ") + cudaGetErrorString(e));
+    s = enqueue_fused_step(b, P, (const ChainDesc*)base + (size_t)v * n, w, ints, b->origin, &nl);
+    cudaGraph_t gr = nullptr;
+    e = cudaStreamEndCapture(b->origin, &gr);
+    if (s == CL_OK && e != cudaSuccess) s = fail(CL_ERR_CUDA, std::string("fused capture: ") + cudaGetErrorString(e));
+    if (s == CL_OK) {
+      e = cudaGraphInstantiate(&b->exec[v], gr, 0);
+      if (e != cudaSuccess) s = fail(CL_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    if (gr) cudaGraphDestroy(gr);
+  }
+  // launches are shared by all chains: counted once, on the first member
+  for (int i = 0; i < n; ++i) b->lats[i]->glaunches = i == 0 ? nl : 0;
+  if (s != CL_OK) drop_graphs(b);
+  return s;
+}
+
 // (Re)capture the batch graph: one step of every member, forked from the
 // origin stream to each member's stream and joined back; two variants (the
 // members' link buffers before and after one swap).
 cl_status capture_batch(cl_batch* b) {
   drop_graphs(b);
+  if (b->fused && !b->lats.empty()) {
+    b->joins.assign(b->lats.size(), nullptr);
+    b->ready.assign(b->lats.size(), nullptr);
+    cudaError_t e = cudaSuccess;
+    for (size_t i = 0; i < b->lats.size() && e == cudaSuccess; ++i)
+      e = cudaEventCreateWithFlags(&b->ready[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) return fail(CL_ERR_CUDA, std::string("batch setup: ") + cudaGetErrorString(e));
+    return capture_batch_fused(b);
+  }
   const int n = (int)b->lats.size();
   if (n == 0) return CL_OK;
   cudaError_t e = cudaSuccess;
@@ -885,6 +1119,8 @@ cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
   b->fork = nullptr;
   b->done = nullptr;
   b->exec[0] = b->exec[1] = nullptr;
+  b->fused = 0;
+  b->dmem = nullptr;
   for (int i = 0; i < n; ++i) {
     cl_status s = check_batch_member(b, lats[i], eps[i], with_cooling ? &cps[i] : nullptr);
     if (s != CL_OK) {
@@ -898,6 +1134,9 @@ cl_status cl_batch_create(int n, cl_lattice* const* lats, const double* eps,
     if (with_cooling) cp = cps[i];
     b->cps.push_back(cp);
   }
+  // fused launches by default where they apply (measured faster than the
+  // per-chain graph on the 64-chain ensemble; see cl_batch_set_fused)
+  b->fused = fusable(b) ? 1 : 0;
   cudaError_t e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->done, cudaEventDisableTiming);
@@ -923,11 +1162,14 @@ cl_status cl_batch_add(cl_batch* b, cl_lattice* lat, double eps, const cl_cool_p
   std::memset(&c, 0, sizeof(c));
   if (b->with_cooling) c = *cp;
   b->cps.push_back(c);
+  const int fused0 = b->fused;
+  if (b->fused && !fusable(b)) b->fused = 0;  // a member of another precision: per-chain graphs
   s = capture_batch(b);
   if (s != CL_OK) {
     b->lats.pop_back();
     b->eps.pop_back();
     b->cps.pop_back();
+    b->fused = fused0;
     cl_status s2 = capture_batch(b);
     (void)s2;
   }
@@ -944,6 +1186,26 @@ cl_status cl_batch_remove(cl_batch* b, cl_lattice* lat) {
   b->eps.erase(b->eps.begin() + i);
   b->cps.erase(b->cps.begin() + i);
   return capture_batch(b);
+}
+
+cl_status cl_batch_set_fused(cl_batch* b, int fused) {
+  if (!b) return fail(CL_ERR_INVALID, "NULL batch");
+  CK(cudaStreamSynchronize(b->origin));
+  const int old = b->fused;
+  b->fused = fused ? 1 : 0;
+  cl_status s = capture_batch(b);
+  if (s != CL_OK) {
+    b->fused = old;
+    cl_status s2 = capture_batch(b);
+    (void)s2;
+  }
+  return s;
+}
+
+cl_status cl_batch_get_fused(const cl_batch* b, int* fused) {
+  if (!b || !fused) return fail(CL_ERR_INVALID, "NULL argument");
+  *fused = b->fused;
+  return CL_OK;
 }
 
 cl_status cl_batch_size(const cl_batch* b, int* n) {
@@ -1265,6 +1527,31 @@ cl_status cl_synchronize(cl_lattice* l) {
   if (!l) return fail(CL_ERR_INVALID, "NULL lattice");
   CK(cudaStreamSynchronize(l->st));
   return CL_OK;
+}
+
+namespace {
+// Poll a stream until its work is done or timeout_s seconds have passed.
+cl_status bounded_wait(cudaStream_t st, double timeout_s) {
+  const auto t0 = std::chrono::steady_clock::now();
+  for (;;) {
+    const cudaError_t e = cudaStreamQuery(st);
+    if (e == cudaSuccess) return CL_OK;
+    if (e != cudaErrorNotReady) return fail(CL_ERR_CUDA, std::string("cudaStreamQuery: ") + cudaGetErrorString(e));
+    const double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    if (el >= timeout_s) return fail(CL_ERR_TIMEOUT, "work still running after the time limit");
+    std::this_thread::sleep_for(std::chrono::microseconds(50));
+  }
+}
+}  // namespace
+
+cl_status cl_wait(cl_lattice* l, double timeout_s) {
+  if (!l || !(timeout_s >= 0.0)) return fail(CL_ERR_INVALID, "NULL lattice or bad time limit");
+  return bounded_wait(l->st, timeout_s);
+}
+
+cl_status cl_batch_wait(cl_batch* b, double timeout_s) {
+  if (!b || !(timeout_s >= 0.0)) return fail(CL_ERR_INVALID, "NULL batch or bad time limit");
+  return bounded_wait(b->origin, timeout_s);
 }
 
 void cl_free(cl_lattice* l) {

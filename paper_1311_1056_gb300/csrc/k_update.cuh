@@ -100,27 +100,32 @@ __device__ __forceinline__ void scaled(mat<T>& r, T c, const mat<T>& a) {
 // ---------------------------------------------------------------- inverses
 // Ui = adj(U) = U^{-1} for every link (det U = 1 by the re-projection).
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_link_inverse(Geo g, const typename vec2_of<T>::type* __restrict__ U,
-                                                      typename vec2_of<T>::type* __restrict__ Ui) {
-  const int mu = blockIdx.x % 4;
-  const int s = (blockIdx.x / 4) * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void k_link_inverse_body(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                      typename vec2_of<T>::type* __restrict__ Ui, int vb) {
+  const int mu = vb % 4;
+  const int s = (vb / 4) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   mat<T> u, ui;
   load(u, U, mu, s, g.V);
   adj(ui, u);
   store(Ui, mu, s, g.V, ui);
 }
+template <typename T>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_link_inverse(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                      typename vec2_of<T>::type* __restrict__ Ui) {
+  k_link_inverse_body<T>(g, U, Ui, blockIdx.x);
+}
 
 // ------------------------------------------------------------- plaquettes
 // P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^{-1} U_nu(x)^{-1} and
 // D = P - P^{-1}, six planes per site.
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__device__ __forceinline__ void k_plaq_body(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                               const typename vec2_of<T>::type* __restrict__ Ui,
                                               typename vec2_of<T>::type* __restrict__ Pq,
-                                              typename vec2_of<T>::type* __restrict__ Dq) {
-  const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p);
-  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+                                              typename vec2_of<T>::type* __restrict__ Dq, int vb) {
+  const int p = vb % 6, mu = plane_mu(p), nu = plane_nu(p);
+  const int s = (vb / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int x[4];
   site_coords(g, s, x);
@@ -139,6 +144,13 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq(Geo g, const typename v
   for (int k = 0; k < 9; ++k) P.e[k] = csub(P.e[k], A.e[k]);
   store(Dq, p, s, g.V, P);
 }
+template <typename T>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                              const typename vec2_of<T>::type* __restrict__ Ui,
+                                              typename vec2_of<T>::type* __restrict__ Pq,
+                                              typename vec2_of<T>::type* __restrict__ Dq) {
+  k_plaq_body<T>(g, U, Ui, Pq, Dq, blockIdx.x);
+}
 
 // ------------------------------------------------------------ clover field
 // F_{mu nu}(x) = sum of (L - L^{-1}) over the four leaves at x; each leaf is a
@@ -148,13 +160,13 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq(Geo g, const typename v
 //   L3 = W^{-1} P(x-mu-nu) W with W = U_mu(x-mu-nu) U_nu(x-nu),
 // so F = D(x) + the three carried D's.  Stored times a complex scale.
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_clover_rot(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__device__ __forceinline__ void k_clover_rot_body(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                     const typename vec2_of<T>::type* __restrict__ Ui,
                                                     const typename vec2_of<T>::type* __restrict__ Dq,
                                                     typename vec2_of<T>::type* __restrict__ F,
-                                                    double sre, double sim) {
-  const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p);
-  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+                                                    double sre, double sim, int vb) {
+  const int p = vb % 6, mu = plane_mu(p), nu = plane_nu(p);
+  const int s = (vb / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int x[4];
   site_coords(g, s, x);
@@ -185,6 +197,14 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_clover_rot(Geo g, const type
   for (int k = 0; k < 9; ++k) acc.e[k] = cmul(acc.e[k], sc);
   store(F, p, s, g.V, acc);
 }
+template <typename T>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_clover_rot(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                    const typename vec2_of<T>::type* __restrict__ Ui,
+                                                    const typename vec2_of<T>::type* __restrict__ Dq,
+                                                    typename vec2_of<T>::type* __restrict__ F,
+                                                    double sre, double sim) {
+  k_clover_rot_body<T>(g, U, Ui, Dq, F, sre, sim, blockIdx.x);
+}
 
 // ----------------------------------------------------- plaquette drift
 // Contributions of the plaquette (x, p) to its four links, into
@@ -195,12 +215,12 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_clover_rot(Geo g, const type
 // stages run as two kernels with the partial G^ parked in Gq, so neither
 // spills; in FP32 one kernel runs both.
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_wilson(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__device__ __forceinline__ void k_plaq_force_wilson_body(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                            const typename vec2_of<T>::type* __restrict__ Ui,
                                                            const typename vec2_of<T>::type* __restrict__ Dq,
-                                                           typename vec2_of<T>::type* C, T beta6) {
-  const int p = blockIdx.x % 6, mu = plane_mu(p), nu = plane_nu(p);
-  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+                                                           typename vec2_of<T>::type* C, T beta6, int vb) {
+  const int p = vb % 6, mu = plane_mu(p), nu = plane_nu(p);
+  const int s = (vb / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   Work<T, 4> ws(0);
   mat<T>&D = ws[0], &M = ws[1], &t = ws[2], &a = ws[3];
@@ -219,6 +239,13 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_wilson(Geo g, con
   load(a, U, nu, s, g.V);
   mul(M, t, a);
   store(C, 4 * p + 3, s, g.V, M);
+}
+template <typename T>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_wilson(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                           const typename vec2_of<T>::type* __restrict__ Ui,
+                                                           const typename vec2_of<T>::type* __restrict__ Dq,
+                                                           typename vec2_of<T>::type* C, T beta6) {
+  k_plaq_force_wilson_body<T>(g, U, Ui, Dq, C, beta6, blockIdx.x);
 }
 
 // Corners c0..c2: G^ (partial) into Gh, slot 0 and slot 2 partials into C.
@@ -340,14 +367,14 @@ __device__ __forceinline__ void force_stage_b(mat<T>& Gh, const Geo& g, int s, c
 // so neither carries __restrict__ and stage b reads Gq with a plain load.
 const int GQ_PLANE = 4;
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_a(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__device__ __forceinline__ void k_plaq_force_a_body(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                       const typename vec2_of<T>::type* __restrict__ Ui,
                                                       const typename vec2_of<T>::type* __restrict__ Dq,
                                                       const typename vec2_of<T>::type* __restrict__ F,
                                                       typename vec2_of<T>::type* Gq,
-                                                      typename vec2_of<T>::type* C, T beta6) {
-  const int p = blockIdx.x % 6;
-  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+                                                      typename vec2_of<T>::type* C, T beta6, int vb) {
+  const int p = vb % 6;
+  const int s = (vb / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int x[4];
   site_coords(g, s, x);
@@ -357,15 +384,24 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_a(Geo g, const ty
   store(Gq, GQ_PLANE * p, s, g.V, Gh);
 }
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_b(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_a(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                      const typename vec2_of<T>::type* __restrict__ Ui,
+                                                      const typename vec2_of<T>::type* __restrict__ Dq,
+                                                      const typename vec2_of<T>::type* __restrict__ F,
+                                                      typename vec2_of<T>::type* Gq,
+                                                      typename vec2_of<T>::type* C, T beta6) {
+  k_plaq_force_a_body<T>(g, U, Ui, Dq, F, Gq, C, beta6, blockIdx.x);
+}
+template <typename T>
+__device__ __forceinline__ void k_plaq_force_b_body(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                       const typename vec2_of<T>::type* __restrict__ Ui,
                                                       const typename vec2_of<T>::type* __restrict__ Pq,
                                                       const typename vec2_of<T>::type* __restrict__ Dq,
                                                       const typename vec2_of<T>::type* __restrict__ F,
                                                       const typename vec2_of<T>::type* Gq,
-                                                      typename vec2_of<T>::type* C, T beta6) {
-  const int p = blockIdx.x % 6;
-  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+                                                      typename vec2_of<T>::type* C, T beta6, int vb) {
+  const int p = vb % 6;
+  const int s = (vb / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int x[4];
   site_coords(g, s, x);
@@ -374,16 +410,26 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_b(Geo g, const ty
   load_rw(Gh, Gq, GQ_PLANE * p, s, g.V);  // before stage b writes slot 1 of (p, s) over it
   force_stage_b(Gh, g, s, x, p, U, Ui, Pq, Dq, F, C, beta6);
 }
+template <typename T>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_b(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                      const typename vec2_of<T>::type* __restrict__ Ui,
+                                                      const typename vec2_of<T>::type* __restrict__ Pq,
+                                                      const typename vec2_of<T>::type* __restrict__ Dq,
+                                                      const typename vec2_of<T>::type* __restrict__ F,
+                                                      const typename vec2_of<T>::type* Gq,
+                                                      typename vec2_of<T>::type* C, T beta6) {
+  k_plaq_force_b_body<T>(g, U, Ui, Pq, Dq, F, Gq, C, beta6, blockIdx.x);
+}
 // Fused form (FP32, which needs no split to stay in registers).
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_ab(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__device__ __forceinline__ void k_plaq_force_ab_body(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                        const typename vec2_of<T>::type* __restrict__ Ui,
                                                        const typename vec2_of<T>::type* __restrict__ Pq,
                                                        const typename vec2_of<T>::type* __restrict__ Dq,
                                                        const typename vec2_of<T>::type* __restrict__ F,
-                                                       typename vec2_of<T>::type* C, T beta6) {
-  const int p = blockIdx.x % 6;
-  const int s = (blockIdx.x / 6) * blockDim.x + threadIdx.x;
+                                                       typename vec2_of<T>::type* C, T beta6, int vb) {
+  const int p = vb % 6;
+  const int s = (vb / 6) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int x[4];
   site_coords(g, s, x);
@@ -391,6 +437,15 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_ab(Geo g, const t
   mat<T>& Gh = wg[0];
   force_stage_a(Gh, g, s, x, p, U, Ui, Dq, F, C, beta6);
   force_stage_b(Gh, g, s, x, p, U, Ui, Pq, Dq, F, C, beta6);
+}
+template <typename T>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_ab(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                       const typename vec2_of<T>::type* __restrict__ Ui,
+                                                       const typename vec2_of<T>::type* __restrict__ Pq,
+                                                       const typename vec2_of<T>::type* __restrict__ Dq,
+                                                       const typename vec2_of<T>::type* __restrict__ F,
+                                                       typename vec2_of<T>::type* C, T beta6) {
+  k_plaq_force_ab_body<T>(g, U, Ui, Pq, Dq, F, C, beta6, blockIdx.x);
 }
 
 // Noise matrix sum_a eta_a lambda_a (Hermitian) into the imaginary part of A,
@@ -430,12 +485,12 @@ __device__ __forceinline__ void exponent(mat<R>& A, const R* g, R eps, R sqrt_ep
 // mu < nu: slot 0 of (x, p) and slot 3 of (x - nu, p); mu > nu: slot 1 of
 // (x, p) and slot 2 of (x - nu, p), p the plane of (mu, nu).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__device__ __forceinline__ void k_update_gather_body(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                        const typename vec2_of<T>::type* __restrict__ C,
                                                        typename vec2_of<T>::type* __restrict__ out,
-                                                       UpdArgs a) {
-  const int MU = blockIdx.x % 4;
-  const int s_raw = (blockIdx.x / 4) * blockDim.x + threadIdx.x;
+                                                       UpdArgs a, int vb) {
+  const int MU = vb % 4;
+  const int s_raw = (vb / 4) * blockDim.x + threadIdx.x;
   if (MODE != MODE_DRIFTMAX && s_raw >= g.V) return;
   // the max pass keeps whole warps alive for its shuffle: lanes past the end
   // redo the last site (same value, so the max is unchanged)
@@ -538,6 +593,13 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const t
 #pragma unroll
   for (int k = 0; k < 9; ++k) Un.e[k] = cmul(Un.e[k], zt);
   store(out, MU, s, g.V, Un);
+}
+template <typename T, int MODE>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_update_gather(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                       const typename vec2_of<T>::type* __restrict__ C,
+                                                       typename vec2_of<T>::type* __restrict__ out,
+                                                       UpdArgs a) {
+  k_update_gather_body<T, MODE>(g, U, C, out, a, blockIdx.x);
 }
 
 }  // namespace clgc

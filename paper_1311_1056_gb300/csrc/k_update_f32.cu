@@ -1,4 +1,5 @@
 // k_update_f32.cu -- the CL-step kernels (k_update.cuh) for float links.
+#include "ensemble.cuh"
 #include "k_update.cuh"
 #include "launch.h"
 
@@ -69,6 +70,10 @@ cudaError_t launch_update_gather_f32(int mode, const GeoH& h, const void* U, con
     default: k_update_gather<float, MODE_UPDATE><<<gr, bs, 0, st>>>(g, u, c, o, a); break;
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_ens_step_f32(int fam, const ChainDesc* cd, const WorkItem* w, int nw, cudaStream_t st) {
+  return launch_ens_step_family<float>(fam, cd, w, nw, st);
 }
 
 }  // namespace clgc

@@ -1,4 +1,5 @@
 // k_update_f64.cu -- the CL-step kernels (k_update.cuh) for double links.
+#include "ensemble.cuh"
 #include "k_update.cuh"
 #include "launch.h"
 
@@ -129,20 +130,49 @@ cudaError_t launch_update_gather(int prec, int mode, const GeoH& h, const void* 
 
 namespace clgc {
 // After an update: step += 1 and t += the step size taken (one thread).
-__global__ void k_step_bump(StepDev* sd, double eps, int adaptive) {
+__device__ __forceinline__ void step_bump(StepDev* sd, double eps, int adaptive) {
   sd->step += 1u;
   sd->t += adaptive ? sd->eps_n : eps;
 }
+__global__ void k_step_bump(StepDev* sd, double eps, int adaptive) { step_bump(sd, eps, adaptive); }
 
 // Adaptive step size from the drift pass's max |K|^2: eps_n = eps min(1, k_ref / K_max);
 // clears the running max for the next step.
-__global__ void k_step_eps(StepDev* sd, double eps, double k_ref) {
+__device__ __forceinline__ void step_eps(StepDev* sd, double eps, double k_ref) {
   const double kmax = sqrt(__longlong_as_double((long long)sd->kmax2_bits));
   const double e = kmax > k_ref ? eps * (k_ref / kmax) : eps;
   sd->eps_n = e;
   sd->sqrt_eps_n = sqrt(e);
   sd->kmax = kmax;
   sd->kmax2_bits = 0ull;
+}
+__global__ void k_step_eps(StepDev* sd, double eps, double k_ref) { step_eps(sd, eps, k_ref); }
+
+// The same for the chains of a fused batch, one thread per listed chain.
+__global__ void k_ens_step_eps(const ChainDesc* __restrict__ cd, const int* __restrict__ chains, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ChainDesc& c = cd[chains[i]];
+  step_eps(c.sd, c.eps, c.k_ref);
+}
+__global__ void k_ens_step_bump(const ChainDesc* __restrict__ cd, const int* __restrict__ chains,
+                                const int* __restrict__ adaptive, int n) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const ChainDesc& c = cd[chains[i]];
+  step_bump(c.sd, c.eps, adaptive[i]);
+}
+
+cudaError_t launch_ens_step_eps(const ChainDesc* cd, const int* chains, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_ens_step_eps<<<(n + 127) / 128, 128, 0, st>>>(cd, chains, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_ens_step_bump(const ChainDesc* cd, const int* chains, const int* adaptive, int n,
+                                 cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_ens_step_bump<<<(n + 127) / 128, 128, 0, st>>>(cd, chains, adaptive, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_step_bump(StepDev* sd, double eps, bool adaptive, cudaStream_t st) {
@@ -154,4 +184,8 @@ cudaError_t launch_step_eps(StepDev* sd, double eps, double k_ref, cudaStream_t 
   k_step_eps<<<1, 1, 0, st>>>(sd, eps, k_ref);
   return cudaGetLastError();
 }
+cudaError_t launch_ens_step_f64(int fam, const ChainDesc* cd, const WorkItem* w, int nw, cudaStream_t st) {
+  return launch_ens_step_family<double>(fam, cd, w, nw, st);
+}
+
 }  // namespace clgc

@@ -22,10 +22,10 @@ inline dim3 grid_sites(int V, int planes = 1) {
   return dim3((unsigned)((V + RED_THREADS - 1) / RED_THREADS), (unsigned)planes);
 }
 
-// Fixed-order block reduction of NQ doubles (slot MAXSLOT takes the max);
-// one record per block into partials.
+// Fixed-order block reduction of NQ doubles (slot MAXSLOT takes the max)
+// into the block's record rec[0 .. NQ-1].
 template <int NQ, int MAXSLOT>
-__device__ __forceinline__ void block_reduce_store(double* v, double* partials) {
+__device__ __forceinline__ void block_reduce_store(double* v, double* rec) {
   __shared__ double sm[RED_THREADS / 32][NQ];
 #pragma unroll
   for (int q = 0; q < NQ; ++q)
@@ -43,7 +43,7 @@ __device__ __forceinline__ void block_reduce_store(double* v, double* partials) 
     int q = threadIdx.x;
     double s = sm[0][q];
     for (int k = 1; k < RED_THREADS / 32; ++k) s = (q == MAXSLOT) ? fmax(s, sm[k][q]) : s + sm[k][q];
-    partials[(size_t)blockIdx.x * NQ + q] = s;
+    rec[q] = s;
   }
 }
 
@@ -422,13 +422,14 @@ __device__ __forceinline__ T cool_grad_site(const Geo& g, const typename vec2_of
 
 // The gradient f into [a][V] (FP64) with, per block, sum |f|, sum f^2,
 // sum (1/3) Tr U U^+ of the links at x and the nonfinite count.
+// Block vb of nvb (the grid-stride loop over sites and the record index).
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename vec2_of<T>::type* __restrict__ U,
-                                                          double* __restrict__ f, double* partials,
-                                                          const CoolState* cs) {
+__device__ __forceinline__ void cool_grad_body(const Geo& g, const typename vec2_of<T>::type* __restrict__ U,
+                                               double* __restrict__ f, double* partials, const CoolState* cs,
+                                               int vb, int nvb) {
   if (cs && cs->done) return;
   double v[NQ_COOL] = {0.0, 0.0, 0.0, 0.0};
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+  for (int s = vb * blockDim.x + threadIdx.x; s < g.V; s += nvb * blockDim.x) {
     int x[4];
     site_coords(g, s, x);
     T fa[8];
@@ -445,7 +446,13 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename
     v[2] += cvt<double>(un) * (1.0 / 3.0);
     v[3] += ok ? 0.0 : 1.0;
   }
-  block_reduce_store<NQ_COOL, -1>(v, partials);
+  block_reduce_store<NQ_COOL, -1>(v, partials + (size_t)vb * NQ_COOL);
+}
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                          double* __restrict__ f, double* partials,
+                                                          const CoolState* cs) {
+  cool_grad_body<T>(g, U, f, partials, cs, blockIdx.x, gridDim.x);
 }
 
 // Single-pass sweep of the D_0 / D_1 rules, part 1: the strength alpha_ad of
@@ -454,13 +461,12 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename
 // and the gradient never leaves the thread: f_ax at x, then Omega_x =
 // exp(-eps alpha_ad f_ax lambda_a) and its inverse (FP64), stored packed.
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS) k_cool_grad_omega(Geo g,
-                                                                const typename vec2_of<T>::type* __restrict__ U,
-                                                                T* __restrict__ Om, T* __restrict__ Omi, double eps,
-                                                                const CoolState* cs) {
+__device__ __forceinline__ void cool_grad_omega_body(const Geo& g, const typename vec2_of<T>::type* __restrict__ U,
+                                                     T* __restrict__ Om, T* __restrict__ Omi, double eps,
+                                                     const CoolState* cs, int vb, int nvb) {
   if (cs->done) return;
   const double c = -eps * cs->alpha_ad;
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+  for (int s = vb * blockDim.x + threadIdx.x; s < g.V; s += nvb * blockDim.x) {
     int x[4];
     site_coords(g, s, x);
     T fa[8];
@@ -474,14 +480,21 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad_omega(Geo g,
     store_herm(Omi, s, g.V, omi);
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_cool_grad_omega(Geo g,
+                                                                const typename vec2_of<T>::type* __restrict__ U,
+                                                                T* __restrict__ Om, T* __restrict__ Omi, double eps,
+                                                                const CoolState* cs) {
+  cool_grad_omega_body<T>(g, U, Om, Omi, eps, cs, blockIdx.x, gridDim.x);
+}
 
 // The adaptive rule (Sec. 4): alpha_ad = alpha / D with D_0 = 1,
 // D_1 = (1/3)<Tr U U^+> (normalised unitarity norm), D_2 = <|f_ax|>_{a,x}
 // (or its RMS).  Sweep count: at least n_min, at most n_max; stop once the
 // norm decreases by less than tol_rel of its distance from 1 or that distance
 // is below d_floor; no sweep when D < d_guard; forced_sweeps >= 0 fixes the count.
-__global__ void k_cool_adapt(Geo g, const double* partials, int nb, CoolArgs a, CoolState* cs,
-                             int first) {
+__device__ __forceinline__ void cool_adapt_body(const Geo& g, const double* partials, int nb, const CoolArgs& a,
+                                                CoolState* cs, int first) {
   __shared__ double tot[NQ_COOL];
   reduce_partials<NQ_COOL, -1>(partials, nb, tot);
   __syncthreads();
@@ -531,6 +544,9 @@ __global__ void k_cool_adapt(Geo g, const double* partials, int nb, CoolArgs a, 
   cs->sweeps += 1;
   cs->un_prev = un;
 }
+__global__ void k_cool_adapt(Geo g, const double* partials, int nb, CoolArgs a, CoolState* cs, int first) {
+  cool_adapt_body(g, partials, nb, a, cs, first);
+}
 
 // The DF64 gradient kernel: its own launch bound, so that the whole
 // reduction grid (8 blocks per SM) is resident in one wave.
@@ -540,16 +556,16 @@ __global__ void __launch_bounds__(RED_THREADS, RED_MAX_BLOCKS / 152) k_cool_grad
   if (cs && cs->done) return;
   double v[NQ_COOL] = {0.0, 0.0, 0.0, 0.0};
   cool_grad_df(g, U, f, v);
-  block_reduce_store<NQ_COOL, -1>(v, partials);
+  block_reduce_store<NQ_COOL, -1>(v, partials + (size_t)blockIdx.x * NQ_COOL);
 }
 
 // Omega_x = exp(-eps alpha_ad f_ax lambda_a) and its inverse: FP64, or
 // double-float in the DF64 form.
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_omega(Geo g, const double* __restrict__ f, T* Om, T* Omi,
-                                                           double eps, const CoolState* cs) {
+__device__ __forceinline__ void cool_omega_body(const Geo& g, const double* __restrict__ f, T* Om, T* Omi, double eps,
+                                                const CoolState* cs, int vb) {
   if (cs->done) return;
-  int s = blockIdx.x * blockDim.x + threadIdx.x;
+  int s = vb * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   if constexpr (std::is_same<T, df64>::value) {
     // DF64: f as hi + lo pairs, the exponential pair in double-float
@@ -574,16 +590,20 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_omega(Geo g, const doub
     store_herm(Omi, s, g.V, omi);
   }
 }
+template <typename T>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_omega(Geo g, const double* __restrict__ f, T* Om, T* Omi,
+                                                           double eps, const CoolState* cs) {
+  cool_omega_body<T>(g, f, Om, Omi, eps, cs, blockIdx.x);
+}
 
 // U_{x,mu} <- Omega_x U_{x,mu} Omega_{x+mu}^{-1}, all links at once (in place:
 // every link is read and written by the same thread).
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_apply(Geo g, typename vec2_of<T>::type* U, const T* __restrict__ Om,
-                                                           const T* __restrict__ Omi,
-                                                           const CoolState* cs) {
+__device__ __forceinline__ void cool_apply_body(const Geo& g, typename vec2_of<T>::type* U, const T* __restrict__ Om,
+                                                const T* __restrict__ Omi, const CoolState* cs, int vb) {
   if (cs && cs->done) return;
-  const int mu = blockIdx.x % 4;
-  const int s = (blockIdx.x / 4) * blockDim.x + threadIdx.x;
+  const int mu = vb % 4;
+  const int s = (vb / 4) * blockDim.x + threadIdx.x;
   if (s >= g.V) return;
   int x[4];
   site_coords(g, s, x);
@@ -595,6 +615,12 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_apply(Geo g, typename v
   mul_herm_right(u, t, oi);
   store(U, mu, s, g.V, u);
 }
+template <typename T>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_apply(Geo g, typename vec2_of<T>::type* U, const T* __restrict__ Om,
+                                                           const T* __restrict__ Omi,
+                                                           const CoolState* cs) {
+  cool_apply_body<T>(g, U, Om, Omi, cs, blockIdx.x);
+}
 
 // Single-pass sweep of the D_0 / D_1 rules, part 2: the apply, site by site
 // (Omega_x loaded once for the site's four links), with per block the sums
@@ -602,12 +628,12 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_apply(Geo g, typename v
 // (FP64) and their nonfinite count, in the gradient's record layout (the
 // |f| and f^2 slots are 0).
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS, 4) k_cool_apply_un(Geo g, typename vec2_of<T>::type* U,
-                                                              const T* __restrict__ Om, const T* __restrict__ Omi,
-                                                              double* partials, const CoolState* cs) {
+__device__ __forceinline__ void cool_apply_un_body(const Geo& g, typename vec2_of<T>::type* U,
+                                                   const T* __restrict__ Om, const T* __restrict__ Omi,
+                                                   double* partials, const CoolState* cs, int vb, int nvb) {
   if (cs->done) return;
   double v[NQ_COOL] = {0.0, 0.0, 0.0, 0.0};
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < g.V; s += gridDim.x * blockDim.x) {
+  for (int s = vb * blockDim.x + threadIdx.x; s < g.V; s += nvb * blockDim.x) {
     int x[4];
     site_coords(g, s, x);
     mat<T> o;
@@ -627,7 +653,13 @@ __global__ void __launch_bounds__(RED_THREADS, 4) k_cool_apply_un(Geo g, typenam
     v[2] += cvt<double>(un) * (1.0 / 3.0);
     v[3] += isfinite(un) ? 0.0 : 1.0;
   }
-  block_reduce_store<NQ_COOL, -1>(v, partials);
+  block_reduce_store<NQ_COOL, -1>(v, partials + (size_t)vb * NQ_COOL);
+}
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS, 4) k_cool_apply_un(Geo g, typename vec2_of<T>::type* U,
+                                                              const T* __restrict__ Om, const T* __restrict__ Omi,
+                                                              double* partials, const CoolState* cs) {
+  cool_apply_un_body<T>(g, U, Om, Omi, partials, cs, blockIdx.x, gridDim.x);
 }
 
 const int DF_APPLY_BLOCK = 128;  // the DF64 apply's largest block (its launch bound)
@@ -755,7 +787,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_obs(Geo g, const typename vec2_
     }
     v[8] += ok ? 0.0 : 1.0;
   }
-  block_reduce_store<NQ_OBS, 7>(v, partials);
+  block_reduce_store<NQ_OBS, 7>(v, partials + (size_t)blockIdx.x * NQ_OBS);
 }
 
 __global__ void k_obs_final(Geo g, const double* partials, int nb, double beta, double th_re,
@@ -816,6 +848,112 @@ __global__ void k_selftest_convert(uint64_t seed, long long n, unsigned long lon
 }
 
 }  // namespace
+
+// ------------------------------------------------------------ fused batch
+// The cooling kernels of a fused batch: one launch over the blocks of every
+// listed chain, each block running the body of the chain's own kernel with
+// the chain's geometry, buffers and rule state (see ensemble.cuh).  Cooling
+// follows the step's update, which wrote the chain's Un: that is the link
+// field these kernels cool (the runtime swaps U and Un after the step).
+namespace {
+
+__device__ __forceinline__ Geo ens_geo(const ChainDesc& c) {
+  Geo g;
+#pragma unroll
+  for (int mu = 0; mu < 4; ++mu) {
+    g.L[mu] = c.L[mu];
+    g.stride[mu] = c.stride[mu];
+  }
+  g.V = c.V;
+  return g;
+}
+__device__ __forceinline__ int ens_reduce_blocks(int V) {
+  const int b = (V + RED_THREADS - 1) / RED_THREADS;
+  return b < RED_MAX_BLOCKS ? b : RED_MAX_BLOCKS;
+}
+
+// first = 1: the call's first gradient, which always runs (as k_cool_grad with no state)
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_ens_cool_grad(const ChainDesc* __restrict__ cd,
+                                                              const WorkItem* __restrict__ w, int first) {
+  typedef typename vec2_of<T>::type V2;
+  const WorkItem it = w[blockIdx.x];
+  const ChainDesc& c = cd[it.chain];
+  cool_grad_body<T>(ens_geo(c), (const V2*)c.Un, (double*)c.f, c.partials, first ? nullptr : c.cs, it.vb,
+                    ens_reduce_blocks(c.V));
+}
+template <typename T>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_ens_cool_omega(const ChainDesc* __restrict__ cd,
+                                                                  const WorkItem* __restrict__ w) {
+  const WorkItem it = w[blockIdx.x];
+  const ChainDesc& c = cd[it.chain];
+  cool_omega_body<T>(ens_geo(c), (const double*)c.f, (T*)c.Om, (T*)c.Omi, c.ca.eps, c.cs, it.vb);
+}
+template <typename T>
+__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_ens_cool_apply(const ChainDesc* __restrict__ cd,
+                                                                  const WorkItem* __restrict__ w) {
+  typedef typename vec2_of<T>::type V2;
+  const WorkItem it = w[blockIdx.x];
+  const ChainDesc& c = cd[it.chain];
+  cool_apply_body<T>(ens_geo(c), (V2*)c.Un, (const T*)c.Om, (const T*)c.Omi, c.cs, it.vb);
+}
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS) k_ens_cool_grad_omega(const ChainDesc* __restrict__ cd,
+                                                                    const WorkItem* __restrict__ w) {
+  typedef typename vec2_of<T>::type V2;
+  const WorkItem it = w[blockIdx.x];
+  const ChainDesc& c = cd[it.chain];
+  cool_grad_omega_body<T>(ens_geo(c), (const V2*)c.Un, (T*)c.Om, (T*)c.Omi, c.ca.eps, c.cs, it.vb,
+                          ens_reduce_blocks(c.V));
+}
+template <typename T>
+__global__ void __launch_bounds__(RED_THREADS, 4) k_ens_cool_apply_un(const ChainDesc* __restrict__ cd,
+                                                                     const WorkItem* __restrict__ w) {
+  typedef typename vec2_of<T>::type V2;
+  const WorkItem it = w[blockIdx.x];
+  const ChainDesc& c = cd[it.chain];
+  cool_apply_un_body<T>(ens_geo(c), (V2*)c.Un, (const T*)c.Om, (const T*)c.Omi, c.partials, c.cs, it.vb,
+                        ens_reduce_blocks(c.V));
+}
+// the rule, one block of 256 threads per listed chain
+__global__ void k_ens_cool_adapt(const ChainDesc* __restrict__ cd, const int* __restrict__ chains, int first) {
+  const ChainDesc& c = cd[chains[blockIdx.x]];
+  cool_adapt_body(ens_geo(c), c.partials, ens_reduce_blocks(c.V), c.ca, c.cs, first);
+}
+
+template <typename T>
+cudaError_t launch_ens_cool_family(int fam, const ChainDesc* cd, const WorkItem* w, int nw, int arg, cudaStream_t st) {
+  const unsigned n = (unsigned)nw;
+  switch (fam) {
+    case ENS_COOL_GRAD: k_ens_cool_grad<T><<<n, RED_THREADS, 0, st>>>(cd, w, arg); break;
+    case ENS_COOL_OMEGA: k_ens_cool_omega<T><<<n, ENS_BLOCK, 0, st>>>(cd, w); break;
+    case ENS_COOL_APPLY: k_ens_cool_apply<T><<<n, ENS_BLOCK, 0, st>>>(cd, w); break;
+    case ENS_COOL_GRAD_OMEGA: k_ens_cool_grad_omega<T><<<n, RED_THREADS, 0, st>>>(cd, w); break;
+    case ENS_COOL_APPLY_UN: k_ens_cool_apply_un<T><<<n, RED_THREADS, 0, st>>>(cd, w); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_ens_step_f64(int fam, const ChainDesc* cd, const WorkItem* w, int nw, cudaStream_t st);
+cudaError_t launch_ens_step_f32(int fam, const ChainDesc* cd, const WorkItem* w, int nw, cudaStream_t st);
+
+cudaError_t launch_ens(int prec, int fam, const ChainDesc* cd, const WorkItem* w, int nw, int arg, cudaStream_t st) {
+  if (nw <= 0) return cudaSuccess;
+  if (prec != 0 && prec != 1) return cudaErrorInvalidValue;
+  if (fam < ENS_COOL_GRAD)
+    return prec == 0 ? launch_ens_step_f64(fam, cd, w, nw, st) : launch_ens_step_f32(fam, cd, w, nw, st);
+  return prec == 0 ? launch_ens_cool_family<double>(fam, cd, w, nw, arg, st)
+                   : launch_ens_cool_family<float>(fam, cd, w, nw, arg, st);
+}
+
+cudaError_t launch_ens_cool_adapt(const ChainDesc* cd, const int* chains, int n, int first, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_ens_cool_adapt<<<n, 256, 0, st>>>(cd, chains, first);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_selftest_convert(uint64_t seed, long long n, unsigned long long* bad, cudaStream_t st) {
   k_selftest_convert<<<RED_MAX_BLOCKS, RED_THREADS, 0, st>>>(seed, n, bad);

@@ -54,6 +54,46 @@ struct ObsOut {
 
 enum { NQ_OBS = 9, NQ_COOL = 4, RED_THREADS = 128, RED_MAX_BLOCKS = 1216 };
 
+// One chain of a fused batch (the ensemble kernels below): its geometry (the
+// fields of lattice.cuh's Geo), device buffers and per-chain parameters.  U
+// holds the links the step starts from; the update writes Un, and cooling
+// then works on Un (the runtime swaps the two after the step).
+struct ChainDesc {
+  int L[4], stride[4], V;
+  void *U, *Un, *Ui, *Pq, *Dq, *F, *C, *Gq, *f, *Om, *Omi;
+  double* partials;
+  CoolState* cs;
+  StepDev* sd;
+  double beta, sre, sim;    // coupling; clover scale -i theta kappa = sre + i sim
+  double eps, sqrt_eps, k_ref;
+  uint64_t seed;
+  CoolArgs ca;
+};
+// One block of a fused launch: chain index and the block index that a
+// launch for that chain alone would have had.
+struct WorkItem {
+  int chain, vb;
+};
+// Fused kernel families (one launch over the work list's blocks of every
+// chain; block size ENS_BLOCK, the reductions' RED_THREADS).
+enum {
+  ENS_INVERSE = 0,      // link inverses, 4 directions
+  ENS_PLAQ = 1,         // plaquettes, 6 planes
+  ENS_CLOVER = 2,       // clover field (theta != 0 chains)
+  ENS_FORCE_WILSON = 3, // drift contributions, theta = 0 chains
+  ENS_FORCE_THETA = 4,  // drift contributions, theta != 0 chains (FP64: two kernels)
+  ENS_UPDATE = 5,       // gather + update, fixed step size
+  ENS_DRIFTMAX = 6,     // gather, drift into Ui, max |K|^2 (adaptive step size)
+  ENS_UPDATE_X = 7,     // update from the drift in Ui (adaptive step size)
+  ENS_COOL_GRAD = 8,    // gradient + rule sums (RED_THREADS blocks, grid-stride per chain)
+  ENS_COOL_OMEGA = 9,   // Omega, Omega^{-1}
+  ENS_COOL_APPLY = 10,  // apply, 4 directions
+  ENS_COOL_GRAD_OMEGA = 11, // single-pass sweeps (D_0 / D_1): gradient + Omega
+  ENS_COOL_APPLY_UN = 12,   // single-pass sweeps: apply + norm sums
+  ENS_NFAM = 13
+};
+const int ENS_BLOCK = 128;
+
 int reduce_blocks(int V);  // number of per-block partial records for V sites
 
 // prec: 0 = FP64 links, 1 = FP32 links.  All pointers are device pointers;
@@ -123,6 +163,16 @@ cudaError_t launch_obs(int prec, const GeoH& g, const void* U, const void* F, in
                        double* partials, double* q_site, cudaStream_t st);
 cudaError_t launch_obs_final(const GeoH& g, const double* partials, double beta, double th_re,
                              double th_im, ObsOut* out, cudaStream_t st);
+// Fused batch: one launch of family fam (ENS_*) over nw work items (device
+// arrays cd, w); FP64 and FP32 storage only.  Per-chain kernels (one thread
+// or one block per chain): the adaptive step size, the step counter, and the
+// cooling rule (first = the call's first sweep).
+// arg: ENS_COOL_GRAD's `first` flag (the call's first gradient runs whatever the rule state).
+cudaError_t launch_ens(int prec, int fam, const ChainDesc* cd, const WorkItem* w, int nw, int arg, cudaStream_t st);
+cudaError_t launch_ens_step_eps(const ChainDesc* cd, const int* chains, int n, cudaStream_t st);
+cudaError_t launch_ens_step_bump(const ChainDesc* cd, const int* chains, const int* adaptive, int n,
+                                 cudaStream_t st);
+cudaError_t launch_ens_cool_adapt(const ChainDesc* cd, const int* chains, int n, int first, cudaStream_t st);
 // Integer-pipe float <-> double conversions (cvt.cuh) against the hardware
 // ones on n generated cases; mismatch counts added into bad[0] (float ->
 // double) and bad[1] (double -> float).

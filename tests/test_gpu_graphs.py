@@ -194,3 +194,108 @@ def test_batch_membership_changes():
     finally:
         for lat in lats + refs:
             lat.close()
+
+
+def _fused_chains(prec):
+    """Unlike chains of one precision: sizes (ragged, not multiples of the
+    block), couplings, theta = 0 and != 0, fixed and adaptive step size."""
+    return [
+        dict(L=(4, 4, 4, 4), beta=5.6, theta=0.0, prec=prec, seed=21, k_ref=0.0),
+        dict(L=(6, 4, 4, 4), beta=6.0, theta=0.5, prec=prec, seed=22, k_ref=6.0),
+        dict(L=(4, 6, 4, 8), beta=6.2, theta=1.5, prec=prec, seed=23, k_ref=0.0),
+        dict(L=(3, 5, 4, 7), beta=5.9, theta=2.0, prec=prec, seed=24, k_ref=4.0),
+        dict(L=(8, 8, 8, 8), beta=6.0, theta=1.0, prec=prec, seed=25, k_ref=0.0),
+    ]
+
+
+@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_FP32_STORAGE])
+def test_fused_batch_equals_each_chain_alone(prec):
+    """Fused mode: one launch per kernel family runs the blocks of every
+    chain, each with its own geometry, buffers, noise and cooling rule -- the
+    single-pass D_0 / D_1 sweeps and the four-kernel D_2 sweeps side by side,
+    different sweep limits, theta = 0 and != 0, adaptive and fixed step size.
+    Every chain must end where it ends alone, bit for bit."""
+    chains = _fused_chains(prec)
+    eps = [0.01, 0.005, 0.01, 0.008, 0.006]
+    cps = [cl.make_cool(**ADAPT), cl.make_cool(eps=0.005, alpha=1.0, mode=cl.CL_D1, forced_sweeps=2),
+           cl.make_cool(eps=0.01, alpha=0.5, mode=cl.CL_D0, n_min=0, n_max=4, tol_rel=0.1),
+           cl.make_cool(eps=0.008, alpha=1.0, mode=cl.CL_D2_RMS, n_min=1, n_max=5, tol_rel=0.05),
+           cl.make_cool(eps=0.006, alpha=1.0, mode=cl.CL_D1, n_min=0, n_max=3, tol_rel=1e-3)]
+
+    def make(c):
+        lat = _lat(L=c["L"], beta=c["beta"], theta=c["theta"], prec=c["prec"], seed=c["seed"])
+        if c["k_ref"] > 0:
+            lat.set_adaptive_step(c["k_ref"])
+        return lat
+
+    alone = []
+    for c, e, cp in zip(chains, eps, cps):
+        with make(c) as lat:
+            reps = []
+            for _ in range(5):
+                lat.step(e, 1)
+                reps.append(lat.cool(cp))
+            alone.append((lat.links(), reps[-1], lat.observables(), lat.langevin_time()))
+    lats = [make(c) for c in chains]
+    try:
+        with cl.Batch(lats, eps, cps, fused=True) as b:
+            assert b.fused
+            b.run(3)
+            b.run(2)
+            b.synchronize()
+            for lat, (U, rep, obs, t) in zip(lats, alone):
+                assert lat.step_count == 5
+                assert np.array_equal(lat.links(), U)
+                assert lat.last_cool_report() == rep
+                assert lat.observables() == obs
+                assert lat.langevin_time() == t
+            # back to per-chain graphs, then fused again, mid-run
+            b.set_fused(False)
+            b.run(1)
+            b.set_fused(True)
+            b.run(1)
+            assert all(lat.step_count == 7 for lat in lats)
+    finally:
+        for lat in lats:
+            lat.close()
+
+
+def test_fused_batch_refuses_mixed_precision():
+    lats = [_lat(prec=cl.CL_FP64), _lat(prec=cl.CL_FP32_STORAGE, seed=4)]
+    try:
+        with cl.Batch(lats, 0.01) as b:
+            with pytest.raises(cl.CLError) as ei:
+                b.set_fused(True)
+            assert ei.value.status == cl.CL_ERR_INVALID
+            assert not b.fused
+            b.run(1)  # still a working per-chain batch
+    finally:
+        for lat in lats:
+            lat.close()
+
+
+def test_batch_default_mode_follows_the_members():
+    """A batch starts fused when its members allow it (one precision, FP64 or
+    FP32 storage); adding a member of another precision switches it to
+    per-chain graphs, and every chain still ends where it would alone."""
+    cp = cl.make_cool(**ADAPT)
+    lats = [_lat(prec=cl.CL_FP32_STORAGE, seed=41), _lat(prec=cl.CL_FP32_STORAGE, seed=42, L=(4, 4, 6, 4))]
+    extra = _lat(prec=cl.CL_FP64, seed=43)
+    refs = [_lat(prec=cl.CL_FP32_STORAGE, seed=41), _lat(prec=cl.CL_FP32_STORAGE, seed=42, L=(4, 4, 6, 4)),
+            _lat(prec=cl.CL_FP64, seed=43)]
+    try:
+        with cl.Batch(lats, 0.01, [cp, cp]) as b:
+            assert b.fused
+            b.run(2)
+            b.add(extra, 0.01, cp)
+            assert not b.fused
+            b.run(2)
+        for ref, n in zip(refs, (4, 4, 2)):
+            for _ in range(n):
+                ref.step(0.01, 1)
+                ref.cool(cp)
+        for lat, ref in zip(lats + [extra], refs):
+            assert np.array_equal(lat.links(), ref.links())
+    finally:
+        for lat in lats + [extra] + refs:
+            lat.close()
