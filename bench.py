@@ -110,16 +110,21 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def dram_traffic(kernel, prec):
-    """Per-launch DRAM bytes from a committed ncu summary, if taken on the current sources."""
-    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+def dram_traffic(kernel, prec, V=None, path=None):
+    """Per-launch DRAM bytes of a roofline family from a committed ncu summary
+    (profiles/dram_traffic.json), if taken on the current sources.  The
+    capture runs a smaller lattice (capture_sites); every kernel's traffic
+    grows with the sites it processes, so the bytes are scaled to V."""
+    p = path or os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as fh:
             d = json.load(fh)
         e = d[prec][kernel]
         if e.get("source_hash") != kernel_source_hash():
             return None
-        return e["bytes_per_launch"]
+        b = e["bytes_per_launch"]
+        cap = d.get("capture_sites")
+        return b * (V / cap) if (V and cap) else b
     except Exception:
         return None
 
@@ -128,28 +133,37 @@ def dram_traffic(kernel, prec):
 # over its kernels: the split force runs a then b once per step).
 TRAFFIC_FAMILIES = {
     "fp64": {"force": ("k_plaq_force_a<double>", "k_plaq_force_b<double>"),
-             "update": ("k_update_gather<double, 0>",), "cool_apply": ("k_cool_apply<double>",),
-             "cool_grad": ("k_cool_grad<double>",), "cool_omega": ("k_cool_omega<double>",)},
+             "update": ("k_update_gather<double, 0>",), "cool_apply": ("k_cool_apply_un<double>",),
+             "cool_grad": ("k_cool_grad<double>",), "cool_omega": ("k_cool_omega<double>",),
+             "cool_grad_omega": ("k_cool_grad_omega<double>",)},
     "fp32": {"force": ("k_plaq_force_ab<float>",), "update": ("k_update_gather<float, 0>",),
-             "cool_apply": ("k_cool_apply<float>",), "cool_grad": ("k_cool_grad<float>",),
-             "cool_omega": ("k_cool_omega<float>",)},
+             "cool_apply": ("k_cool_apply_un<float>",), "cool_grad": ("k_cool_grad<float>",),
+             "cool_omega": ("k_cool_omega<float>",), "cool_grad_omega": ("k_cool_grad_omega<float>",)},
     "df64": {"force": ("k_plaq_force_a_df", "k_plaq_force_b_df"),
              "update": ("k_update_gather<df64, 0>",), "cool_apply": ("k_cool_apply_df",),
              "cool_grad": ("k_cool_grad_df",), "cool_omega": ("k_cool_omega<df64>",)},
 }
 
 
-def ingest_ncu(path, out_json=None):
-    """Reads an ncu launch list (--csv, metrics gpu__time_duration.sum and
-    dram__bytes_{read,write}.sum, --kernel-name-base demangled), prints its
-    per-kernel summary as a markdown table and writes the per-launch DRAM bytes
-    of each roofline family to profiles/dram_traffic.json, stamped with the
-    current kernel-source hash."""
+def ingest_ncu(path, out_json=None, capture_sites=None):
+    """Reads ncu launch lists (--csv, metrics gpu__time_duration.sum and
+    dram__bytes_{read,write}.sum, --kernel-name-base demangled; one path or a
+    list), prints the per-kernel summary as a markdown table and writes the
+    per-launch DRAM bytes of each roofline family to profiles/dram_traffic.json,
+    stamped with the current kernel-source hash and, when given, the sites of
+    the captured lattice (dram_traffic scales to the bench's lattice)."""
     import csv
     import re
-    rows = list(csv.reader(line for line in open(path) if line.startswith('"')))
-    hdr, rows = rows[0], rows[1:]
-    col = {h: i for i, h in enumerate(hdr)}
+    paths = [path] if isinstance(path, str) else list(path)
+    rows = []
+    for k, pth in enumerate(paths):
+        part = list(csv.reader(line for line in open(pth) if line.startswith('"')))
+        hdr = part[0]
+        col = {h: i for i, h in enumerate(hdr)}
+        for r in part[1:]:
+            r = list(r)
+            r[col["ID"]] = "%d:%s" % (k, r[col["ID"]])  # launch IDs restart in every file
+            rows.append(r)
     scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "ns": 1e-6, "nsecond": 1e-6, "us": 1e-3,
              "usecond": 1e-3, "ms": 1.0, "msecond": 1.0, "s": 1e3, "second": 1e3}
     launches = {}
@@ -178,6 +192,8 @@ def ingest_ncu(path, out_json=None):
             n, a["n"], a["ms"], 100 * a["ms"] / tot, a["ms"] / a["n"], a["rd"] / a["n"] / 1e9, a["wr"] / a["n"] / 1e9))
     h = kernel_source_hash()
     out = {"source_hash": h}
+    if capture_sites:
+        out["capture_sites"] = capture_sites
     for form, fams in TRAFFIC_FAMILIES.items():
         for fam, kernels in fams.items():
             if all(k in agg for k in kernels):
@@ -394,7 +410,7 @@ def roofline_of(prec_name, V, phases, sm_max_mhz, theta_on=True):
                "152 SMs x 128 FP32 FMA/clk x %d MHz (FP32 is not in MEASURED_PEAKS.json)" % sm_max_mhz)
         if not ops:
             return {"kernel": dom, "bound": "alu", "pipe": "fp32", "achieved": None, "peak": round(peak, 4),
-                    "unit": "TFLOP/s", "frac": None, "traffic": dram_traffic(dom, prec_name),
+                    "unit": "TFLOP/s", "frac": None, "traffic": dram_traffic(dom, prec_name, V),
                     "avg_launch_ms": round(per, 4), "launches": n, "peak_source": src}
         flops = (2 * ops["ffma"] + ops["fadd"] + ops["fmul"]) * V
         inst = (ops["ffma"] + ops["fadd"] + ops["fmul"]) * V
@@ -404,7 +420,7 @@ def roofline_of(prec_name, V, phases, sm_max_mhz, theta_on=True):
         return {"kernel": dom, "bound": "alu", "pipe": "fp32", "achieved": round(ach, 4),
                 "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
                 "fp32_pipe_inst_per_s": round(inst_rate * 1e12, 1), "fp32_pipe_inst_frac": round(inst_rate / inst_peak, 4),
-                "traffic": dram_traffic(dom, prec_name), "flops_per_launch": flops,
+                "traffic": dram_traffic(dom, prec_name, V), "flops_per_launch": flops,
                 "avg_launch_ms": round(per, 4), "launches": n, "peak_source": src}
     flops = fm[dom] * V
     if pipe[dom] == "fp64":
@@ -416,7 +432,7 @@ def roofline_of(prec_name, V, phases, sm_max_mhz, theta_on=True):
     ach = flops / (per * 1e-3) / 1e12
     return {"kernel": dom, "bound": "alu", "pipe": pipe[dom], "achieved": round(ach, 4),
             "peak": round(peak, 4), "unit": "TFLOP/s", "frac": round(ach / peak, 4),
-            "traffic": dram_traffic(dom, prec_name), "flops_per_launch": flops,
+            "traffic": dram_traffic(dom, prec_name, V), "flops_per_launch": flops,
             "avg_launch_ms": round(per, 4), "launches": n, "peak_source": src}
 
 
@@ -829,10 +845,14 @@ def precision_mode(args):
 # 16^4 long runs (the theta-scan config): FP64, FP32 storage and DF64
 # ensembles of independent chains (disjoint Philox seeds per form), compared
 # in distribution after thermalisation.
-LONGRUN = dict(L=(16, 16, 16, 16), beta=6.0, thetas=(0.0, 0.5, 1.0, 2.0), eps=0.005, every=10)
+# Without the adaptive step size most theta = 2 chains (and some theta = 1
+# chains) run away within 1000 steps at eps 0.005; with k_ref = 12 (the
+# batch and serving workloads' value) every chain stays finite.
+LONGRUN = dict(L=(16, 16, 16, 16), beta=6.0, thetas=(0.0, 0.5, 1.0, 2.0), eps=0.005, every=10, k_ref=12.0)
 LONGRUN_NAME = ("16^4 SU(3) Wilson + clover theta, beta 6.0, theta in {0, 0.5, 1, 2}, cold start; CL steps at "
-                "eps 0.005 with adaptive cooling (alpha_ad = 0.1 / D_2, 0..10 sweeps, stop below 1 % relative "
-                "progress or within 1e-6 of SU(3)); observables every 10 steps")
+                "eps 0.005 with the adaptive step size (k_ref 12) and adaptive cooling (alpha_ad = 0.1 / D_2, "
+                "0..10 sweeps, stop below 1 % relative progress or within 1e-6 of SU(3)); observables every 10 "
+                "steps")
 
 
 def longrun_mode(args):
@@ -855,7 +875,7 @@ def longrun_mode(args):
             seeds = [7000 + off + i for i in range(args.longrun_chains)]
             t0 = time.perf_counter()
             ser = studies.longrun(L, w["beta"], theta, prec, seeds, args.longrun_steps, every=w["every"],
-                                  eps=w["eps"])
+                                  eps=w["eps"], k_ref=w["k_ref"])
             sec = time.perf_counter() - t0
             st = studies.chain_means(ser)
             stats[name] = st
@@ -868,15 +888,20 @@ def longrun_mode(args):
                                                    for j, k in enumerate(studies.SERIES_KEYS)}
             _log("longrun theta %.1f %s: %.1f s" % (theta, name, sec))
         for name in ("fp32_storage", "df64"):
+            if stats[name]["chains"] < 2 or stats["fp64"]["chains"] < 2:
+                row["z_%s_vs_fp64" % name] = None  # too few finite chains for an error bar
+                continue
             z = studies.compare_means(stats[name], stats["fp64"], floors[name])
             row["z_%s_vs_fp64" % name] = dict(zip(studies.SERIES_KEYS, np.round(z, 3).tolist()))
         out["%g" % theta] = row
     clocks = sampler.stop()
-    zmax = max(v for row in out.values() for key in row if key.startswith("z_") for v in row[key].values())
+    zs = [v for row in out.values() for key in row if key.startswith("z_") and row[key] for v in row[key].values()]
+    runaway = sum(row[f]["nonfinite_chains"] for row in out.values() for f in ("fp64", "fp32_storage", "df64"))
     print(json.dumps({"metric": "long-run observables per arithmetic form (ensemble means, 3 sigma bar)",
                       "workload": LONGRUN_NAME, "lattice": list(L), "steps": args.longrun_steps,
                       "chains_per_form": args.longrun_chains, "thermalisation_dropped": 0.2,
-                      "max_z": zmax, "thetas": out, "clocks": clocks}), flush=True)
+                      "max_z": max(zs) if zs else None, "runaway_chains": runaway, "thetas": out,
+                      "clocks": clocks}), flush=True)
 
 
 def main():
@@ -907,11 +932,13 @@ def main():
     ap.add_argument("--batch-steps", type=int, default=200)
     ap.add_argument("--batch-arms", nargs="*", default=None, help="batch: run only these arms")
     ap.add_argument("--no-serve-df64", action="store_true", help="serve: skip the double-float arm")
-    ap.add_argument("--ingest-ncu", metavar="CSV", default=None,
-                    help="summarise an ncu launch list with DRAM bytes and update profiles/dram_traffic.json")
+    ap.add_argument("--ingest-ncu", metavar="CSV", nargs="+", default=None,
+                    help="summarise ncu launch lists with DRAM bytes and update profiles/dram_traffic.json")
+    ap.add_argument("--ingest-sites", type=int, default=None,
+                    help="--ingest-ncu: sites of the captured lattice (the bench scales the bytes to its own)")
     args = ap.parse_args()
     if args.ingest_ncu:
-        return ingest_ncu(args.ingest_ncu)
+        return ingest_ncu(args.ingest_ncu, capture_sites=args.ingest_sites)
     if args.mode == "batch":
         return batch_mode(args)
     if args.mode == "serve":

@@ -51,3 +51,23 @@ def test_ingest_folds_launches_into_families(tmp_path):
     assert "fp32" not in out  # no kernel of that form in the list
     saved = json.loads(out_json.read_text())
     assert saved["source_hash"] == bench.kernel_source_hash() == out["fp64"]["force"]["source_hash"]
+
+
+def test_ingest_scales_a_small_capture_to_the_bench_lattice(tmp_path):
+    """Per-kernel captures run a smaller lattice; the bytes per launch are
+    stored with the captured site count and scaled to the bench's sites."""
+    lines = [HDR]
+    up = "void k_update_gather<float, 0>(Geo, const vec2_of<T1>::type *, UpdArgs)"
+    lines += _launch(0, up, 0.6, 0.1, 1.0)
+    a = tmp_path / "a.csv"
+    a.write_text("\n".join(lines) + "\n")
+    lines = [HDR] + _launch(0, up, 0.8, 0.1, 1.0)  # a second file: its launch IDs restart
+    b = tmp_path / "b.csv"
+    b.write_text("\n".join(lines) + "\n")
+    out_json = tmp_path / "traffic.json"
+    agg, out = bench.ingest_ncu([str(a), str(b)], str(out_json), capture_sites=331776)
+    assert agg["k_update_gather<float, 0>"]["n"] == 2
+    per = out["fp32"]["update"]["bytes_per_launch"]
+    assert abs(per - 0.8e9) < 1.0
+    scaled = bench.dram_traffic("update", "fp32", 32 ** 4, path=str(out_json))
+    assert abs(scaled - 0.8e9 * 32 ** 4 / 331776) < 1.0

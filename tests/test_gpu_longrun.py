@@ -3,7 +3,8 @@
 Complex-Langevin trajectories decorrelate chaotically, so after many steps
 two arithmetic forms (or the GPU and the oracle) can only agree
 statistically.  Here independent ensembles -- disjoint Philox seeds, cold
-starts, CL with adaptive cooling (alpha_ad = 0.1 / D_2, 0..10 sweeps) --
+starts, CL with the adaptive step size (k_ref 12) and adaptive cooling
+(alpha_ad = 0.1 / D_2, 0..10 sweeps) --
 are run long enough to thermalise, and the ensemble means of Re/Im of the
 plaquette, the unitarity norm and Re/Im Q_L (first 20 % of each chain
 dropped, errors from the chain-to-chain scatter) must agree within 4
@@ -32,7 +33,7 @@ def test_forms_agree_in_distribution(theta):
     L, beta, steps, k = (8, 8, 8, 8), 6.0, 600, 6
     st = {}
     for name, prec, off in (("fp64", cl.CL_FP64, 0), ("fp32", cl.CL_FP32_STORAGE, 100), ("df64", cl.CL_DF64, 200)):
-        ser = studies.longrun(L, beta, theta, prec, [300 + off + i for i in range(k)], steps)
+        ser = studies.longrun(L, beta, theta, prec, [300 + off + i for i in range(k)], steps, k_ref=12.0)
         st[name] = studies.chain_means(ser)
         assert st[name]["dropped"] == 0
     for name, floor in (("fp32", 1e-6), ("df64", 1e-12)):
