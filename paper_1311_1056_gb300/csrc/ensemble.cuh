@@ -80,7 +80,7 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_ens_force_b(const ChainDesc*
 }
 
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_ens_force_ab(const ChainDesc* __restrict__ cd,
+__global__ void __maxnreg__(FORCE_AB_MAXNREG) k_ens_force_ab(const ChainDesc* __restrict__ cd,
                                                                  const WorkItem* __restrict__ w) {
   typedef typename vec2_of<T>::type V2;
   const WorkItem it = w[blockIdx.x];

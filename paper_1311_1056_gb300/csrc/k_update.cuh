@@ -438,8 +438,15 @@ __device__ __forceinline__ void k_plaq_force_ab_body(Geo g, const typename vec2_
   force_stage_a(Gh, g, s, x, p, U, Ui, Dq, F, C, beta6);
   force_stage_b(Gh, g, s, x, p, U, Ui, Pq, Dq, F, C, beta6);
 }
+// Left to itself the compiler gives the fused FP32 force 228 registers, two
+// blocks of 128 per SM; capped at 160 it keeps three (a few hundred bytes of
+// spills, served by L1): 1.27 -> 1.04 ms per 32^4 step on GB300 (caps of 152
+// and 168: 1.08 and 1.10 ms; 128: 1.50 ms; the split a / b form in FP32:
+// 1.57 ms).  __maxnreg__ excludes __launch_bounds__; at 160 registers every
+// tuned block size up to TUNE_MAX_BLOCK still launches.
+const int FORCE_AB_MAXNREG = 160;
 template <typename T>
-__global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_plaq_force_ab(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+__global__ void __maxnreg__(FORCE_AB_MAXNREG) k_plaq_force_ab(Geo g, const typename vec2_of<T>::type* __restrict__ U,
                                                        const typename vec2_of<T>::type* __restrict__ Ui,
                                                        const typename vec2_of<T>::type* __restrict__ Pq,
                                                        const typename vec2_of<T>::type* __restrict__ Dq,
