@@ -205,6 +205,7 @@ def _fused_chains(prec):
         dict(L=(4, 6, 4, 8), beta=6.2, theta=1.5, prec=prec, seed=23, k_ref=0.0),
         dict(L=(3, 5, 4, 7), beta=5.9, theta=2.0, prec=prec, seed=24, k_ref=4.0),
         dict(L=(8, 8, 8, 8), beta=6.0, theta=1.0, prec=prec, seed=25, k_ref=0.0),
+        dict(L=(2, 1, 3, 1), beta=6.0, theta=0.7, prec=prec, seed=26, k_ref=0.0),  # extents of 1
     ]
 
 
@@ -216,11 +217,12 @@ def test_fused_batch_equals_each_chain_alone(prec):
     different sweep limits, theta = 0 and != 0, adaptive and fixed step size.
     Every chain must end where it ends alone, bit for bit."""
     chains = _fused_chains(prec)
-    eps = [0.01, 0.005, 0.01, 0.008, 0.006]
+    eps = [0.01, 0.005, 0.01, 0.008, 0.006, 0.01]
     cps = [cl.make_cool(**ADAPT), cl.make_cool(eps=0.005, alpha=1.0, mode=cl.CL_D1, forced_sweeps=2),
            cl.make_cool(eps=0.01, alpha=0.5, mode=cl.CL_D0, n_min=0, n_max=4, tol_rel=0.1),
            cl.make_cool(eps=0.008, alpha=1.0, mode=cl.CL_D2_RMS, n_min=1, n_max=5, tol_rel=0.05),
-           cl.make_cool(eps=0.006, alpha=1.0, mode=cl.CL_D1, n_min=0, n_max=3, tol_rel=1e-3)]
+           cl.make_cool(eps=0.006, alpha=1.0, mode=cl.CL_D1, n_min=0, n_max=3, tol_rel=1e-3),
+           cl.make_cool(eps=0.01, alpha=1.0, mode=cl.CL_D2_MEANABS, forced_sweeps=3)]
 
     def make(c):
         lat = _lat(L=c["L"], beta=c["beta"], theta=c["theta"], prec=c["prec"], seed=c["seed"])
