@@ -133,11 +133,11 @@ def dram_traffic(kernel, prec, V=None, path=None):
 # over its kernels: the split force runs a then b once per step).
 TRAFFIC_FAMILIES = {
     "fp64": {"force": ("k_plaq_force_a<double>", "k_plaq_force_b<double>"),
-             "update": ("k_update_gather<double, 0>",), "cool_apply": ("k_cool_apply_un<double>",),
+             "update": ("k_update_gather<double, 0>",), "cool_apply": ("k_cool_apply_tiles<double>",),
              "cool_grad": ("k_cool_grad<double>",), "cool_omega": ("k_cool_omega<double>",),
              "cool_grad_omega": ("k_cool_grad_omega<double>",)},
     "fp32": {"force": ("k_plaq_force_ab<float>",), "update": ("k_update_gather<float, 0>",),
-             "cool_apply": ("k_cool_apply_un<float>",), "cool_grad": ("k_cool_grad<float>",),
+             "cool_apply": ("k_cool_apply_tiles<float>",), "cool_grad": ("k_cool_grad<float>",),
              "cool_omega": ("k_cool_omega<float>",), "cool_grad_omega": ("k_cool_grad_omega<float>",)},
     "df64": {"force": ("k_plaq_force_a_df", "k_plaq_force_b_df"),
              "update": ("k_update_gather<df64, 0>",), "cool_apply": ("k_cool_apply_df",),

@@ -49,6 +49,7 @@ namespace clrt {
 
 // Internal precision codes equal cl_precision: 0 FP64, 1 FP32 storage, 2 DF64.
 size_t real_size(const cl_lattice* l) { return l->prec == 1 ? 4 : 8; }
+size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
 cudaEvent_t take_event(cl_lattice* l) {
   if (!l->ev_pool->empty()) {
@@ -190,11 +191,12 @@ cl_status check_cool(const cl_cool_params* cp) {
 //
 // D_0 and D_1 (FP64, FP32 storage) run single-pass sweeps: their strength
 // needs only the unitarity norm, so after the first sweep each apply also
-// sums the norm of the links it writes, the rule decides the next sweep
-// from those sums, and one kernel forms the gradient and Omega together (f
-// stays in registers): rule, gradient + Omega, apply per sweep instead of
-// gradient, rule, Omega, apply.  D_2 needs sum |f_ax| before Omega, so it
-// keeps the four-kernel sweep, as does the DF64 form.
+// sums the norm of the links it writes (one record per tile), the rule
+// decides the next sweep from those records, and one kernel forms the
+// gradient and Omega together (f stays in registers): rule, gradient +
+// Omega, apply per sweep instead of gradient, rule, Omega, apply.  D_2 needs
+// sum |f_ax| before Omega, so it keeps the four-kernel sweep, as does the
+// DF64 form.
 cl_status do_cool(cl_lattice* l, const cl_cool_params* cp) {
   CoolArgs a = cool_args(cp);
   const int n_iter = cp->forced_sweeps >= 0 ? cp->forced_sweeps : cp->n_max;
@@ -210,16 +212,16 @@ cl_status do_cool(cl_lattice* l, const cl_cool_params* cp) {
       return launch_cool_omega(l->prec, l->g, l->f, l->Om, l->Omi, cp->eps, l->cs, l->st);
     }));
     CK(timed(l, CL_PHASE_COOL_APPLY, [&] {
-      return launch_cool_apply_un(l->prec, l->g, l->U, l->Om, l->Omi, l->partials, l->cs, l->st);
+      return launch_cool_apply_tiles(l->prec, l->g, l->U, l->Om, l->Omi, l->crec, l->cs, l->st);
     }));
     for (int k = 1; k <= n_iter; ++k) {
-      CK(timed(l, CL_PHASE_COOL_RULE, [&] { return launch_cool_adapt(l->g, l->partials, a, l->cs, 0, l->st); }));
+      CK(timed(l, CL_PHASE_COOL_RULE, [&] { return launch_cool_adapt_tiles(l->g, l->crec, a, l->cs, l->st); }));
       if (k == n_iter) break;
       CK(timed(l, CL_PHASE_COOL_GRAD_OMEGA, [&] {
         return launch_cool_grad_omega(l->prec, l->g, l->U, l->Om, l->Omi, cp->eps, l->cs, l->st);
       }));
       CK(timed(l, CL_PHASE_COOL_APPLY, [&] {
-        return launch_cool_apply_un(l->prec, l->g, l->U, l->Om, l->Omi, l->partials, l->cs, l->st);
+        return launch_cool_apply_tiles(l->prec, l->g, l->U, l->Om, l->Omi, l->crec, l->cs, l->st);
       }));
     }
     return CL_OK;
@@ -360,17 +362,20 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
   //  * Gq, the split force's parked partial sums: plane p at C plane 4p + 1
   //    (Gq points at plane 1; the force kernels index it GQ_PLANE * p), the
   //    slot that stage b writes only after reading the partial back;
-  //  * the cooling fields f (8 reals per site, [a][V]) and the packed
-  //    Hermitian Omega, Omega^{-1} (9 reals per site each), used only by the
-  //    cooling sweeps and the start's gauge transformation, never while C
-  //    holds drift contributions.  They need 8 + 8 + 9 * 2 * 8 bytes per site
-  //    at most, C has 24 * 9 * 8 or more.
+  //  * the cooling fields f (8 FP64 per site, [a][V]) and the packed
+  //    Hermitian Omega, Omega^{-1} (9 reals per site each), then, on a
+  //    256-byte boundary, the single-pass apply's tile records (16 bytes per
+  //    tile, at most V / 128 + L3 tiles); used only by the cooling sweeps and
+  //    the start's gauge transformation, never while C holds drift
+  //    contributions.  They need at most 64 + 144 + 17 bytes per site plus
+  //    256, and C has 24 * 9 * 8 bytes per site or more.
   {
     char* c = (char*)l->C;
     l->Gq = c + l->esz * 9 * Vs;
     l->f = c;
     l->Om = c + sizeof(double) * 8 * Vs;
     l->Omi = c + sizeof(double) * 8 * Vs + real_size(l) * 9 * Vs;
+    l->crec = (double*)(c + align256(sizeof(double) * 8 * Vs + 2 * real_size(l) * 9 * Vs));
   }
   cudaError_t e = l->prec == 2 ? prepare_df64_kernels() : cudaSuccess;
   if (e == cudaSuccess) e = init_state(l);
@@ -817,7 +822,7 @@ struct FusedPlan {
     int n;
   };
   List fam[ENS_NFAM + 3];  // + the gradient of the first sweep (all chains), the first Omega (all), spare
-  List all_chains, adaptive_chains, adaptive_flags;
+  List all_chains, adaptive_chains, adaptive_flags, sp_chains, four_chains;
   int n_iter;
   bool any_adaptive;
 };
@@ -863,7 +868,13 @@ FusedPlan plan_fused(const cl_batch* b) {
   add(ENS_COOL_OMEGA, four, tiles);
   add(ENS_COOL_APPLY, four, x4);
   add(ENS_COOL_GRAD_OMEGA, sp, red);
-  add(ENS_COOL_APPLY_UN, sp, red);
+  P.fam[ENS_COOL_APPLY_UN].off = P.items.size();
+  for (int i = 0; i < n; ++i)
+    if (sp(i)) {
+      const int nt = cool_tiles(b->lats[i]->g);
+      for (int t = 0; t < nt; ++t) P.items.push_back(WorkItem{i, t});
+    }
+  P.fam[ENS_COOL_APPLY_UN].n = (int)(P.items.size() - P.fam[ENS_COOL_APPLY_UN].off);
   P.all_chains.off = P.ints.size();
   for (int i = 0; i < n; ++i) P.ints.push_back(i);
   P.all_chains.n = n;
@@ -874,6 +885,14 @@ FusedPlan plan_fused(const cl_batch* b) {
   P.adaptive_flags.off = P.ints.size();
   for (int i = 0; i < n; ++i) P.ints.push_back(ad(i) ? 1 : 0);
   P.adaptive_flags.n = n;
+  P.sp_chains.off = P.ints.size();
+  for (int i = 0; i < n; ++i)
+    if (sp(i)) P.ints.push_back(i);
+  P.sp_chains.n = (int)(P.ints.size() - P.sp_chains.off);
+  P.four_chains.off = P.ints.size();
+  for (int i = 0; i < n; ++i)
+    if (four(i)) P.ints.push_back(i);
+  P.four_chains.n = (int)(P.ints.size() - P.four_chains.off);
   P.any_adaptive = P.adaptive_chains.n > 0;
   P.n_iter = 0;
   if (b->with_cooling)
@@ -903,6 +922,7 @@ ChainDesc describe(const cl_lattice* l, double eps, const cl_cool_params& cp, bo
   c.Om = l->Om;
   c.Omi = l->Omi;
   c.partials = l->partials;
+  c.arec = l->crec;
   c.cs = l->cs;
   c.sd = l->sd;
   c.beta = l->p.beta;
@@ -958,8 +978,16 @@ cl_status enqueue_fused_step(const cl_batch* b, const FusedPlan& P, const ChainD
     }
     for (int k = 1; k <= P.n_iter; ++k) {
       CK(fam(ENS_COOL_GRAD, ENS_COOL_GRAD, 0));
-      CK(launch_ens_cool_adapt(cd, all, n, 0, st));
-      ++nl;
+      // the rule: four-kernel chains from the gradient's records, single-pass
+      // chains from their apply's tile records
+      if (P.four_chains.n) {
+        CK(launch_ens_cool_adapt(cd, ints + P.four_chains.off, P.four_chains.n, 0, st));
+        ++nl;
+      }
+      if (P.sp_chains.n) {
+        CK(launch_ens_cool_adapt_tiles(cd, ints + P.sp_chains.off, P.sp_chains.n, st));
+        ++nl;
+      }
       if (k == P.n_iter) break;
       CK(fam(ENS_COOL_OMEGA, ENS_COOL_OMEGA, 0));
       CK(fam(ENS_COOL_GRAD_OMEGA, ENS_COOL_GRAD_OMEGA, 0));

@@ -493,12 +493,9 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad_omega(Geo g,
 // (or its RMS).  Sweep count: at least n_min, at most n_max; stop once the
 // norm decreases by less than tol_rel of its distance from 1 or that distance
 // is below d_floor; no sweep when D < d_guard; forced_sweeps >= 0 fixes the count.
-__device__ __forceinline__ void cool_adapt_body(const Geo& g, const double* partials, int nb, const CoolArgs& a,
-                                                CoolState* cs, int first) {
-  __shared__ double tot[NQ_COOL];
-  reduce_partials<NQ_COOL, -1>(partials, nb, tot);
-  __syncthreads();
-  if (threadIdx.x != 0) return;
+// tot: sum |f_ax|, sum f_ax^2, sum (1/3) Tr U U^+ over the links, nonfinite count.
+__device__ __forceinline__ void cool_rule(const Geo& g, const double* tot, const CoolArgs& a, CoolState* cs,
+                                          int first) {
   if (first) {
     cs->alpha_ad = 0.0;
     cs->alpha_ad_last = 0.0;
@@ -543,6 +540,14 @@ __device__ __forceinline__ void cool_adapt_body(const Geo& g, const double* part
   cs->alpha_ad_last = cs->alpha_ad;
   cs->sweeps += 1;
   cs->un_prev = un;
+}
+__device__ __forceinline__ void cool_adapt_body(const Geo& g, const double* partials, int nb, const CoolArgs& a,
+                                                CoolState* cs, int first) {
+  __shared__ double tot[NQ_COOL];
+  reduce_partials<NQ_COOL, -1>(partials, nb, tot);
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  cool_rule(g, tot, a, cs, first);
 }
 __global__ void k_cool_adapt(Geo g, const double* partials, int nb, CoolArgs a, CoolState* cs, int first) {
   cool_adapt_body(g, partials, nb, a, cs, first);
@@ -622,18 +627,31 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_apply(Geo g, typename v
   cool_apply_body<T>(g, U, Om, Omi, cs, blockIdx.x);
 }
 
-// Single-pass sweep of the D_0 / D_1 rules, part 2: the apply, site by site
-// (Omega_x loaded once for the site's four links), with per block the sums
-// the rule needs for the next sweep: (1/3) Tr U U^+ of the updated links
-// (FP64) and their nonfinite count, in the gradient's record layout (the
-// |f| and f^2 slots are 0).
+// Single-pass sweep of the D_0 / D_1 rules, part 2: the apply over tiles of
+// COOL_TILE consecutive sites inside one x3 layer (tile `tile` of layer
+// `layer`; the last tile of a layer may be short), one thread per site and
+// its four links (Omega_x loaded once), with one record per tile of what the
+// rule needs for the next sweep: the sum of (1/3) Tr U U^+ over the tile's
+// updated links (FP64, summed in a fixed order) and their nonfinite count (a
+// NaN or Inf entry makes a site's sum of squares NaN or +Inf).  A record per
+// tile, not per block of a grid-stride loop, makes the records and the rule's
+// sum independent of the launch shape: a fused batch, which runs the tiles of
+// many chains in one launch, gives each chain the records of its lone run.
+// Resident blocks of COOL_TILE threads the tile kernels are built for: 72
+// registers a thread with FP32 links, 128 with FP64 ones (no spills).
+#define COOL_TILE_MIN_BLOCKS(T) (sizeof(T) == 4 ? 7 : 4)
+__device__ __forceinline__ int layer_sites(const Geo& g) { return g.V / g.L[3]; }
+__device__ __forceinline__ int tiles_per_layer(const Geo& g) { return (layer_sites(g) + COOL_TILE - 1) / COOL_TILE; }
+
 template <typename T>
-__device__ __forceinline__ void cool_apply_un_body(const Geo& g, typename vec2_of<T>::type* U,
-                                                   const T* __restrict__ Om, const T* __restrict__ Omi,
-                                                   double* partials, const CoolState* cs, int vb, int nvb) {
-  if (cs->done) return;
-  double v[NQ_COOL] = {0.0, 0.0, 0.0, 0.0};
-  for (int s = vb * blockDim.x + threadIdx.x; s < g.V; s += nvb * blockDim.x) {
+__device__ __forceinline__ void cool_apply_tile(const Geo& g, typename vec2_of<T>::type* U, const T* __restrict__ Om,
+                                                const T* __restrict__ Omi, double2* rec, int layer, int tile) {
+  const int V3 = layer_sites(g);
+  const int s0 = layer * V3 + tile * COOL_TILE;
+  const int s1 = min(s0 + COOL_TILE, (layer + 1) * V3);
+  const int s = s0 + (int)threadIdx.x;
+  double2 v = make_double2(0.0, 0.0);
+  if (s < s1) {
     int x[4];
     site_coords(g, s, x);
     mat<T> o;
@@ -649,17 +667,75 @@ __device__ __forceinline__ void cool_apply_un_body(const Geo& g, typename vec2_o
       store(U, mu, s, g.V, u);
       un += norm2(u);
     }
-    // a NaN or Inf entry makes the sum of squares NaN or +Inf
-    v[2] += cvt<double>(un) * (1.0 / 3.0);
-    v[3] += isfinite(un) ? 0.0 : 1.0;
+    v.x = cvt<double>(un) * (1.0 / 3.0);
+    v.y = isfinite(un) ? 0.0 : 1.0;
   }
-  block_reduce_store<NQ_COOL, -1>(v, partials + (size_t)vb * NQ_COOL);
+  // fixed-order tile sum: warp shuffles, then the warps' sums in order
+  __shared__ double2 sm[COOL_TILE / 32];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+  }
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double2 t = sm[0];
+#pragma unroll
+    for (int w = 1; w < COOL_TILE / 32; ++w) {
+      t.x += sm[w].x;
+      t.y += sm[w].y;
+    }
+    rec[layer * tiles_per_layer(g) + tile] = t;
+  }
 }
+
+// One block per tile (block b: layer b / tiles_per_layer, tile b % tiles_per_layer).
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS, 4) k_cool_apply_un(Geo g, typename vec2_of<T>::type* U,
-                                                              const T* __restrict__ Om, const T* __restrict__ Omi,
-                                                              double* partials, const CoolState* cs) {
-  cool_apply_un_body<T>(g, U, Om, Omi, partials, cs, blockIdx.x, gridDim.x);
+__global__ void __launch_bounds__(COOL_TILE, COOL_TILE_MIN_BLOCKS(T))
+    k_cool_apply_tiles(Geo g, typename vec2_of<T>::type* U, const T* __restrict__ Om, const T* __restrict__ Omi,
+                       double2* rec, const CoolState* cs) {
+  if (cs->done) return;
+  const int tpl = tiles_per_layer(g);
+  cool_apply_tile<T>(g, U, Om, Omi, rec, blockIdx.x / tpl, blockIdx.x % tpl);
+}
+
+// The rule from the tile records: a fixed-order sum over the nrec records by
+// COOL_RULE_THREADS threads (thread t takes records t, t + COOL_RULE_THREADS,
+// ..., then warp shuffles and the warps' sums in order), with the |f| slots
+// of the record layout 0 (D_0 / D_1 do not use them).
+enum { COOL_RULE_THREADS = 1024 };
+__device__ __forceinline__ void cool_adapt_tiles_body(const Geo& g, const double2* __restrict__ rec, int nrec,
+                                                      const CoolArgs& a, CoolState* cs) {
+  __shared__ double2 sm[COOL_RULE_THREADS / 32];
+  double2 v = make_double2(0.0, 0.0);
+#pragma unroll 4
+  for (int b = threadIdx.x; b < nrec; b += COOL_RULE_THREADS) {
+    const double2 r = __ldg(rec + b);
+    v.x += r.x;
+    v.y += r.y;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+  }
+  if ((threadIdx.x & 31) == 0) sm[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x >= 32) return;
+  v = sm[threadIdx.x];
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, off);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, off);
+  }
+  if (threadIdx.x != 0 || cs->done) return;
+  const double tot[NQ_COOL] = {0.0, 0.0, v.x, v.y};
+  cool_rule(g, tot, a, cs, 0);
+}
+__global__ void __launch_bounds__(COOL_RULE_THREADS) k_cool_adapt_tiles(Geo g, const double2* rec, int nrec,
+                                                                        CoolArgs a, CoolState* cs) {
+  cool_adapt_tiles_body(g, rec, nrec, a, cs);
 }
 
 const int DF_APPLY_BLOCK = 128;  // the DF64 apply's largest block (its launch bound)
@@ -907,18 +983,27 @@ __global__ void __launch_bounds__(RED_THREADS) k_ens_cool_grad_omega(const Chain
                           ens_reduce_blocks(c.V));
 }
 template <typename T>
-__global__ void __launch_bounds__(RED_THREADS, 4) k_ens_cool_apply_un(const ChainDesc* __restrict__ cd,
-                                                                     const WorkItem* __restrict__ w) {
+__global__ void __launch_bounds__(COOL_TILE, COOL_TILE_MIN_BLOCKS(T)) k_ens_cool_apply_tiles(const ChainDesc* __restrict__ cd,
+                                                                   const WorkItem* __restrict__ w) {
   typedef typename vec2_of<T>::type V2;
   const WorkItem it = w[blockIdx.x];
   const ChainDesc& c = cd[it.chain];
-  cool_apply_un_body<T>(ens_geo(c), (V2*)c.Un, (const T*)c.Om, (const T*)c.Omi, c.partials, c.cs, it.vb,
-                        ens_reduce_blocks(c.V));
+  const Geo g = ens_geo(c);
+  if (c.cs->done) return;
+  const int tpl = tiles_per_layer(g);
+  cool_apply_tile<T>(g, (V2*)c.Un, (const T*)c.Om, (const T*)c.Omi, (double2*)c.arec, it.vb / tpl, it.vb % tpl);
 }
 // the rule, one block of 256 threads per listed chain
 __global__ void k_ens_cool_adapt(const ChainDesc* __restrict__ cd, const int* __restrict__ chains, int first) {
   const ChainDesc& c = cd[chains[blockIdx.x]];
   cool_adapt_body(ens_geo(c), c.partials, ens_reduce_blocks(c.V), c.ca, c.cs, first);
+}
+// the rule of single-pass chains from their tile records, one block per listed chain
+__global__ void __launch_bounds__(COOL_RULE_THREADS) k_ens_cool_adapt_tiles(const ChainDesc* __restrict__ cd,
+                                                               const int* __restrict__ chains) {
+  const ChainDesc& c = cd[chains[blockIdx.x]];
+  const Geo g = ens_geo(c);
+  cool_adapt_tiles_body(g, (const double2*)c.arec, g.L[3] * tiles_per_layer(g), c.ca, c.cs);
 }
 
 template <typename T>
@@ -929,7 +1014,7 @@ cudaError_t launch_ens_cool_family(int fam, const ChainDesc* cd, const WorkItem*
     case ENS_COOL_OMEGA: k_ens_cool_omega<T><<<n, ENS_BLOCK, 0, st>>>(cd, w); break;
     case ENS_COOL_APPLY: k_ens_cool_apply<T><<<n, ENS_BLOCK, 0, st>>>(cd, w); break;
     case ENS_COOL_GRAD_OMEGA: k_ens_cool_grad_omega<T><<<n, RED_THREADS, 0, st>>>(cd, w); break;
-    case ENS_COOL_APPLY_UN: k_ens_cool_apply_un<T><<<n, RED_THREADS, 0, st>>>(cd, w); break;
+    case ENS_COOL_APPLY_UN: k_ens_cool_apply_tiles<T><<<n, COOL_TILE, 0, st>>>(cd, w); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -952,6 +1037,12 @@ cudaError_t launch_ens(int prec, int fam, const ChainDesc* cd, const WorkItem* w
 cudaError_t launch_ens_cool_adapt(const ChainDesc* cd, const int* chains, int n, int first, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   k_ens_cool_adapt<<<n, 256, 0, st>>>(cd, chains, first);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ens_cool_adapt_tiles(const ChainDesc* cd, const int* chains, int n, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_ens_cool_adapt_tiles<<<n, COOL_RULE_THREADS, 0, st>>>(cd, chains);
   return cudaGetLastError();
 }
 
@@ -1093,17 +1184,29 @@ cudaError_t launch_cool_grad_omega(int prec, const GeoH& h, const void* U, void*
   return cudaGetLastError();
 }
 
-cudaError_t launch_cool_apply_un(int prec, const GeoH& h, void* U, const void* Om, const void* Omi,
-                                 double* partials, const CoolState* cs, cudaStream_t st) {
+int cool_tiles(const GeoH& h) {
+  const int V3 = h.V / h.L[3];
+  return h.L[3] * ((V3 + COOL_TILE - 1) / COOL_TILE);
+}
+
+cudaError_t launch_cool_apply_tiles(int prec, const GeoH& h, void* U, const void* Om, const void* Omi, double* rec,
+                                    const CoolState* cs, cudaStream_t st) {
   Geo g = to_geo(h);
+  const unsigned n = (unsigned)cool_tiles(h);
   if (prec == 0)
-    k_cool_apply_un<double><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (double2*)U, (const double*)Om,
-                                                                        (const double*)Omi, partials, cs);
+    k_cool_apply_tiles<double><<<n, COOL_TILE, 0, st>>>(g, (double2*)U, (const double*)Om, (const double*)Omi,
+                                                        (double2*)rec, cs);
   else if (prec == 1)
-    k_cool_apply_un<float><<<reduce_blocks(g.V), RED_THREADS, 0, st>>>(g, (float2*)U, (const float*)Om,
-                                                                       (const float*)Omi, partials, cs);
+    k_cool_apply_tiles<float><<<n, COOL_TILE, 0, st>>>(g, (float2*)U, (const float*)Om, (const float*)Omi,
+                                                       (double2*)rec, cs);
   else
     return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_cool_adapt_tiles(const GeoH& h, const double* rec, CoolArgs a, CoolState* cs, cudaStream_t st) {
+  Geo g = to_geo(h);
+  k_cool_adapt_tiles<<<1, COOL_RULE_THREADS, 0, st>>>(g, (const double2*)rec, cool_tiles(h), a, cs);
   return cudaGetLastError();
 }
 

@@ -62,6 +62,7 @@ struct ChainDesc {
   int L[4], stride[4], V;
   void *U, *Un, *Ui, *Pq, *Dq, *F, *C, *Gq, *f, *Om, *Omi;
   double* partials;
+  double* arec;             // the single-pass apply's tile records
   CoolState* cs;
   StepDev* sd;
   double beta, sre, sim;    // coupling; clover scale -i theta kappa = sre + i sim
@@ -89,7 +90,7 @@ enum {
   ENS_COOL_OMEGA = 9,   // Omega, Omega^{-1}
   ENS_COOL_APPLY = 10,  // apply, 4 directions
   ENS_COOL_GRAD_OMEGA = 11, // single-pass sweeps (D_0 / D_1): gradient + Omega
-  ENS_COOL_APPLY_UN = 12,   // single-pass sweeps: apply + norm sums
+  ENS_COOL_APPLY_UN = 12,   // single-pass sweeps: apply per tile + norm sums (one item per tile)
   ENS_NFAM = 13
 };
 const int ENS_BLOCK = 128;
@@ -151,12 +152,17 @@ cudaError_t launch_cool_apply(int prec, const GeoH& g, void* U, const void* Om, 
                               const CoolState* cs, cudaStream_t st);
 // Single-pass sweep of the D_0 / D_1 rules (FP64 and FP32 storage only):
 // Omega and Omega^{-1} straight from the gradient with the strength the rule
-// already set, then the apply with the rule's inputs for the next sweep
-// (unitarity norm, nonfinite count) in `partials` (the gradient's layout).
+// already set; the apply over tiles of COOL_TILE sites inside one x3 layer,
+// one record per tile of the rule's inputs for the next sweep ((1/3) Tr U U^+
+// and nonfinite count, 2 doubles; cool_tiles(g) records); the rule from
+// those records.
+enum { COOL_TILE = 128 };
+int cool_tiles(const GeoH& g);
 cudaError_t launch_cool_grad_omega(int prec, const GeoH& g, const void* U, void* Om, void* Omi, double eps,
                                    const CoolState* cs, cudaStream_t st);
-cudaError_t launch_cool_apply_un(int prec, const GeoH& g, void* U, const void* Om, const void* Omi,
-                                 double* partials, const CoolState* cs, cudaStream_t st);
+cudaError_t launch_cool_apply_tiles(int prec, const GeoH& g, void* U, const void* Om, const void* Omi,
+                                    double* rec, const CoolState* cs, cudaStream_t st);
+cudaError_t launch_cool_adapt_tiles(const GeoH& g, const double* rec, CoolArgs a, CoolState* cs, cudaStream_t st);
 // Observables: per-site pass (F must hold the unscaled clover field when
 // with_q) then the final fixed-order reduction into *out.
 cudaError_t launch_obs(int prec, const GeoH& g, const void* U, const void* F, int with_q,
@@ -173,6 +179,8 @@ cudaError_t launch_ens_step_eps(const ChainDesc* cd, const int* chains, int n, c
 cudaError_t launch_ens_step_bump(const ChainDesc* cd, const int* chains, const int* adaptive, int n,
                                  cudaStream_t st);
 cudaError_t launch_ens_cool_adapt(const ChainDesc* cd, const int* chains, int n, int first, cudaStream_t st);
+// the rule of single-pass chains from their tile records (ChainDesc::arec)
+cudaError_t launch_ens_cool_adapt_tiles(const ChainDesc* cd, const int* chains, int n, cudaStream_t st);
 // Integer-pipe float <-> double conversions (cvt.cuh) against the hardware
 // ones on n generated cases; mismatch counts added into bad[0] (float ->
 // double) and bad[1] (double -> float).

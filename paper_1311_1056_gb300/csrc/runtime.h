@@ -27,6 +27,7 @@ struct cl_lattice {
   void* f;     // cooling gradient [8][V] (FP64 in both forms; inside C)
   void* Om;    // packed Hermitian Omega [9][V] (inside C)
   void* Omi;   // and its inverse (inside C)
+  double* crec;  // single-pass apply's tile records, 2 doubles per tile (inside C)
   double* partials;
   clgc::CoolState* cs;
   clgc::ObsOut* obs;
