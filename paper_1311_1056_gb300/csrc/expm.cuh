@@ -45,15 +45,28 @@ __constant__ df64 c_invfact_df[28] = {
     df_const(1.0 / 15511210043330985984000000.0), df_const(1.0 / 403291461126605635584000000.0),
     df_const(1.0 / 10888869450418352160768000000.0)};
 
+// Truncation tolerance of the Taylor series (last term r^N / N! below it).
+// FP64 results: 1.4e-17, under the FP64 rounding of the result (2^-53 =
+// 1.1e-16).  The FP32-storage form rounds the exponential to FP32 (2^-24 =
+// 6e-8) as soon as it is formed, so its series, still evaluated in FP64,
+// stops at 1e-11: a truncation error 6,000 times below that rounding, and
+// about a third fewer terms for the CL update's argument.
+const float TAYLOR_TOL_FP64 = 1.4e-17f;
+const float TAYLOR_TOL_FP32_STORAGE = 1.0e-11f;
+template <typename T>
+__host__ __device__ constexpr float taylor_tol() {
+  return sizeof(T) == 4 ? TAYLOR_TOL_FP32_STORAGE : TAYLOR_TOL_FP64;
+}
+
 // Number of Taylor terms for ||B||_F <= r <= 1 (float arithmetic: an estimate
 // on the cheap pipe; the bound has a factor > 2 of slack at the cut).
-__device__ __forceinline__ int taylor_terms(float r) {
+__device__ __forceinline__ int taylor_terms(float r, float tol = TAYLOR_TOL_FP64) {
   float t = 1.0f;
   int n = 0;
   do {
     ++n;
     t *= r / (float)n;
-  } while (t >= 1.4e-17f && n < 26);
+  } while (t >= tol && n < 26);
   return n;
 }
 
@@ -69,9 +82,10 @@ __device__ __forceinline__ int scaling_steps(float r) {
 // a + b A + c A^2) is done in the link type T (FP64 or FP32); the scalar
 // Cayley-Hamilton recurrences run in FP64.
 // r_hint >= 0 is the Frobenius norm of A when the caller has it (e.g. from an
-// FP32 copy); < 0 computes it.
+// FP32 copy); < 0 computes it.  tol: the series' truncation tolerance.
 template <typename T>
-__device__ __forceinline__ void expm_traceless(mat<T>& E, const mat<T>& A, float r_hint = -1.f) {
+__device__ __forceinline__ void expm_traceless(mat<T>& E, const mat<T>& A, float r_hint = -1.f,
+                                               float tol = TAYLOR_TOL_FP64) {
   mat<T> A2;
   mul(A2, A, A);
   const cx<T> t1 = trace(A2), t0 = trace_mul(A2, A);
@@ -93,7 +107,7 @@ __device__ __forceinline__ void expm_traceless(mat<T>& E, const mat<T>& A, float
     b0 = cx<double>{c0.re * sc2 * sc, c0.im * sc2 * sc};
     b1 = cx<double>{c1.re * sc2, c1.im * sc2};
   }
-  int N = taylor_terms(r);
+  int N = taylor_terms(r, tol);
   cx<double> a = {c_invfact[N], 0.0}, b = {0.0, 0.0}, c = {0.0, 0.0};
   for (int k = N - 1; k >= 0; --k) {
     cx<double> na = cfma(c, b0, cx<double>{c_invfact[k], 0.0});
@@ -217,7 +231,8 @@ __device__ __forceinline__ void herm_square(herm& q, const herm& h) {
 }
 
 // Omega = exp(H) and Omega^{-1} = exp(-H) for traceless Hermitian H.
-__device__ __forceinline__ void expm_hermitian_pair(herm& om, herm& omi, const herm& h) {
+__device__ __forceinline__ void expm_hermitian_pair(herm& om, herm& omi, const herm& h,
+                                                    float tol = TAYLOR_TOL_FP64) {
   herm h2;
   herm_square(h2, h);
   double c1 = 0.5 * (h2.d0 + h2.d1 + h2.d2);  // Tr H^2 / 2 = ||H||_F^2 / 2
@@ -240,7 +255,7 @@ __device__ __forceinline__ void expm_hermitian_pair(herm& om, herm& omi, const h
     b1 = c1 * sc * sc;
     b0 = c0 * sc * sc * sc;
   }
-  int N = taylor_terms(r);
+  int N = taylor_terms(r, tol);
   // exp(B) = a + bB + cB^2 and exp(-B) = ap - bp B + cp B^2 (det(-B) = -det B)
   double a = c_invfact[N], b = 0.0, c = 0.0;
   double ap = a, bp = 0.0, cp = 0.0;
@@ -290,10 +305,19 @@ __device__ __forceinline__ void expm_hermitian_pair(herm& om, herm& omi, const h
 // det(U)^(-1/3) on the principal branch.  Near det = 1 (|det - 1| < 1e-4, the
 // normal case after an update that preserves det up to rounding) the binomial
 // series (1 + d)^(-1/3) = 1 - d/3 + 2d^2/9 - 14d^3/81 + 35d^4/243 - ... is
-// exact to 1e-17; otherwise |det|^(-1/3) exp(-i arg(det)/3).
+// exact to 1e-17; below |d| = 3e-6 (rounding drift of FP64 or FP32 links) its
+// first three terms already are (the next is 14/81 |d|^3 < 5e-18);
+// otherwise |det|^(-1/3) exp(-i arg(det)/3).
 __device__ __forceinline__ cx<double> det_inv_cuberoot(cx<double> d) {
   cx<double> e = {d.re - 1.0, d.im};
-  if (fma(e.re, e.re, e.im * e.im) < 1e-8) {
+  const double e2 = fma(e.re, e.re, e.im * e.im);
+  if (e2 < 1e-11) {
+    cx<double> p = {2.0 / 9.0, 0.0};
+    p = cfma(p, e, cx<double>{-1.0 / 3.0, 0.0});
+    p = cfma(p, e, cx<double>{1.0, 0.0});
+    return p;
+  }
+  if (e2 < 1e-8) {
     cx<double> p = {35.0 / 243.0, 0.0};
     p = cfma(p, e, cx<double>{-14.0 / 81.0, 0.0});
     p = cfma(p, e, cx<double>{2.0 / 9.0, 0.0});

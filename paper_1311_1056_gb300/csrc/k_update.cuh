@@ -588,7 +588,7 @@ __device__ __forceinline__ void k_update_gather_body(Geo g, const typename vec2_
     convert(A, Af);
   }
   mat<double> E;
-  expm_traceless(E, A, rA);
+  expm_traceless(E, A, rA, taylor_tol<T>());
   mat<T> Et, Ul, Un;
   convert(Et, E);
   load(Ul, U, MU, s, g.V);

@@ -221,7 +221,7 @@ __global__ void k_gauge_omega(Geo g, T* Om, T* Omi, uint64_t seed, double sigma)
   double r[8];
   normals_f64<4>(r, seed, 0u, (uint32_t)s, 0u, STREAM_GAUGE);
   herm h = herm_from_algebra(r, -sigma), om, omi;
-  expm_hermitian_pair(om, omi, h);
+  expm_hermitian_pair(om, omi, h, taylor_tol<T>());
   store_herm(Om, s, g.V, om);
   store_herm(Omi, s, g.V, omi);
 }
@@ -475,7 +475,7 @@ __device__ __forceinline__ void cool_grad_omega_body(const Geo& g, const typenam
 #pragma unroll
     for (int a = 0; a < 8; ++a) fd[a] = cvt<double>(fa[a]);
     herm h = herm_from_algebra(fd, c), om, omi;
-    expm_hermitian_pair(om, omi, h);
+    expm_hermitian_pair(om, omi, h, taylor_tol<T>());
     store_herm(Om, s, g.V, om);
     store_herm(Omi, s, g.V, omi);
   }
@@ -590,7 +590,7 @@ __device__ __forceinline__ void cool_omega_body(const Geo& g, const double* __re
 #pragma unroll
     for (int a = 0; a < 8; ++a) fa[a] = __ldg(f + (size_t)a * g.V + s);
     herm h = herm_from_algebra(fa, -eps * cs->alpha_ad), om, omi;
-    expm_hermitian_pair(om, omi, h);
+    expm_hermitian_pair(om, omi, h, taylor_tol<T>());
     store_herm(Om, s, g.V, om);
     store_herm(Omi, s, g.V, omi);
   }
