@@ -113,10 +113,16 @@ cl_status ensure_stage(cl_lattice* l) {
 
 bool theta_nonzero(const cl_lattice* l) { return l->p.theta_re != 0.0 || l->p.theta_im != 0.0; }
 
+// The link-inverse pass: FP64 and DF64 only (the FP32-storage kernels form
+// each inverse from its link where they use it).
+bool needs_inverse_pass(const cl_lattice* l) { return l->prec != 1; }
+
 // Link inverses, plaquettes and D = P - P^{-1}, then (theta != 0) the clover
 // field scaled by (sre + i sim), then the per-plaquette drift contributions.
 cudaError_t do_force(cl_lattice* l, bool th, double sre, double sim) {
-  cudaError_t e = timed(l, CL_PHASE_CLOVER, [&] { return launch_link_inverse(l->prec, l->g, l->U, l->Ui, l->st); });
+  cudaError_t e = cudaSuccess;
+  if (needs_inverse_pass(l))
+    e = timed(l, CL_PHASE_CLOVER, [&] { return launch_link_inverse(l->prec, l->g, l->U, l->Ui, l->st); });
   if (e == cudaSuccess)
     e = timed(l, CL_PHASE_CLOVER, [&] { return launch_plaq(l->prec, l->g, l->U, l->Ui, l->Pq, l->Dq, l->st); });
   if (e == cudaSuccess && th)
@@ -243,7 +249,8 @@ cl_status do_cool(cl_lattice* l, const cl_cool_params* cp) {
 }
 
 cl_status do_obs(cl_lattice* l, ObsOut* dst, double* q_site) {
-  CK(timed(l, CL_PHASE_OBS, [&] { return launch_link_inverse(l->prec, l->g, l->U, l->Ui, l->st); }));
+  if (needs_inverse_pass(l))
+    CK(timed(l, CL_PHASE_OBS, [&] { return launch_link_inverse(l->prec, l->g, l->U, l->Ui, l->st); }));
   CK(timed(l, CL_PHASE_OBS, [&] { return launch_plaq(l->prec, l->g, l->U, l->Ui, l->Pq, l->Dq, l->st); }));
   CK(timed(l, CL_PHASE_OBS, [&] { return launch_clover_rot(l->prec, l->g, l->U, l->Ui, l->Dq, l->F, 1.0, 0.0, l->st); }));
   CK(timed(l, CL_PHASE_OBS, [&] { return launch_obs(l->prec, l->g, l->U, l->F, 1, l->partials, q_site, l->st); }));
@@ -854,7 +861,7 @@ FusedPlan plan_fused(const cl_batch* b) {
   auto x4 = [&](int V) { return 4 * tiles(V); };
   auto x6 = [&](int V) { return 6 * tiles(V); };
   auto red = [](int V) { return reduce_blocks(V); };
-  add(ENS_INVERSE, all, x4);
+  add(ENS_INVERSE, [&](int i) { return needs_inverse_pass(b->lats[i]); }, x4);
   add(ENS_PLAQ, all, x6);
   add(ENS_CLOVER, th, x6);
   add(ENS_FORCE_WILSON, [&](int i) { return !th(i); }, x6);

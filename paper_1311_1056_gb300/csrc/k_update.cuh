@@ -116,6 +116,27 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_link_inverse(Geo g, const ty
   k_link_inverse_body<T>(g, U, Ui, blockIdx.x);
 }
 
+// The inverse of link (mu, site) as the plaquette, clover and force kernels
+// use it.  FP64: loaded from the U^{-1} field the link-inverse pass wrote
+// (forming it costs 126 flops on the FP64 pipe these kernels are bound by).
+// FP32 storage: formed from the link (the same adjugate, so the same bits,
+// on the FP32 pipe, which these memory- and latency-bound kernels leave
+// idle); no link-inverse pass runs and the load usually hits a line of U the
+// kernel reads anyway.
+template <typename T>
+__host__ __device__ constexpr bool inverse_on_the_fly() { return sizeof(T) == 4; }
+template <typename T>
+__device__ __forceinline__ void load_inv(mat<T>& ui, const typename vec2_of<T>::type* __restrict__ U,
+                                         const typename vec2_of<T>::type* __restrict__ Ui, int mu, int site, int V) {
+  if constexpr (inverse_on_the_fly<T>()) {
+    mat<T> u;
+    load(u, U, mu, site, V);
+    adj(ui, u);
+  } else {
+    load(ui, Ui, mu, site, V);
+  }
+}
+
 // ------------------------------------------------------------- plaquettes
 // P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^{-1} U_nu(x)^{-1} and
 // D = P - P^{-1}, six planes per site.
@@ -134,8 +155,8 @@ __device__ __forceinline__ void k_plaq_body(Geo g, const typename vec2_of<T>::ty
   load(a, U, mu, s, g.V);
   load(b, U, nu, hop(g, s, x, mu, 1), g.V);
   mul(A, a, b);
-  load(a, Ui, mu, hop(g, s, x, nu, 1), g.V);
-  load(b, Ui, nu, s, g.V);
+  load_inv(a, U, Ui, mu, hop(g, s, x, nu, 1), g.V);
+  load_inv(b, U, Ui, nu, s, g.V);
   mul(B, a, b);
   mul(P, A, B);
   store(Pq, p, s, g.V, P);
@@ -176,19 +197,19 @@ __device__ __forceinline__ void k_clover_rot_body(Geo g, const typename vec2_of<
   mat<T>&acc = ws[0], &w = ws[1], &d = ws[2], &t = ws[3];
   load(acc, Dq, p, s, g.V);
   // L2 = U_mu(x-mu)^{-1} D(x-mu) U_mu(x-mu)
-  load(w, Ui, mu, xmm, g.V);
+  load_inv(w, U, Ui, mu, xmm, g.V);
   load(d, Dq, p, xmm, g.V);
   mul(t, w, d);
   load(w, U, mu, xmm, g.V);
   mul_acc<+1>(acc, t, w);
   // L3 + L4 = U_nu(x-nu)^{-1} [D(x-nu) + U_mu(x-mu-nu)^{-1} D(x-mu-nu) U_mu(x-mu-nu)] U_nu(x-nu)
-  load(w, Ui, mu, xmm_mn, g.V);
+  load_inv(w, U, Ui, mu, xmm_mn, g.V);
   load(d, Dq, p, xmm_mn, g.V);
   mul(t, w, d);
   load(w, U, mu, xmm_mn, g.V);
   load(d, Dq, p, xmn, g.V);
   mul_acc<+1>(d, t, w);
-  load(w, Ui, nu, xmn, g.V);
+  load_inv(w, U, Ui, nu, xmn, g.V);
   mul(t, w, d);
   load(w, U, nu, xmn, g.V);
   mul_acc<+1>(acc, t, w);
@@ -227,14 +248,14 @@ __device__ __forceinline__ void k_plaq_force_wilson_body(Geo g, const typename v
   load(D, Dq, p, s, g.V);
   scaled(M, -beta6, D);
   store(C, 4 * p + 0, s, g.V, M);
-  load(a, Ui, mu, s, g.V);
+  load_inv(a, U, Ui, mu, s, g.V);
   mul(t, a, M);
   load(a, U, mu, s, g.V);
   mul(M, t, a);
   store(C, 4 * p + 2, s, g.V, M);
   scaled(M, beta6, D);
   store(C, 4 * p + 1, s, g.V, M);
-  load(a, Ui, nu, s, g.V);
+  load_inv(a, U, Ui, nu, s, g.V);
   mul(t, a, M);
   load(a, U, nu, s, g.V);
   mul(M, t, a);
@@ -271,7 +292,7 @@ __device__ __forceinline__ void force_stage_a(mat<T>& Gh, const Geo& g, int s, c
   load_signed(t, F, pc, c1, g.V, m);
   load(q, U, mu, s, g.V);
   mul(D, q, t);  // a G1 (D is re-read below)
-  load(q, Ui, mu, s, g.V);
+  load_inv(q, U, Ui, mu, s, g.V);
   mul(t, D, q);  // G1^
 #pragma unroll
   for (int k = 0; k < 9; ++k) Gh.e[k] = cadd(Gh.e[k], t.e[k]);
@@ -284,8 +305,8 @@ __device__ __forceinline__ void force_stage_a(mat<T>& Gh, const Geo& g, int s, c
   mul(D, M, q);  // ab
   load_signed(q, F, pc, hop(g, c1, x, nu, 1), g.V, m);
   mul(t, D, q);  // ab G2
-  load(M, Ui, mu, s, g.V);
-  load(q, Ui, nu, c1, g.V);
+  load_inv(M, U, Ui, mu, s, g.V);
+  load_inv(q, U, Ui, nu, c1, g.V);
   mul(D, q, M);  // (ab)^{-1}
   mul_acc<+1>(Gh, t, D);
 }
@@ -308,7 +329,7 @@ __device__ __forceinline__ void force_stage_b(mat<T>& Gh, const Geo& g, int s, c
   load_signed(q, F, pc, c3, g.V, m);
   load(M, U, nu, s, g.V);
   mul(t, M, q);
-  load(M, Ui, nu, s, g.V);
+  load_inv(M, U, Ui, nu, s, g.V);
   mul(q, t, M);
   load(D, Dq, p, s, g.V);
   scaled(M, beta6, D);
@@ -343,7 +364,7 @@ __device__ __forceinline__ void force_stage_b(mat<T>& Gh, const Geo& g, int s, c
   load_rw(M, C, 4 * p + 2, s, g.V);
 #pragma unroll
   for (int k = 0; k < 9; ++k) M.e[k] = cadd(M.e[k], K.e[k]);
-  load(Gh, Ui, mu, s, g.V);
+  load_inv(Gh, U, Ui, mu, s, g.V);
   mul(t, Gh, M);
   load(Gh, U, mu, s, g.V);
   mul(M, t, Gh);
@@ -352,7 +373,7 @@ __device__ __forceinline__ void force_stage_b(mat<T>& Gh, const Geo& g, int s, c
   load_rw(M, C, 4 * p + 3, s, g.V);
 #pragma unroll
   for (int k = 0; k < 9; ++k) M.e[k] = csub(M.e[k], K.e[k]);
-  load(Gh, Ui, nu, s, g.V);
+  load_inv(Gh, U, Ui, nu, s, g.V);
   mul(t, Gh, M);
   load(Gh, U, nu, s, g.V);
   mul(M, t, Gh);
