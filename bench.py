@@ -54,9 +54,17 @@ CPU_SAMPLE_L = (8, 8, 8, 8)
 MUL, MULACC, ADJ, HERM = 198, 216, 126, 162
 
 
+# FP64 flops per unit that the FP32-storage form's FP64 work executes
+# (2 x DFMA + DMUL + DADD thread instructions from ncu, 24^4, divided by the
+# links or sites; profiles/ncu_fp32_update_cooling_24x4.md).  Its series stop
+# at the FP32-storage tolerance, whose term count follows each argument's
+# norm, so the analytic model above does not apply to them.
+FP32_STORAGE_FP64_FLOPS = {"update": 4 * 663, "cool_omega": 163, "cool_grad_omega": 160}
+
+
 def flop_model(prec, theta_on=True, n_taylor=15):
     expm = MUL + 6 + 72 + 36 + 16 * n_taylor + 9 * (6 + 8) + 6  # Cayley-Hamilton + Horner
-    det_root = 64 + 35                                           # det + cube-root series
+    det_root = 64 + 19                                           # det + three-term cube-root series
     if theta_on:
         force = 6 * (13 * MUL + 9 * MULACC + 162)                # per-plaquette drift, 6 planes
     else:
@@ -73,10 +81,10 @@ def flop_model(prec, theta_on=True, n_taylor=15):
         m["update"] = 4 * (12 * 18 + 32 + 38 + expm + MUL + det_root + 54)
         pipe = {k: "fp64" for k in m}
     else:
-        m["update"] = 4 * (expm - 36 + det_root)                 # FP64 part only
         pipe = {k: "fp32" for k in m}
-        pipe["update"] = pipe["cool_omega"] = pipe["cool_grad_omega"] = "fp64"
-        m["cool_grad_omega"] = 209  # FP64 part only (the gradient is FP32 there)
+        for k, v in FP32_STORAGE_FP64_FLOPS.items():  # FP64 part only
+            m[k] = v
+            pipe[k] = "fp64"
     return m, pipe
 
 
