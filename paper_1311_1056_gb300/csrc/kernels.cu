@@ -457,7 +457,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_cool_grad(Geo g, const typename
 
 // Single-pass sweep of the D_0 / D_1 rules, part 1: the strength alpha_ad of
 // these rules needs only the unitarity norm, which the previous sweep's apply
-// (k_cool_apply_un) summed, so the rule has decided before this kernel runs
+// (k_cool_apply_tiles) summed, so the rule has decided before this kernel runs
 // and the gradient never leaves the thread: f_ax at x, then Omega_x =
 // exp(-eps alpha_ad f_ax lambda_a) and its inverse (FP64), stored packed.
 template <typename T>
