@@ -299,16 +299,15 @@ __device__ __forceinline__ void force_stage_a(mat<T>& Gh, const Geo& g, int s, c
   load(D, Dq, p, s, g.V);
   commutator_acc(M, D, t);
   store(C, 4 * p + 2, s, g.V, M);
-  // corner c2: G2^ = (ab) G2 (ab)^{-1}
+  // corner c2: G2^ = (ab) G2 (ab)^{-1}, with (ab)^{-1} = adj(ab) = adj(b) adj(a)
+  // (the inverses used everywhere are adjugates: det U = 1 by the re-projection)
   load(M, U, mu, s, g.V);
   load(q, U, nu, c1, g.V);
   mul(D, M, q);  // ab
   load_signed(q, F, pc, hop(g, c1, x, nu, 1), g.V, m);
   mul(t, D, q);  // ab G2
-  load_inv(M, U, Ui, mu, s, g.V);
-  load_inv(q, U, Ui, nu, c1, g.V);
-  mul(D, q, M);  // (ab)^{-1}
-  mul_acc<+1>(Gh, t, D);
+  adj(M, D);     // (ab)^{-1}
+  mul_acc<+1>(Gh, t, M);
 }
 
 // Corner c3, K, and the four slots completed; Gh holds the stage-a sum.
