@@ -66,7 +66,7 @@ def flop_model(prec, theta_on=True, n_taylor=15):
     expm = MUL + 6 + 72 + 36 + 16 * n_taylor + 9 * (6 + 8) + 6  # Cayley-Hamilton + Horner
     det_root = 64 + 19                                           # det + three-term cube-root series
     if theta_on:
-        force = 6 * (13 * MUL + 9 * MULACC + 162)                # per-plaquette drift, 6 planes
+        force = 6 * (12 * MUL + ADJ + 9 * MULACC + 162)          # per-plaquette drift, 6 planes
     else:
         force = 6 * (4 * MUL + 36)
     m = {
