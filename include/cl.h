@@ -388,8 +388,12 @@ cl_status cl_server_run_trace(cl_server* srv, int n, const cl_request* reqs, con
 void cl_server_free(cl_server* srv);
 
 /* Links as host AoS doubles (layout above), any precision (FP32 links are
- * widened).  host_aos holds V*4*18 doubles; pinned memory copies fastest.
- * Synchronises.  Errors: CL_ERR_INVALID (NULL), CL_ERR_OOM (staging), CL_ERR_CUDA. */
+ * widened).  host_aos holds V*4*18 doubles.  Page-locked host memory that the
+ * device can address (cudaHostAlloc, cudaHostRegister, a framework's pinned
+ * tensor) is read or written in place by the layout kernel over the host
+ * link; pageable memory goes through a device staging buffer (allocated on
+ * first use).  Synchronises.  Errors: CL_ERR_INVALID (NULL), CL_ERR_OOM
+ * (staging), CL_ERR_CUDA. */
 cl_status cl_get_links(cl_lattice* lat, double* host_aos);
 /* Replace the links from host AoS doubles (FP32 storage rounds them).
  * Enqueue only, but host_aos may be reused on return (the copy completes first). */

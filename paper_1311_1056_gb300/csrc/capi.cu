@@ -544,8 +544,28 @@ cl_status cl_set_links_device(cl_lattice* l, const double* dev_aos) {
   return CL_OK;
 }
 
+// The device's view of page-locked host memory (cudaHostAlloc, a registered
+// range, a framework's pinned tensor), else NULL (pageable memory).  The
+// layout kernels then read or write the host array directly over the
+// host link, one pass instead of a copy through the staging buffer plus a
+// pass over it.
+static void* device_view(const void* host) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, host) != cudaSuccess) {
+    cudaGetLastError();  // not a pointer CUDA knows: clear the error, take the copy path
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 cl_status cl_get_links(cl_lattice* l, double* host_aos) {
   if (!l || !host_aos) return fail(CL_ERR_INVALID, "NULL argument");
+  if (double* dv = (double*)device_view(host_aos)) {
+    cl_status s = cl_get_links_device(l, dv);
+    if (s != CL_OK) return s;
+    CK(cudaStreamSynchronize(l->st));
+    return CL_OK;
+  }
   cl_status s = ensure_stage(l);
   if (s != CL_OK) return s;
   s = cl_get_links_device(l, l->stage);
@@ -558,6 +578,13 @@ cl_status cl_get_links(cl_lattice* l, double* host_aos) {
 
 cl_status cl_set_links(cl_lattice* l, const double* host_aos) {
   if (!l || !host_aos) return fail(CL_ERR_INVALID, "NULL argument");
+  if (const double* dv = (const double*)device_view(host_aos)) {
+    cl_status s = cl_set_links_device(l, dv);
+    if (s != CL_OK) return s;
+    // the host buffer may be reused on return: wait for the pass that reads it
+    CK(cudaStreamSynchronize(l->st));
+    return CL_OK;
+  }
   cl_status s = ensure_stage(l);
   if (s != CL_OK) return s;
   CK(cudaMemcpyAsync(l->stage, host_aos, sizeof(double) * 18 * 4 * (size_t)l->g.V,

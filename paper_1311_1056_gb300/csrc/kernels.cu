@@ -248,30 +248,58 @@ __global__ void k_noise_sample(int site0, int n, uint64_t seed, uint32_t step, u
 }
 
 // ------------------------------------------------------------ conversion
-// AoS [site][plane][row][col]{re,im} doubles <-> SoA planes of T2.
+// AoS [site][plane][row][col]{re,im} doubles <-> SoA planes of T2, through a
+// shared-memory transpose of CONV_SITES sites: the AoS side (often the host's
+// page-locked memory, read or written over the host link) is one contiguous
+// run per block, and the SoA side is CONV_SITES consecutive sites per row.
+// The tile's pitch is odd in 16-byte units, so the column-wise accesses of a
+// quarter warp hit distinct banks.
+const int CONV_SITES = 32, CONV_MAX_ROWS = 54;  // up to 6 planes
+__host__ __device__ constexpr int conv_pitch(int rows) { return rows + 1 + (rows & 1); }
+
 template <typename T>
-__global__ void k_aos_to_soa(Geo g, const double* __restrict__ aos, typename vec2_of<T>::type* U,
-                             int nplanes) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;  // complex element index
-  size_t n = (size_t)g.V * nplanes * 9;
-  if (idx >= n) return;
-  int s = (int)(idx / (9 * nplanes));
-  int r = (int)(idx - (size_t)s * 9 * nplanes);
-  int p = r / 9, k = r - 9 * p;
-  U[((size_t)p * 9 + k) * g.V + s] = pack(cx<T>{(T)aos[2 * idx], (T)aos[2 * idx + 1]});
+__global__ void __launch_bounds__(256) k_aos_to_soa(Geo g, const double* __restrict__ aos,
+                                                    typename vec2_of<T>::type* U, int nplanes) {
+  __shared__ double2 buf[CONV_SITES * conv_pitch(CONV_MAX_ROWS)];
+  const int R = 9 * nplanes, pitch = conv_pitch(R);
+  const int s0 = blockIdx.x * CONV_SITES;
+  const int ns = min(CONV_SITES, g.V - s0);
+  const double* src = aos + 2 * (size_t)s0 * R;
+  for (int e = threadIdx.x; e < ns * R; e += blockDim.x) {
+    const int j = e / R, r = e - j * R;
+    buf[j * pitch + r] = make_double2(src[2 * e], src[2 * e + 1]);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < R * CONV_SITES; e += blockDim.x) {
+    const int r = e / CONV_SITES, j = e - r * CONV_SITES;
+    if (j < ns) {
+      const double2 v = buf[j * pitch + r];
+      U[(size_t)r * g.V + s0 + j] = pack(cx<T>{(T)v.x, (T)v.y});
+    }
+  }
 }
 template <typename T>
-__global__ void k_soa_to_aos(Geo g, const typename vec2_of<T>::type* __restrict__ U,
-                             double* aos, int nplanes) {
-  size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  size_t n = (size_t)g.V * nplanes * 9;
-  if (idx >= n) return;
-  int s = (int)(idx / (9 * nplanes));
-  int r = (int)(idx - (size_t)s * 9 * nplanes);
-  int p = r / 9, k = r - 9 * p;
-  const cx<T> c = unpack(U[((size_t)p * 9 + k) * g.V + s]);
-  aos[2 * idx] = (double)c.re;
-  aos[2 * idx + 1] = (double)c.im;
+__global__ void __launch_bounds__(256) k_soa_to_aos(Geo g, const typename vec2_of<T>::type* __restrict__ U,
+                                                    double* aos, int nplanes) {
+  __shared__ double2 buf[CONV_SITES * conv_pitch(CONV_MAX_ROWS)];
+  const int R = 9 * nplanes, pitch = conv_pitch(R);
+  const int s0 = blockIdx.x * CONV_SITES;
+  const int ns = min(CONV_SITES, g.V - s0);
+  for (int e = threadIdx.x; e < R * CONV_SITES; e += blockDim.x) {
+    const int r = e / CONV_SITES, j = e - r * CONV_SITES;
+    if (j < ns) {
+      const cx<T> c = unpack(U[(size_t)r * g.V + s0 + j]);
+      buf[j * pitch + r] = make_double2((double)c.re, (double)c.im);
+    }
+  }
+  __syncthreads();
+  double* dst = aos + 2 * (size_t)s0 * R;
+  for (int e = threadIdx.x; e < ns * R; e += blockDim.x) {
+    const int j = e / R, r = e - j * R;
+    const double2 v = buf[j * pitch + r];
+    dst[2 * e] = v.x;
+    dst[2 * e + 1] = v.y;
+  }
 }
 
 // --------------------------------------------------------------- cooling
@@ -1095,8 +1123,8 @@ cudaError_t launch_gauge_omega(int prec, const GeoH& h, void* Om, void* Omi, uin
 cudaError_t launch_aos_to_soa(int prec, const GeoH& h, const double* aos, void* U, int nplanes,
                               cudaStream_t st) {
   Geo g = to_geo(h);
-  size_t n = (size_t)g.V * nplanes * 9;
-  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (nplanes < 1 || 9 * nplanes > CONV_MAX_ROWS) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)((g.V + CONV_SITES - 1) / CONV_SITES);
   return by_prec(prec, [&](auto t) {
     using T = decltype(t);
     k_aos_to_soa<T><<<blocks, 256, 0, st>>>(g, aos, (typename vec2_of<T>::type*)U, nplanes);
@@ -1106,8 +1134,8 @@ cudaError_t launch_aos_to_soa(int prec, const GeoH& h, const double* aos, void* 
 cudaError_t launch_soa_to_aos(int prec, const GeoH& h, const void* U, double* aos, int nplanes,
                               cudaStream_t st) {
   Geo g = to_geo(h);
-  size_t n = (size_t)g.V * nplanes * 9;
-  unsigned blocks = (unsigned)((n + 255) / 256);
+  if (nplanes < 1 || 9 * nplanes > CONV_MAX_ROWS) return cudaErrorInvalidValue;
+  const unsigned blocks = (unsigned)((g.V + CONV_SITES - 1) / CONV_SITES);
   return by_prec(prec, [&](auto t) {
     using T = decltype(t);
     k_soa_to_aos<T><<<blocks, 256, 0, st>>>(g, (const typename vec2_of<T>::type*)U, aos, nplanes);

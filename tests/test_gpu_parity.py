@@ -67,6 +67,31 @@ def test_links_roundtrip_and_step_counter():
         assert lat.step_count == 2
 
 
+@pytest.mark.parametrize("prec", [cl.CL_FP64, cl.CL_FP32_STORAGE])
+def test_links_roundtrip_through_pinned_host_memory(prec):
+    """Page-locked host arrays are read and written in place by the layout
+    kernels; pageable ones go through the staging buffer.  Both paths give
+    the same links."""
+    import torch
+    L = (6, 4, 5, 3)
+    V = 6 * 4 * 5 * 3
+    U = LI.sl3c_lattice(L, seed=4, spread=0.3)
+    with cl.Lattice(L, prec=prec) as lat:
+        pin = torch.empty(V * 4 * 18, dtype=torch.float64, pin_memory=True)
+        a_pin = pin.numpy().view(np.complex128).reshape(V, 4, 3, 3)
+        a_pin[...] = U
+        cl.cl_set_links(lat.h, a_pin)           # in place from pinned memory
+        via_pin = lat.links()                   # out through the staging buffer
+        lat.set_links(U)                        # in through the staging buffer
+        via_stage = lat.links()
+        np.testing.assert_array_equal(via_pin, via_stage)
+        a_pin[...] = 0
+        cl.cl_get_links(lat.h, V, a_pin)        # out in place to pinned memory
+        np.testing.assert_array_equal(a_pin, via_stage)
+        if prec == cl.CL_FP64:
+            np.testing.assert_array_equal(via_stage, U)
+
+
 # --------------------------------------------------------- drift and q_L
 @pytest.mark.parametrize("L", SHAPES)
 @pytest.mark.parametrize("beta,theta", [(5.8, 0.0), (0.0, 1.1 + 0.3j), (6.0, 2.0), (5.5, 0.7j)])
