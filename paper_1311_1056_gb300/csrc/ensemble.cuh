@@ -122,7 +122,7 @@ cudaError_t launch_ens_step_family(int fam, const ChainDesc* cd, const WorkItem*
     case ENS_CLOVER: k_ens_clover<T><<<n, ENS_BLOCK, 0, st>>>(cd, w); break;
     case ENS_FORCE_WILSON: k_ens_force_wilson<T><<<n, ENS_BLOCK, 0, st>>>(cd, w); break;
     case ENS_FORCE_THETA:
-      if (sizeof(T) == 8) {
+      if constexpr (sizeof(T) == 8) {  // FP64: the split form (only it is instantiated)
         k_ens_force_a<T><<<n, ENS_BLOCK, 0, st>>>(cd, w);
         k_ens_force_b<T><<<n, ENS_BLOCK, 0, st>>>(cd, w);
       } else {
