@@ -666,7 +666,7 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_cool_apply(Geo g, typename v
 // sum independent of the launch shape: a fused batch, which runs the tiles of
 // many chains in one launch, gives each chain the records of its lone run.
 // Resident blocks of COOL_TILE threads the tile kernels are built for: 72
-// registers a thread with FP32 links, 128 with FP64 ones (no spills).
+// registers a thread with FP32 links, 128 with FP64 ones (a few bytes of spills).
 #define COOL_TILE_MIN_BLOCKS(T) (sizeof(T) == 4 ? 7 : 4)
 __device__ __forceinline__ int layer_sites(const Geo& g) { return g.V / g.L[3]; }
 __device__ __forceinline__ int tiles_per_layer(const Geo& g) { return (layer_sites(g) + COOL_TILE - 1) / COOL_TILE; }
