@@ -104,7 +104,8 @@ def measured_peaks():
 
 # The sources of the kernels the bench launches (their launch shapes included);
 # the host runtime, the server and the chain kernel do not change them.
-KERNEL_SOURCES = ("df64.cuh", "expm.cuh", "k_update.cuh", "k_update_df64.cu", "k_update_f32.cu", "k_update_f64.cu",
+KERNEL_SOURCES = ("bm_tables.cuh", "df64.cuh", "expm.cuh", "k_update.cuh", "k_update_df64.cu", "k_update_f32.cu",
+                  "k_update_f64.cu",
                   "kernels.cu", "launch.h",
                   "lattice.cuh", "philox.cuh", "su3.cuh")
 

@@ -447,6 +447,15 @@ cl_status cl_noise_sample(cl_precision prec, uint64_t seed, uint32_t step, int m
  * buffer, synchronises.  Errors: CL_ERR_INVALID (NULL, n < 0), CL_ERR_OOM,
  * CL_ERR_CUDA. */
 cl_status cl_selftest_convert(uint64_t seed, int64_t n, int64_t* bad_f2d, int64_t* bad_d2f);
+/* Self-test of the FP64 noise's transcendentals: the table-driven ln and
+ * sincospi that the FP64 Box-Muller uses for its uniforms (k + 1/2) 2^-52
+ * (Sec. 2 noise), against CUDA's log and sincospi on n generated uniforms
+ * (the whole range, the deep tail of ln, values next to 1 and next to the
+ * sine table's grid).  Returns the largest distances in units in the last
+ * place, rounded up.  A diagnostic with no counterpart in the paper: current
+ * device, legacy default stream, its own 16-byte device buffer, synchronises.
+ * Errors: CL_ERR_INVALID (NULL, n < 0), CL_ERR_OOM, CL_ERR_CUDA. */
+cl_status cl_selftest_box_muller(uint64_t seed, int64_t n, int64_t* ulp_ln, int64_t* ulp_sincos);
 /* Topological charge density q_L(x) (Sec. 5), host doubles [site]{re,im} (2*V). */
 cl_status cl_qdensity(cl_lattice* lat, double* host_q);
 

@@ -125,6 +125,8 @@ SIGNATURES = {
                                        ctypes.c_int, ctypes.c_int, _dp]),
     "cl_selftest_convert": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
                                            ctypes.POINTER(ctypes.c_int64)]),
+    "cl_selftest_box_muller": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64),
+                                              ctypes.POINTER(ctypes.c_int64)]),
     "cl_wait": (ctypes.c_int, [_P, ctypes.c_double]),
     "cl_batch_wait": (ctypes.c_int, [_P, ctypes.c_double]),
     "cl_batch_set_fused": (ctypes.c_int, [_P, ctypes.c_int]),
@@ -512,6 +514,14 @@ def noise_sample(prec, seed, step, mu, site0, nsites):
 def cl_selftest_convert(seed, n):
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(load().cl_selftest_convert(seed, n, ctypes.byref(a), ctypes.byref(b)), "cl_selftest_convert")
+    return a.value, b.value
+
+
+def cl_selftest_box_muller(seed, n):
+    """(ulp_ln, ulp_sincos): largest distances of the FP64 noise's ln and
+    sincospi from CUDA's log and sincospi over n generated uniforms."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().cl_selftest_box_muller(seed, n, ctypes.byref(a), ctypes.byref(b)), "cl_selftest_box_muller")
     return a.value, b.value
 
 

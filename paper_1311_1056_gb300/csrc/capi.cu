@@ -700,6 +700,23 @@ cl_status cl_selftest_convert(uint64_t seed, int64_t n, int64_t* bad_f2d, int64_
   return CL_OK;
 }
 
+cl_status cl_selftest_box_muller(uint64_t seed, int64_t n, int64_t* ulp_ln, int64_t* ulp_sincos) {
+  if (!ulp_ln || !ulp_sincos || n < 0) return fail(CL_ERR_INVALID, "NULL argument or n < 0");
+  unsigned long long* d = nullptr;
+  cudaError_t e = cudaMalloc(&d, 2 * sizeof(unsigned long long));
+  if (e != cudaSuccess)
+    return fail(e == cudaErrorMemoryAllocation ? CL_ERR_OOM : CL_ERR_CUDA, cudaGetErrorString(e));
+  unsigned long long h[2] = {0, 0};
+  e = cudaMemset(d, 0, sizeof(h));
+  if (e == cudaSuccess) e = launch_selftest_box_muller(seed, (long long)n, d, 0);
+  if (e == cudaSuccess) e = cudaMemcpy(h, d, sizeof(h), cudaMemcpyDeviceToHost);
+  cudaFree(d);
+  if (e != cudaSuccess) return fail(CL_ERR_CUDA, cudaGetErrorString(e));
+  *ulp_ln = (int64_t)h[0];
+  *ulp_sincos = (int64_t)h[1];
+  return CL_OK;
+}
+
 cl_status cl_qdensity(cl_lattice* l, double* host_q) {
   if (!l || !host_q) return fail(CL_ERR_INVALID, "NULL argument");
   if (!l->qsite) CK(cudaMalloc(&l->qsite, sizeof(double) * 2 * (size_t)l->g.V));

@@ -951,6 +951,37 @@ __global__ void k_selftest_convert(uint64_t seed, long long n, unsigned long lon
   if (b1) atomicAdd(bad + 1, b1);
 }
 
+// Distance in units in the last place of b (at least the spacing of the
+// smallest normal, so exact zeros compare by absolute error).
+__device__ __forceinline__ double ulps(double a, double b) {
+  const double fb = fabs(b);
+  const double up = __longlong_as_double(__double_as_longlong(fb) + 1);  // the next double above |b|
+  const double u = fmax(up - fb, 2.2250738585072014e-308);
+  return fabs(a - b) / u;
+}
+// The table-driven ln and sincospi of the FP64 Box-Muller (philox.cuh)
+// against CUDA's log and sincospi on n uniforms (k + 1/2) 2^-52: k over its
+// whole range, its smallest values, and values next to 2^52; the largest
+// distances in ulp (rounded up) into worst[0] (ln) and worst[1] (sin, cos).
+__global__ void k_selftest_box_muller(uint64_t seed, long long n, unsigned long long* worst) {
+  double w0 = 0.0, w1 = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const uint64_t r = splitmix64(seed + (uint64_t)i);
+    uint64_t k = r >> 12;                                        // 52 bits
+    if ((i & 15) == 1) k >>= (r & 63) % 52;                      // small k: deep tail of ln
+    if ((i & 15) == 2) k = ((1ull << 52) - 1) - (k >> 30);       // u next to 1
+    if ((i & 15) == 3) k = (k >> 45) << 45 | ((r & 1) ? 0 : (1ull << 45) - 1);  // next to the sin grid
+    const double u = u52_bits(k);
+    w0 = fmax(w0, ulps(ln_unit(u), log(u)));
+    double s, c, s0, c0;
+    sincospi_2u52(k, &s, &c);
+    sincospi(2.0 * u, &s0, &c0);
+    w1 = fmax(w1, fmax(ulps(s, s0), ulps(c, c0)));
+  }
+  atomicMax(worst, (unsigned long long)ceil(w0));
+  atomicMax(worst + 1, (unsigned long long)ceil(w1));
+}
+
 }  // namespace
 
 // ------------------------------------------------------------ fused batch
@@ -1076,6 +1107,11 @@ cudaError_t launch_ens_cool_adapt_tiles(const ChainDesc* cd, const int* chains, 
 
 cudaError_t launch_selftest_convert(uint64_t seed, long long n, unsigned long long* bad, cudaStream_t st) {
   k_selftest_convert<<<RED_MAX_BLOCKS, RED_THREADS, 0, st>>>(seed, n, bad);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_selftest_box_muller(uint64_t seed, long long n, unsigned long long* worst, cudaStream_t st) {
+  k_selftest_box_muller<<<RED_MAX_BLOCKS, RED_THREADS, 0, st>>>(seed, n, worst);
   return cudaGetLastError();
 }
 

@@ -185,5 +185,9 @@ cudaError_t launch_ens_cool_adapt_tiles(const ChainDesc* cd, const int* chains, 
 // ones on n generated cases; mismatch counts added into bad[0] (float ->
 // double) and bad[1] (double -> float).
 cudaError_t launch_selftest_convert(uint64_t seed, long long n, unsigned long long* bad, cudaStream_t st);
+// The FP64 Box-Muller's table-driven ln and sincospi against CUDA's log and
+// sincospi on n generated uniforms; the largest distances in ulp (rounded
+// up) into worst[0] (ln) and worst[1] (sin, cos).
+cudaError_t launch_selftest_box_muller(uint64_t seed, long long n, unsigned long long* worst, cudaStream_t st);
 
 }  // namespace clgc
