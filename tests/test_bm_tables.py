@@ -40,8 +40,12 @@ def test_table_values_match_their_definitions():
     sc = _pairs(src, "BM_SC_TAB")
     assert len(sc) == 129
     for j, (s, c) in enumerate(sc):
-        # the reference rounds pi j / 64 first, an error of up to ~3e-16 in the angle
-        assert abs(s - math.sin(math.pi * j / 64)) < 5e-16 and abs(c - math.cos(math.pi * j / 64)) < 5e-16
+        # reference on the first quadrant (the rounded angle pi m / 64 <= pi / 2
+        # is off by at most 2e-16), carried to quadrant q by the symmetries
+        q, m = divmod(j, 32)
+        s1, c1 = math.sin(math.pi * m / 64), math.cos(math.pi * m / 64)
+        rs, rc = [(s1, c1), (c1, -s1), (-s1, -c1), (-c1, s1), (s1, c1)][q]
+        assert abs(s - rs) < 3e-16 and abs(c - rc) < 3e-16, (j, s, rs, c, rc)
         if j % 32 == 0:  # exact zeros and ones at multiples of pi/2
             assert {abs(s), abs(c)} == {0.0, 1.0}
     consts = {k: float.fromhex(v) for k, v in re.findall(r"const double (BM_\w+) = (\S+);", src)}
