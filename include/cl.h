@@ -112,11 +112,12 @@ typedef struct {
 /* Create a lattice on the current CUDA device and initialise its links
  * (start, then the optional random gauge transformation).  cuda_stream is a
  * cudaStream_t (may be NULL).  On success *out owns the device memory
- * (per site: 54 complex 3x3 matrices -- links, a second link buffer,
- * inverses, plaquettes, their differences, the clover field and the 24 drift
- * contributions, whose planes also hold the theta force's parked partial
- * sums and, outside the CL step, the cooling fields: 7,776 bytes in FP64 and
- * DF64, 3,888 in FP32; cl_lattice_bytes gives the exact figure).
+ * (per site: 54 complex 3x3 matrices in FP64 and DF64 -- links, a second
+ * link buffer, inverses, plaquettes, their differences, the clover field and
+ * the 24 drift contributions, whose planes also hold the theta force's
+ * parked partial sums and, outside the CL step, the cooling fields: 7,776
+ * bytes; 50 in FP32 storage, which forms the inverses where it uses them:
+ * 3,600 bytes; cl_lattice_bytes gives the exact figure).
  * Errors: CL_ERR_INVALID (NULL, extents < 1, V*6*9 beyond int range),
  * CL_ERR_OOM, CL_ERR_CUDA. */
 cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice** out);

@@ -145,14 +145,15 @@ cl_status do_steps(cl_lattice* l, double eps, int n) {
     CK(do_force(l, th, sre, sim));
     const bool adaptive = l->k_ref > 0.0;
     if (adaptive) {
-      // drift into the (now free) link-inverse buffer with max |K|, then the
-      // step size on the device, then the update from the stored drift
+      // drift into the plaquette buffer (dead once the force has run) with
+      // max |K|, then the step size on the device, then the update from the
+      // stored drift
       CK(timed(l, CL_PHASE_UPDATE, [&] {
-        return launch_update_gather(l->prec, 2, l->g, l->U, l->C, l->Ui, eps, l->p.seed, l->sd, false, l->st);
+        return launch_update_gather(l->prec, 2, l->g, l->U, l->C, l->Pq, eps, l->p.seed, l->sd, false, l->st);
       }));
       CK(timed(l, CL_PHASE_UPDATE, [&] { return launch_step_eps(l->sd, eps, l->k_ref, l->st); }));
       CK(timed(l, CL_PHASE_UPDATE, [&] {
-        return launch_update_gather(l->prec, 3, l->g, l->U, l->Ui, l->Un, eps, l->p.seed, l->sd, true, l->st);
+        return launch_update_gather(l->prec, 3, l->g, l->U, l->Pq, l->Un, eps, l->p.seed, l->sd, true, l->st);
       }));
     } else {
       CK(timed(l, CL_PHASE_UPDATE, [&] {
@@ -288,7 +289,8 @@ namespace clrt {
 size_t lattice_bytes(int V, int prec) {
   const size_t Vs = (size_t)V, esz = prec == 1 ? 8 : 16, real = prec == 1 ? 4 : 8;
   (void)real;  // the cooling fields and the parked force partials live inside C (see cl_init_lattice)
-  return esz * 9 * Vs * (4 + 4 + 4 + 6 + 6 + 24 + 6) + sizeof(double) * NQ_OBS * (size_t)reduce_blocks(V) +
+  const size_t inverses = prec == 1 ? 0 : 4;  // the FP32-storage form keeps no inverse field
+  return esz * 9 * Vs * (4 + 4 + inverses + 6 + 6 + 24 + 6) + sizeof(double) * NQ_OBS * (size_t)reduce_blocks(V) +
          sizeof(CoolState) + sizeof(ObsOut) + sizeof(uint32_t);
 }
 
@@ -349,7 +351,7 @@ cl_status cl_init_lattice(const cl_params* params, void* cuda_stream, cl_lattice
   const size_t Vs = (size_t)V;
   alloc(&l->U, l->esz * 4 * 9 * Vs);
   alloc(&l->Un, l->esz * 4 * 9 * Vs);
-  alloc(&l->Ui, l->esz * 4 * 9 * Vs);
+  if (needs_inverse_pass(l)) alloc(&l->Ui, l->esz * 4 * 9 * Vs);  // FP32 storage forms inverses in place
   alloc(&l->Pq, l->esz * 6 * 9 * Vs);
   alloc(&l->Dq, l->esz * 6 * 9 * Vs);
   alloc(&l->C, l->esz * 24 * 9 * Vs);

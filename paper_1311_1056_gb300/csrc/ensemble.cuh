@@ -90,8 +90,9 @@ __global__ void __maxnreg__(FORCE_AB_MAXNREG) k_ens_force_ab(const ChainDesc* __
 }
 
 // The update modes as the runtime runs them: MODE_UPDATE reads C and writes
-// Un at the fixed step size; MODE_DRIFTMAX writes the drift into Ui;
-// MODE_UPDATE_X reads it back from Ui and writes Un at the device step size.
+// Un at the fixed step size; MODE_DRIFTMAX writes the drift into Pq (dead
+// after the force); MODE_UPDATE_X reads it back and writes Un at the device
+// step size.
 template <typename T, int MODE>
 __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_ens_update(const ChainDesc* __restrict__ cd,
                                                                const WorkItem* __restrict__ w) {
@@ -105,8 +106,8 @@ __global__ void __launch_bounds__(TUNE_MAX_BLOCK) k_ens_update(const ChainDesc* 
   a.seed = c.seed;
   a.sd = c.sd;
   a.adaptive = MODE == MODE_UPDATE_X ? 1 : 0;
-  const V2* in = (const V2*)(MODE == MODE_UPDATE_X ? c.Ui : c.C);
-  V2* out = (V2*)(MODE == MODE_DRIFTMAX ? c.Ui : c.Un);
+  const V2* in = (const V2*)(MODE == MODE_UPDATE_X ? c.Pq : c.C);
+  V2* out = (V2*)(MODE == MODE_DRIFTMAX ? c.Pq : c.Un);
   k_update_gather_body<T, MODE>(geo_of(c), (const V2*)c.U, in, out, a, it.vb);
 }
 

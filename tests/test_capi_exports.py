@@ -88,4 +88,8 @@ def test_oversized_lattice_is_rejected_before_any_device_work():
     p = cl.make_params((80, 80, 80, 80))
     with pytest.raises(cl.CLError):
         cl.cl_lattice_bytes(p)
-    assert cl.cl_lattice_bytes(cl.make_params((79, 79, 79, 79), prec=cl.CL_FP32_STORAGE)) > 150e9
+    b64 = cl.cl_lattice_bytes(cl.make_params((79, 79, 79, 79)))
+    b32 = cl.cl_lattice_bytes(cl.make_params((79, 79, 79, 79), prec=cl.CL_FP32_STORAGE))
+    assert b64 > 280e9  # 54 FP64 matrices per site: more than one GB300 holds
+    # FP32 storage: 50 matrices of half the size (no inverse field)
+    assert abs(b32 / b64 - 50 / 108) < 1e-3
